@@ -1,0 +1,163 @@
+/*
+ * ttfit.h -- C ABI of the GB300 variational MPO-MPO fit.
+ *
+ * The library approximates the product C ~ A B of two matrix product operators
+ * by a bond-limited MPO C, minimising ||A B - C||_F^2 (Sec. 2.3, Eq. fit_min)
+ * with the variational two-site fit (Alg. 5), whose local update is Alg. 3
+ * (site-canonical gauge) or Alg. 4 (inverse-canonical gauge), optionally with
+ * the randomized SVD of Sec. 3.1 in place of the exact SVD.
+ *
+ * Conventions shared by every entry point:
+ *   - An MPO of length L has cores X_l of shape (chi_{l-1}, d_l, d'_l, chi_l),
+ *     d the output leg and d' the input leg (Sec. 2, MPO definition), stored
+ *     row-major in that index order; chi_0 = chi_L = 1.
+ *   - C = A B contracts A's input leg with B's output leg (Sec. 2), so
+ *     A.d_in[l] must equal B.d_out[l].
+ *   - All core pointers are DEVICE pointers on the current CUDA device; all
+ *     other pointers are host pointers.
+ *   - No entry point throws; each returns a tt_status. A handle is bound to
+ *     the stream in its options and is not thread-safe. Argument errors leave
+ *     the handle usable; CUDA errors, device-side error words and numerical
+ *     failures poison it (every later call returns TT_ERR_STATE).
+ *   - There is no CPU fallback: every step of a sweep runs in this library's
+ *     CUDA kernels on the device.
+ */
+#ifndef TTFIT_H
+#define TTFIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TT_OK = 0,
+  TT_ERR_INVALID_ARGUMENT = 1, /* NULL where a value is required, chi_max < 1, tol < 0, ... */
+  TT_ERR_SHAPE_MISMATCH = 2,   /* L differ, A.d_in != B.d_out, bond[0] or bond[L] != 1      */
+  TT_ERR_OUT_OF_MEMORY = 3,    /* a device allocation failed (nothing leaks)                */
+  TT_ERR_CUDA = 4,             /* a CUDA runtime call or kernel launch failed               */
+  TT_ERR_NUMERICAL = 5,        /* NaN/Inf in a local tensor, SVD did not converge           */
+  TT_ERR_TIMEOUT = 6,          /* a bounded device-side wait gave up                        */
+  TT_ERR_STATE = 7             /* handle poisoned by an earlier error, or wrong call order  */
+} tt_status;
+
+/* Gauge of C (Sec. 2.3.1). SITE: C_l cores with an orthogonality centre moved by
+ * the sweep (Alg. 3). INVERSE: Psi_l cores and Y_l = Lambda_l^{-1} bond
+ * vectors (Alg. 4); C_l = Psi_l Y_l (l < L), C_L = Psi_L. */
+typedef enum { TT_GAUGE_SITE_CANONICAL = 0, TT_GAUGE_INVERSE_CANONICAL = 1 } tt_gauge;
+
+/* Local update: exact truncated SVD of the two-site tensor (Sec. 2.3.4), or the
+ * Gaussian-sketch randomized SVD (Sec. 3.1) with k = chi_max + oversample. */
+typedef enum { TT_UPDATE_2SITE_SVD = 0, TT_UPDATE_2SITE_RSVD = 1 } tt_update;
+
+/* Arithmetic of the contractions (environments, halves, two-site tensor).
+ * FP64: FP64 CUDA-core kernels. FP32: FP32 CUDA-core kernels.
+ * TF32 / BF16_SPLIT: tensor-core kernels (tcgen05) with FP32 accumulation;
+ * BF16_SPLIT uses hi+lo BF16 operand pairs (three products).
+ * The factorisation stage always returns FP64 factors. */
+typedef enum { TT_PREC_FP64 = 0, TT_PREC_FP32 = 1, TT_PREC_TF32 = 2, TT_PREC_BF16_SPLIT = 3 } tt_precision;
+
+/* Initial guess (Sec. 2.3.5). RANDOM: right-canonical MPO from a Philox4x32-10
+ * Gaussian stream (core 1 Gaussian, core l>=2 the orthonormal-row factor of a
+ * Gaussian matrix), bonds min(chi_max, prod d d' left, prod d d' right).
+ * COPY_B: B itself. GIVEN: options.init_C. The guess is brought to
+ * right-canonical form (orthogonality centre at site 1) before the sweeps. */
+typedef enum { TT_INIT_RANDOM = 0, TT_INIT_COPY_B = 1, TT_INIT_GIVEN = 2 } tt_init;
+
+typedef enum { TT_DTYPE_F64 = 0, TT_DTYPE_F32 = 1 } tt_dtype;
+
+/* Describes an MPO held by the caller. Arrays d_out, d_in have L entries and
+ * bond has L+1 (bond[0] = bond[L] = 1). cores[l] is a device pointer to
+ * bond[l]*d_out[l]*d_in[l]*bond[l+1] values of type dtype, row-major
+ * (chi_{l-1}, d, d', chi_l). The library never keeps these pointers. */
+typedef struct {
+  int L;
+  const int* d_out;
+  const int* d_in;
+  const int* bond;
+  void* const* cores;
+  int dtype; /* tt_dtype */
+} tt_mpo_desc;
+
+/* Options; pass NULL for defaults. struct_size must be sizeof(tt_fit_options). */
+typedef struct {
+  size_t struct_size;
+  int update;          /* tt_update, default TT_UPDATE_2SITE_SVD                          */
+  int oversample;      /* sketch columns beyond chi_max (RSVD), default 10                 */
+  uint64_t seed;       /* Philox key for the sketches and the random guess, default 0      */
+  int precision;       /* tt_precision, default TT_PREC_FP64                              */
+  int init;            /* tt_init, default TT_INIT_RANDOM                                 */
+  const tt_mpo_desc* init_C; /* for TT_INIT_GIVEN                                          */
+  double sv_cutoff;    /* drop s_j <= sv_cutoff * s_1; <0 = default (1e-13 FP64, 1e-6 else) */
+  double conv_tol;     /* delta threshold; <0 = use tol                                    */
+  void* stream;        /* cudaStream_t; NULL = legacy default stream                       */
+  int prepare_inputs;  /* 1 (default): RQ + QR sweep of A and B (Alg. 5 left_orthogonalize) */
+  uint32_t fault_inject; /* host-side fault injection for tests (TT_FAULT_*), default 0     */
+} tt_fit_options;
+
+/* Host-side fault injection (tests only; nothing here touches the device). */
+#define TT_FAULT_ALLOC_FAIL 0x1u  /* the create-time allocation reports out-of-memory       */
+#define TT_FAULT_NAN_INPUT 0x2u   /* treat the first local tensor as containing a NaN       */
+#define TT_FAULT_SVD_NOCONV 0x4u  /* report the first factorisation as not converged        */
+
+/* Per-call summary of tt_fit_sweep. */
+typedef struct {
+  int sweeps_done;      /* directional sweeps completed since create                       */
+  int converged;        /* 1 once delta <= conv_tol                                        */
+  double delta;         /* |n2_s - n2_{s-1}| / n2_s of the last sweep (inf after the first) */
+  double norm2_C;       /* ||C||^2 = sum of kept s^2 at the last window of the last sweep  */
+  double max_discarded; /* max over the last sweep's windows of sqrt(sum_{j>k} s_j^2)/||M|| */
+  double seconds;       /* wall time of this call (device work included)                   */
+} tt_sweep_report;
+
+typedef struct tt_fit tt_fit;
+
+/* Create a fit of C ~ A B with at most chi_max bond dimension and truncation
+ * tolerance tol (tau of Sec. 2.3.4: a window discards singular values while
+ * sqrt(sum of discarded s^2) <= (tol / L) ||M||_F; tol = 0 caps by chi_max only).
+ * A and B are copied (stream-ordered) and prepared: input canonicalisation
+ * (Alg. 5), initial guess, right environments R_L..R_3 and their halves.
+ * On success *out owns every device buffer; free it with tt_fit_destroy.
+ * Errors: TT_ERR_INVALID_ARGUMENT, TT_ERR_SHAPE_MISMATCH, TT_ERR_OUT_OF_MEMORY,
+ * TT_ERR_CUDA (then *out is NULL). */
+tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max, double tol,
+                        int gauge, const tt_fit_options* opt, tt_fit** out);
+
+/* Run up to n_sweeps directional sweeps of Alg. 5 (forward l = 1..L-1, then
+ * backward l = L-1..1, alternating; the direction continues across calls).
+ * Stops early once converged. rep may be NULL. Synchronises the handle's
+ * stream before returning. */
+tt_status tt_fit_sweep(tt_fit* h, int n_sweeps, tt_sweep_report* rep);
+
+/* Export C as a plain MPO. Two-step: with C->cores == NULL, fill
+ * C->L, and the caller-provided arrays C->d_out, C->d_in (L ints) and C->bond
+ * (L+1 ints); then call again with cores pointing to caller device buffers of
+ * the reported sizes in C->dtype. lambdas (nullable, host) receives, for each
+ * inner bond l = 1..L-1 in order, the bond[l] singular values of the last
+ * update of that bond. In the inverse gauge C_l = Psi_l Y_l (l < L). */
+tt_status tt_fit_result(const tt_fit* h, tt_mpo_desc* C, double* lambdas);
+
+/* Free every buffer of the handle (NULL is a no-op). */
+void tt_fit_destroy(tt_fit* h);
+
+const char* tt_status_string(tt_status s);
+
+/* Last error message of the handle ("" when none); valid until the next call.
+ * With h == NULL: the message of the calling thread's last failed
+ * tt_fit_create ("NULL handle" when there is none). */
+const char* tt_fit_last_error(const tt_fit* h);
+
+/* Per-stage device time of the last tt_fit_sweep call, in milliseconds, and
+ * the algorithmic FP64/FP32 flops of the contraction stages it ran:
+ * out[0] halves, out[1] two-site tensor, out[2] environment finish,
+ * out[3] factorisation, out[4] gauge update, out[5] contraction flops
+ * (minimal count), out[6] kernel launches issued. Returns TT_ERR_STATE if no
+ * sweep ran. */
+tt_status tt_fit_stage_times(const tt_fit* h, double out[7]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TTFIT_H */

@@ -16,7 +16,9 @@ Readings of the paper taken here (each also listed in the design doc):
   the product AB, so the same prepared A, B serve both gauges.
 * Initial guess: random right-canonical MPO (OC at site 1), bonds
   min(chi_max, prod of local dims to the left, to the right); core 1 Gaussian,
-  core l >= 2 the orthonormal-row factor of a Gaussian matrix.
+  core l >= 2 the orthonormal-row factor of a Gaussian matrix. A given guess
+  (or a copy of B) is trimmed by a QR sweep and then right-orthogonalized by
+  an RQ sweep; neither changes the operator.
   In the inverse gauge Psi_l = C0_l and Y_l = 1.
 * Truncation (Sec. 2.3.4): keep k = min(chi_max, min{k : sqrt(sum_{j>k} s_j^2)
   <= (tau/L) ||M||_F}), then drop s_j <= sv_cutoff * s_1 (Sec. 2.3.1 allows
@@ -24,6 +26,9 @@ Readings of the paper taken here (each also listed in the design doc):
 * Randomized update (Sec. 3.1): sketch width k_s = chi_max + oversample; when
   k_s >= min(m, n) the exact SVD is used. Omega is a fresh Philox Gaussian
   matrix per (sweep, window), n x k_s row-major.
+* Singular pairs carry a fixed sign: the largest-magnitude entry of u_j is
+  positive (the paper leaves the sign open; the sketch of Sec. 3.1 is not
+  invariant under sign changes of the bond basis, so both sides fix it).
 * Convergence: ||C||^2 = sum of kept s^2 at the last window of a sweep (the
   orthogonality centre); delta_s = | ||C||^2_s - ||C||^2_{s-1} | / ||C||^2_s.
 """
@@ -35,7 +40,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import philox
-from .mpo import canonicalize_input, qr_pos, right_orthogonalize
+from .mpo import canonicalize_input, left_orthogonalize, qr_pos, right_orthogonalize
 
 
 # --------------------------------------------------------------------------
@@ -78,6 +83,18 @@ def keep_rank(S, norm_M, tau, L, chi_max, sv_cutoff):
     if n:
         k = min(k, int(np.count_nonzero(S > sv_cutoff * S[0])))   # an all-zero M keeps k = 1
     return max(k, 1)
+
+
+def fix_signs(U, Vt):
+    """Sign convention of each singular pair: the entry of largest magnitude of
+    u_j is positive (first such index on ties). The pair (u_j, v_j) is defined
+    only up to a common sign; fixing it makes the bond bases, and with them the
+    Gaussian sketch of the randomized update, reproducible."""
+    if U.shape[1] == 0:
+        return U, Vt
+    i = np.argmax(np.abs(U), axis=0)
+    sgn = np.where(U[i, np.arange(U.shape[1])] < 0, -1.0, 1.0)
+    return U * sgn[None, :], Vt * sgn[:, None]
 
 
 def exact_svd(M):
@@ -141,6 +158,7 @@ class FitState:
     B: list
     Psi: list                      # C cores (site gauge: C_l; inverse gauge: Psi_l)
     Y: list                        # Y_l per bond l = 0..L (site gauge: all ones)
+    S: list = field(default_factory=list)   # kept singular values of the last update per bond
     Lenv: list = field(default_factory=list)
     Renv: list = field(default_factory=list)
     history: list = field(default_factory=list)
@@ -170,14 +188,14 @@ class FitOracle:
         din = [b.shape[2] for b in B]
         if init == "random":
             C0 = random_right_canonical(dout, din, self.chi_max, self.seed)
-        elif init == "copy_b":
-            C0 = right_orthogonalize(B)
+        elif init == "copy_b":                   # QR sweep (trims bonds), then RQ sweep
+            C0 = right_orthogonalize(left_orthogonalize(B))
         elif init == "given":
-            C0 = right_orthogonalize([np.asarray(x, np.float64) for x in init_C])
+            C0 = right_orthogonalize(left_orthogonalize([np.asarray(x, np.float64) for x in init_C]))
         else:
             raise ValueError(init)
         Y = [np.ones(1)] + [np.ones(C0[l].shape[3]) for l in range(L - 1)] + [np.ones(1)]
-        self.st = FitState(A=A, B=B, Psi=C0, Y=Y)
+        self.st = FitState(A=A, B=B, Psi=C0, Y=Y, S=[None] * (L + 1))
         self._precompute_right_envs()
 
     # cores seen by the environments: Psi_l Y_l (left) and Y_{l-1} Psi_l (right)
@@ -213,7 +231,9 @@ class FitOracle:
             U, S, Vt = exact_svd(M)
         k = keep_rank(S, norm_M, self.tau, L, self.chi_max, self.sv_cutoff)
         disc = math.sqrt(float(np.sum(S[k:] ** 2))) / norm_M if norm_M > 0 else 0.0
-        U, S, Vt = U[:, :k], S[:k], Vt[:k, :]
+        U, Vt = fix_signs(U[:, :k], Vt[:k, :])
+        S = S[:k]
+        st.S[l] = S.copy()
         if self.gauge == "site":
             if forward:                           # C_l, C_{l+1} <- U, S V^T
                 left, right = U, S[:, None] * Vt
@@ -265,8 +285,8 @@ class FitOracle:
         return [self._c_left(l) if l < L else self.st.Psi[L - 1].copy() for l in range(1, L + 1)]
 
     def lambdas(self):
-        """Singular values of the last update per bond (inverse gauge: 1/Y)."""
-        return [np.where(y != 0, 1.0 / np.where(y != 0, y, 1.0), 0.0) for y in self.st.Y[1:self.L]]
+        """Kept singular values of the last update of each inner bond 1..L-1."""
+        return [s.copy() for s in self.st.S[1:self.L]]
 
 
 def fit(A, B, chi_max, tol, n_sweeps, **kw):

@@ -1,0 +1,105 @@
+// Shared device/host helpers of the fit library (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+namespace ttfit {
+
+// Linear index -> memory offset through a mixed radix of up to three levels,
+// i = (i0 * n1 + i1) * n2 + i2, offset = i0*s0 + i1*s1 + i2*s2. Every tensor
+// permutation used by the contraction chain is a sum of two such maps (rows,
+// columns), so one GEMM kernel covers every layout.
+struct IdxMap {
+  int n1 = 1, n2 = 1;
+  long long s0 = 0, s1 = 0, s2 = 0;
+  __host__ __device__ __forceinline__ long long operator()(long long i) const {
+    long long i2 = i % n2;
+    long long t = i / n2;
+    long long i1 = t % n1;
+    long long i0 = t / n1;
+    return i0 * s0 + i1 * s1 + i2 * s2;
+  }
+  // uniform stride map
+  static IdxMap lin(long long s) {
+    IdxMap m;
+    m.s2 = s;
+    m.n2 = 1 << 30;
+    return m;
+  }
+  // two-level map: i = i1 * n2 + i2
+  static IdxMap two(int n2, long long s1, long long s2) {
+    IdxMap m;
+    m.n1 = 1 << 30;
+    m.n2 = n2;
+    m.s1 = s1;
+    m.s2 = s2;
+    return m;
+  }
+  static IdxMap three(int n1, int n2, long long s0, long long s1, long long s2) {
+    IdxMap m;
+    m.n1 = n1;
+    m.n2 = n2;
+    m.s0 = s0;
+    m.s1 = s1;
+    m.s2 = s2;
+    return m;
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11) and the Box-Muller Gaussian of element
+// i of stream s: counter (i lo, i hi, s lo, s hi), key (seed lo, seed hi);
+// ua = (x0*2^21 + (x1>>11)) 2^-53, ub = (x2*2^21 + (x3>>11)) 2^-53,
+// value sqrt(-2 ln(1-ua)) cos(2 pi ub).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox_round(uint32_t& c0, uint32_t& c1, uint32_t& c2, uint32_t& c3,
+                                             uint32_t k0, uint32_t k1) {
+  const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+  uint32_t lo0 = m0 * c0, hi0 = __umulhi(m0, c0);
+  uint32_t lo1 = m1 * c2, hi1 = __umulhi(m1, c2);
+  uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+  c0 = n0;
+  c1 = lo1;
+  c2 = n2;
+  c3 = lo0;
+}
+
+__device__ __forceinline__ double philox_normal(uint64_t seed, uint64_t stream, uint64_t idx) {
+  uint32_t c0 = (uint32_t)idx, c1 = (uint32_t)(idx >> 32), c2 = (uint32_t)stream, c3 = (uint32_t)(stream >> 32);
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    philox_round(c0, c1, c2, c3, k0, k1);
+  }
+  const double two53 = 1.0 / 9007199254740992.0;
+  double ua = (double)(((uint64_t)c0 << 21) + (c1 >> 11)) * two53;
+  double ub = (double)(((uint64_t)c2 << 21) + (c3 >> 11)) * two53;
+  return sqrt(-2.0 * log1p(-ua)) * cospi(2.0 * ub);
+}
+
+inline uint64_t omega_stream(int sweep, int site) {
+  return (1ull << 40) | ((uint64_t)sweep << 20) | (uint64_t)site;
+}
+inline uint64_t init_stream(int site) { return (2ull << 40) | (uint64_t)site; }
+
+// Device error word bits (written by kernels, read by the host after a window).
+enum : uint32_t {
+  ERRW_NAN = 1u,        // non-finite value in a two-site tensor
+  ERRW_NOCONV = 2u,     // Jacobi sweeps hit their limit
+  ERRW_BADSHAPE = 4u,   // a kernel saw dimensions outside its compiled limits
+  ERRW_TIMEOUT = 8u,    // a bounded mbarrier wait expired
+};
+
+}  // namespace ttfit

@@ -1,0 +1,1109 @@
+// Host driver of the variational MPO-MPO fit and its C ABI (include/ttfit.h).
+//
+// Sweep schedule (Alg. 5): right environments R_L..R_3 are precomputed; a
+// forward step at window (l, l+1) finishes L_{l-1} from the cached half
+// H1_{l-1} = L_{l-2} A_{l-1} B_{l-1} and the new C_{l-1}, builds the fresh half
+// H1_l = L_{l-1} A_l B_l, joins it with the cached H2_{l+1} = A_{l+1} B_{l+1} R_{l+2}
+// into the two-site tensor (Fig. derivatives (d)), factorises it and applies
+// Alg. 3 or Alg. 4. The backward step mirrors this. Each environment is thus
+// the paper's three-diagram contraction (Fig. envs) split as "half" (first two
+// diagrams, shared with the two-site tensor) and "finish" (third diagram).
+#include <cuda_runtime.h>
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/ttfit.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace ttfit;
+
+namespace {
+
+struct TTError : std::runtime_error {
+  tt_status code;
+  TTError(tt_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define CK(...)                                                                                      \
+  do {                                                                                               \
+    cudaError_t e_ = (__VA_ARGS__);                                                                  \
+    if (e_ != cudaSuccess)                                                                           \
+      throw TTError(e_ == cudaErrorMemoryAllocation ? TT_ERR_OUT_OF_MEMORY : TT_ERR_CUDA,             \
+                    std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_));                                \
+  } while (0)
+
+// Device allocations owned by a handle.
+struct DevPool {
+  std::vector<void*> ptrs;
+  uint32_t fault = 0;
+  template <typename T>
+  T* alloc(size_t n) {
+    if (fault & TT_FAULT_ALLOC_FAIL) throw TTError(TT_ERR_OUT_OF_MEMORY, "injected allocation failure");
+    void* p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw TTError(TT_ERR_OUT_OF_MEMORY, "cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes failed");
+    }
+    ptrs.push_back(p);
+    return (T*)p;
+  }
+  void release(void* p) {
+    for (auto& q : ptrs)
+      if (q == p) {
+        cudaFree(q);
+        q = nullptr;
+      }
+  }
+  ~DevPool() {
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+  }
+};
+
+struct Dims {
+  int L = 0;
+  std::vector<int> ds, du, dt;  // per site: A out, A in (= B out), B in
+  std::vector<int> a, b, c;     // bonds 0..L of A, B, C (current)
+  std::vector<int> cb;          // capacity of C bonds (buffer sizes)
+};
+
+}  // namespace
+
+struct tt_fit {
+  // configuration
+  int L = 0, chi_max = 0, gauge = 0, update = 0, oversample = 10, precision = 0, init = 0;
+  double tol = 0, cutoff = 1e-13, conv_tol = 0;
+  uint64_t seed = 0;
+  uint32_t fault = 0;
+  cudaStream_t st = nullptr;
+  int sm_count = 0;
+  Dims D;
+  DevPool pool;
+  // prepared inputs, FP64 natural layout
+  std::vector<double*> A64, B64;
+  // C (site gauge: C_l; inverse gauge: Psi_l), natural layout, FP64; Y per bond
+  std::vector<double*> C64, Y;
+  std::vector<std::vector<double>> lam;  // singular values of the last update per bond
+  // contraction tensors in the working type (float or double)
+  std::vector<void*> Aop, Anat, Bl, Br, Lenv, Renv, H1, H2, Ut, Vt;
+  void *X1 = nullptr, *Zs = nullptr, *Th = nullptr, *gws = nullptr;
+  size_t gws_elems = 0;
+  // factorisation workspace (FP64)
+  double *fX, *fQ, *fR, *fU, *fV, *fVw, *fS, *fUM, *fVM, *fOm, *fY, *fBt, *fQ2, *fR2;
+  size_t fsz = 0;
+  double* dnorm = nullptr;
+  int* dk = nullptr;
+  double* ddinfo = nullptr;
+  uint32_t* errw = nullptr;
+  // host mirrors (pinned)
+  int* hk = nullptr;
+  double* hdinfo = nullptr;
+  uint32_t* herrw = nullptr;
+  // state
+  int sweeps_done = 0;
+  bool forward = true, converged = false, poisoned = false;
+  double last_n2 = -1.0, delta = INFINITY, max_disc = 0.0;
+  bool fault_nan_pending = false, fault_noconv_pending = false;
+  std::string last_error;
+  // timing
+  cudaEvent_t ev[8] = {};      // stage boundaries of one window (0..4) and of its gauge update (5, 6)
+  bool gauge_pending = false;  // ev[5], ev[6] recorded but not yet read
+  double stage_ms[5] = {0, 0, 0, 0, 0};
+  double flops = 0;
+  long long launches = 0, tc_launches = 0;
+  bool have_times = false;
+  bool use_f32 = false;
+};
+
+namespace {
+
+inline long long prodll(std::initializer_list<long long> v) {
+  long long p = 1;
+  for (auto x : v) p *= x;
+  return p;
+}
+
+// ---------------------------------------------------------------------------
+// small helpers on FP64 device matrices
+// ---------------------------------------------------------------------------
+// Contraction dispatch: the tensor-core kernel for TF32 chains whenever TMA can
+// address both operands (16-byte aligned rows), the CUDA-core kernel otherwise
+// (FP64 / FP32 chains, and the 1- or 2-wide bonds at the ends of the chain).
+template <typename T>
+void gemm(tt_fit* h, const GemmArgs<T>& g, bool chain = false) {
+  const size_t wse = h->gws_elems * sizeof(double) / sizeof(T);
+  if constexpr (sizeof(T) == 4) {
+    if (chain && h->precision == TT_PREC_TF32 && (long long)g.M * g.N * g.K >= (1ll << 18)) {
+      cudaError_t e = gemm_tf32(g, (float*)h->gws, wse, h->sm_count, h->errw, h->st);
+      if (e == cudaSuccess) {
+        h->launches += 2;
+        h->tc_launches += 1;
+        return;
+      }
+      if (e != cudaErrorNotSupported) CK(e);
+    }
+  }
+  CK(gemm_simt<T>(g, (T*)h->gws, wse, h->sm_count, h->st));
+  h->launches += 2;
+}
+
+template <typename Tin, typename Tout>
+void copymap(tt_fit* h, int rows, int cols, const Tin* in, IdxMap im, IdxMap in_, Tout* out, IdxMap om, IdxMap on,
+             double scale = 1.0) {
+  CK(copy_map<Tin, Tout>(rows, cols, in, im, in_, out, om, on, scale, h->st));
+  h->launches += 1;
+}
+
+void qr(tt_fit* h, int q, int p, double* X, double* Q, double* R) {
+  if (h->use_f32) CK(qr_householder<float>(q, p, X, Q, R, h->st));
+  else CK(qr_householder<double>(q, p, X, Q, R, h->st));
+  h->launches += 1;
+}
+
+// Row-major (rows x cols) -> column-major copy (ld rows).
+void to_colmajor(tt_fit* h, int rows, int cols, const double* in, double* out) {
+  copymap<double, double>(h, rows, cols, in, IdxMap::lin(cols), IdxMap::lin(1), out, IdxMap::lin(1), IdxMap::lin(rows));
+}
+
+// Right-to-left RQ sweep (each core the orthonormal-row factor, bond trimmed to
+// min(rows, cols)); X's cores are replaced. bond updated.
+void rq_sweep(tt_fit* h, std::vector<double*>& X, std::vector<int>& bond, const std::vector<int>& dA,
+              const std::vector<int>& dB, int upto) {
+  const int L = (int)X.size();
+  for (int j = L - 1; j >= upto; --j) {
+    const int bl = bond[j], br = bond[j + 1], dd = dA[j] * dB[j];
+    const int q = dd * br, p = bl, r = std::min(q, p);
+    // core j row-major (bl x q) == column-major q x bl: QR of X_j^T
+    CK(cudaMemcpyAsync(h->fX, X[j], sizeof(double) * (size_t)q * p, cudaMemcpyDeviceToDevice, h->st));
+    qr(h, q, p, h->fX, h->fQ, h->fR);
+    double* nc = h->pool.alloc<double>((size_t)r * q);
+    CK(cudaMemcpyAsync(nc, h->fQ, sizeof(double) * (size_t)q * r, cudaMemcpyDeviceToDevice, h->st));
+    if (j > 0) {
+      const int bl2 = bond[j - 1], dd2 = dA[j - 1] * dB[j - 1];
+      double* np = h->pool.alloc<double>((size_t)bl2 * dd2 * r);
+      GemmArgs<double> g;
+      g.M = bl2 * dd2;
+      g.N = r;
+      g.K = bl;
+      g.A = X[j - 1];
+      g.am = IdxMap::lin(bl);
+      g.ak = IdxMap::lin(1);
+      g.B = h->fR;
+      g.bn = IdxMap::lin(1);
+      g.bk = IdxMap::lin(r);
+      g.b_kfast = false;
+      g.C = np;
+      g.cm = IdxMap::lin(r);
+      g.cn = IdxMap::lin(1);
+      gemm<double>(h, g);
+      CK(cudaStreamSynchronize(h->st));
+      h->pool.release(X[j - 1]);
+      X[j - 1] = np;
+    } else {
+      CK(cudaStreamSynchronize(h->st));
+    }
+    h->pool.release(X[j]);
+    X[j] = nc;
+    bond[j] = r;
+  }
+}
+
+// Left-to-right QR sweep (Alg. 5 left_orthogonalize), bonds trimmed.
+void qr_sweep(tt_fit* h, std::vector<double*>& X, std::vector<int>& bond, const std::vector<int>& dA,
+              const std::vector<int>& dB) {
+  const int L = (int)X.size();
+  for (int j = 0; j < L - 1; ++j) {
+    const int bl = bond[j], br = bond[j + 1], dd = dA[j] * dB[j];
+    const int q = bl * dd, p = br, r = std::min(q, p);
+    to_colmajor(h, q, p, X[j], h->fX);
+    qr(h, q, p, h->fX, h->fQ, h->fR);
+    double* nc = h->pool.alloc<double>((size_t)q * r);
+    copymap<double, double>(h, q, r, h->fQ, IdxMap::lin(1), IdxMap::lin(q), nc, IdxMap::lin(r), IdxMap::lin(1));
+    const int dd2 = dA[j + 1] * dB[j + 1], br2 = bond[j + 2];
+    const int N = dd2 * br2;
+    double* nn = h->pool.alloc<double>((size_t)r * N);
+    GemmArgs<double> g;
+    g.M = r;
+    g.N = N;
+    g.K = br;
+    g.A = h->fR;
+    g.am = IdxMap::lin(1);
+    g.ak = IdxMap::lin(r);
+    g.a_kfast = false;
+    g.B = X[j + 1];
+    g.bn = IdxMap::lin(1);
+    g.bk = IdxMap::lin(N);
+    g.b_kfast = false;
+    g.C = nn;
+    g.cm = IdxMap::lin(N);
+    g.cn = IdxMap::lin(1);
+    gemm<double>(h, g);
+    CK(cudaStreamSynchronize(h->st));
+    h->pool.release(X[j]);
+    h->pool.release(X[j + 1]);
+    X[j] = nc;
+    X[j + 1] = nn;
+    bond[j + 1] = r;
+  }
+}
+
+void check_errw(tt_fit* h, const char* where) {
+  if (*h->herrw & ERRW_NAN) throw TTError(TT_ERR_NUMERICAL, std::string("non-finite two-site tensor at ") + where);
+  if (*h->herrw & ERRW_NOCONV) throw TTError(TT_ERR_NUMERICAL, std::string("Jacobi SVD did not converge at ") + where);
+  if (*h->herrw & ERRW_TIMEOUT) throw TTError(TT_ERR_TIMEOUT, std::string("bounded device wait expired at ") + where);
+  if (*h->herrw) throw TTError(TT_ERR_NUMERICAL, std::string("device error word set at ") + where);
+}
+
+// ---------------------------------------------------------------------------
+// the contraction chain in working type T
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Chain {
+  tt_fit* h;
+  explicit Chain(tt_fit* hh) : h(hh) {}
+  T* P(void* p) { return (T*)p; }
+
+  // H1_j = L_{j-1} A_j B_j, stored [c0][s][t][a1][b1] (j is 0-based site index)
+  void half_left(int j) {
+    Dims& D = h->D;
+    const int a0 = D.a[j], a1 = D.a[j + 1], b0 = D.b[j], b1 = D.b[j + 1], c0 = D.c[j];
+    const int ds = D.ds[j], du = D.du[j], dt = D.dt[j];
+    GemmArgs<T> g;
+    g.M = c0 * b0;
+    g.N = ds * du * a1;
+    g.K = a0;
+    g.A = P(h->Lenv[j]);
+    g.am = IdxMap::lin(a0);
+    g.ak = IdxMap::lin(1);
+    g.B = P(h->Aop[j]);
+    g.bn = IdxMap::lin(a0);
+    g.bk = IdxMap::lin(1);
+    g.C = P(h->X1);
+    g.cm = IdxMap::two(b0, (long long)ds * a1 * b0 * du, du);
+    g.cn = IdxMap::three(du, a1, (long long)a1 * b0 * du, 1, (long long)b0 * du);
+    gemm<T>(h, g, true);
+    GemmArgs<T> g2;
+    g2.M = c0 * ds * a1;
+    g2.N = dt * b1;
+    g2.K = b0 * du;
+    g2.A = P(h->X1);
+    g2.am = IdxMap::lin((long long)b0 * du);
+    g2.ak = IdxMap::lin(1);
+    g2.B = P(h->Bl[j]);
+    g2.bn = IdxMap::lin((long long)b0 * du);
+    g2.bk = IdxMap::lin(1);
+    g2.C = P(h->H1[j]);
+    g2.cm = IdxMap::two(a1, (long long)dt * a1 * b1, b1);
+    g2.cn = IdxMap::two(b1, (long long)a1 * b1, 1);
+    gemm<T>(h, g2, true);
+    h->flops += 2.0 * g.M * g.N * g.K + 2.0 * g2.M * g2.N * g2.K;
+  }
+
+  // H2_j = A_j B_j R_{j+1}, stored [s][t][c1][a0][b0] (bond indices of site j)
+  void half_right(int j) {
+    Dims& D = h->D;
+    const int a1 = D.a[j], a2 = D.a[j + 1], b1 = D.b[j], b2 = D.b[j + 1], c2 = D.c[j + 1];
+    const int ds = D.ds[j], du = D.du[j], dt = D.dt[j];
+    GemmArgs<T> g;
+    g.M = a1 * ds * du;
+    g.N = c2 * b2;
+    g.K = a2;
+    g.A = P(h->Anat[j]);
+    g.am = IdxMap::lin(a2);
+    g.ak = IdxMap::lin(1);
+    g.B = P(h->Renv[j + 1]);
+    g.bn = IdxMap::lin(a2);
+    g.bk = IdxMap::lin(1);
+    g.C = P(h->Zs);
+    g.cm = IdxMap::two(du, (long long)c2 * du * b2, b2);
+    g.cn = IdxMap::two(b2, (long long)du * b2, 1);
+    gemm<T>(h, g, true);
+    GemmArgs<T> g2;
+    g2.M = a1 * ds * c2;
+    g2.N = b1 * dt;
+    g2.K = du * b2;
+    g2.A = P(h->Zs);
+    g2.am = IdxMap::lin((long long)du * b2);
+    g2.ak = IdxMap::lin(1);
+    g2.B = P(h->Br[j]);
+    g2.bn = IdxMap::lin((long long)du * b2);
+    g2.bk = IdxMap::lin(1);
+    g2.C = P(h->H2[j]);
+    g2.cm = IdxMap::three(ds, c2, b1, (long long)dt * c2 * a1 * b1, (long long)a1 * b1);
+    g2.cn = IdxMap::two(dt, 1, (long long)c2 * a1 * b1);
+    gemm<T>(h, g2, true);
+    h->flops += 2.0 * g.M * g.N * g.K + 2.0 * g2.M * g2.N * g2.K;
+  }
+
+  // Theta(window l, l+1) = H1_l . H2_{l+1}, row-major (c0 s1 t1) x (s2 t2 c2)
+  void join(int l, int& m, int& n) {
+    Dims& D = h->D;
+    const int a1 = D.a[l + 1], b1 = D.b[l + 1], c0 = D.c[l], c2 = D.c[l + 2];
+    m = c0 * D.ds[l] * D.dt[l];
+    n = D.ds[l + 1] * D.dt[l + 1] * c2;
+    GemmArgs<T> g;
+    g.M = m;
+    g.N = n;
+    g.K = a1 * b1;
+    g.A = P(h->H1[l]);
+    g.am = IdxMap::lin((long long)a1 * b1);
+    g.ak = IdxMap::lin(1);
+    g.B = P(h->H2[l + 1]);
+    g.bn = IdxMap::lin((long long)a1 * b1);
+    g.bk = IdxMap::lin(1);
+    g.C = P(h->Th);
+    g.cm = IdxMap::lin(n);
+    g.cn = IdxMap::lin(1);
+    gemm<T>(h, g, true);
+    h->flops += 2.0 * g.M * g.N * g.K;
+  }
+
+  // L_j (bond j+1) = Ut_j . H1_j ; stored [c][b][a]
+  void finish_left(int j) {
+    Dims& D = h->D;
+    const int a1 = D.a[j + 1], b1 = D.b[j + 1], c0 = D.c[j], c1 = D.c[j + 1];
+    const int K = c0 * D.ds[j] * D.dt[j];
+    GemmArgs<T> g;
+    g.M = c1;
+    g.N = a1 * b1;
+    g.K = K;
+    g.A = P(h->Ut[j]);
+    g.am = IdxMap::lin(K);
+    g.ak = IdxMap::lin(1);
+    g.B = P(h->H1[j]);
+    g.bn = IdxMap::lin(1);
+    g.bk = IdxMap::lin((long long)a1 * b1);
+    g.b_kfast = false;
+    g.C = P(h->Lenv[j + 1]);
+    g.cm = IdxMap::lin((long long)a1 * b1);
+    g.cn = IdxMap::two(b1, 1, a1);
+    gemm<T>(h, g, true);
+    h->flops += 2.0 * g.M * g.N * g.K;
+  }
+
+  // R_j (bond j) = Vt_j . H2_j ; stored [c][b][a]
+  void finish_right(int j) {
+    Dims& D = h->D;
+    const int a0 = D.a[j], b0 = D.b[j], c0 = D.c[j], c1 = D.c[j + 1];
+    const int K = D.ds[j] * D.dt[j] * c1;
+    GemmArgs<T> g;
+    g.M = c0;
+    g.N = a0 * b0;
+    g.K = K;
+    g.A = P(h->Vt[j]);
+    g.am = IdxMap::lin(K);
+    g.ak = IdxMap::lin(1);
+    g.B = P(h->H2[j]);
+    g.bn = IdxMap::lin(1);
+    g.bk = IdxMap::lin((long long)a0 * b0);
+    g.b_kfast = false;
+    g.C = P(h->Renv[j]);
+    g.cm = IdxMap::lin((long long)a0 * b0);
+    g.cn = IdxMap::two(b0, 1, a0);
+    gemm<T>(h, g, true);
+    h->flops += 2.0 * g.M * g.N * g.K;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// factorisation of the m x n two-site matrix (Sec. 2.3.4 / Sec. 3.1):
+// result U_M (m x p col-major, ld m), S (p, sorted), V_M (n x p, ld n).
+// Returns p (number of computed singular triplets).
+// ---------------------------------------------------------------------------
+template <typename T>
+int factorize(tt_fit* h, int m, int n, int sweep, int site1) {
+  const bool svd32 = h->use_f32;
+  auto jac = [&](int q, int p, double* W, double* U, double* S, double* V) {
+    if (svd32) CK(jacobi_svd<float>(q, p, W, U, S, V, h->fVw, 60, h->errw, h->st));
+    else CK(jacobi_svd<double>(q, p, W, U, S, V, h->fVw, 60, h->errw, h->st));
+    h->launches += 1;
+  };
+  // Theta (T, row-major) -> FP64 copy; norm (flags NaN/Inf)
+  const T* th = (const T*)h->Th;
+  double* M64 = h->fOm + 0;  // reuse: fOm is sized >= m*n? use fY scratch instead
+  M64 = h->fY;
+  copymap<T, double>(h, m, n, th, IdxMap::lin(n), IdxMap::lin(1), M64, IdxMap::lin(n), IdxMap::lin(1));
+  CK(frob_norm<double>(M64, (long long)m * n, h->dnorm, h->errw, h->st));
+  h->launches += 1;
+  const int ks = h->chi_max + h->oversample;
+  if (h->update == TT_UPDATE_2SITE_RSVD && ks < std::min(m, n)) {
+    CK(philox_fill(h->fOm, (long long)n * ks, h->seed, omega_stream(sweep, site1), 1.0, h->st));
+    h->launches += 1;
+    GemmArgs<double> g;  // Ysk = M Omega (m x ks, col-major)
+    g.M = m; g.N = ks; g.K = n;
+    g.A = M64; g.am = IdxMap::lin(n); g.ak = IdxMap::lin(1);
+    g.B = h->fOm; g.bn = IdxMap::lin(1); g.bk = IdxMap::lin(ks); g.b_kfast = false;
+    g.C = h->fX; g.cm = IdxMap::lin(1); g.cn = IdxMap::lin(m);
+    gemm<double>(h, g);
+    qr(h, m, ks, h->fX, h->fQ, h->fR);                 // Q (m x ks)
+    GemmArgs<double> g2;  // Bm^T = M^T Q (n x ks, col-major)
+    g2.M = n; g2.N = ks; g2.K = m;
+    g2.A = M64; g2.am = IdxMap::lin(1); g2.ak = IdxMap::lin(n); g2.a_kfast = false;
+    g2.B = h->fQ; g2.bn = IdxMap::lin(m); g2.bk = IdxMap::lin(1);
+    g2.C = h->fBt; g2.cm = IdxMap::lin(1); g2.cn = IdxMap::lin(n);
+    gemm<double>(h, g2);
+    qr(h, n, ks, h->fBt, h->fQ2, h->fR2);              // Bm^T = Q2 R2
+    jac(ks, ks, h->fR2, h->fU, h->fS, h->fV);          // R2 = Ur S Vr^T
+    GemmArgs<double> g3;  // U_M = Q Vr (m x ks)
+    g3.M = m; g3.N = ks; g3.K = ks;
+    g3.A = h->fQ; g3.am = IdxMap::lin(1); g3.ak = IdxMap::lin(m); g3.a_kfast = false;
+    g3.B = h->fV; g3.bn = IdxMap::lin(ks); g3.bk = IdxMap::lin(1);
+    g3.C = h->fUM; g3.cm = IdxMap::lin(1); g3.cn = IdxMap::lin(m);
+    gemm<double>(h, g3);
+    GemmArgs<double> g4;  // V_M = Q2 Ur (n x ks)
+    g4.M = n; g4.N = ks; g4.K = ks;
+    g4.A = h->fQ2; g4.am = IdxMap::lin(1); g4.ak = IdxMap::lin(n); g4.a_kfast = false;
+    g4.B = h->fU; g4.bn = IdxMap::lin(ks); g4.bk = IdxMap::lin(1);
+    g4.C = h->fVM; g4.cm = IdxMap::lin(1); g4.cn = IdxMap::lin(n);
+    gemm<double>(h, g4);
+    CK(fix_signs(m, n, ks, h->fUM, m, h->fVM, n, h->st));
+    h->launches += 1;
+    return ks;
+  }
+  // exact: work on the tall orientation X (q x p col-major)
+  const bool tr = m < n;
+  const int q = tr ? n : m, p = tr ? m : n;
+  if (tr) CK(cudaMemcpyAsync(h->fX, M64, sizeof(double) * (size_t)m * n, cudaMemcpyDeviceToDevice, h->st));
+  else to_colmajor(h, m, n, M64, h->fX);
+  double* Ufull;
+  if (q > p) {
+    qr(h, q, p, h->fX, h->fQ, h->fR);                  // X = Qx Rx
+    jac(p, p, h->fR, h->fU, h->fS, h->fV);             // Rx = Ur S Vr^T
+    GemmArgs<double> g;  // Ufull = Qx Ur (q x p)
+    g.M = q; g.N = p; g.K = p;
+    g.A = h->fQ; g.am = IdxMap::lin(1); g.ak = IdxMap::lin(q); g.a_kfast = false;
+    g.B = h->fU; g.bn = IdxMap::lin(p); g.bk = IdxMap::lin(1);
+    g.C = h->fBt; g.cm = IdxMap::lin(1); g.cn = IdxMap::lin(q);
+    gemm<double>(h, g);
+    Ufull = h->fBt;
+  } else {
+    jac(q, p, h->fX, h->fU, h->fS, h->fV);
+    Ufull = h->fU;
+  }
+  // X = Ufull S Vr^T ; Theta = X (tr = false) or X^T (tr = true)
+  const size_t qb = sizeof(double) * (size_t)q * p, pb = sizeof(double) * (size_t)p * p;
+  if (!tr) {
+    CK(cudaMemcpyAsync(h->fUM, Ufull, qb, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(h->fVM, h->fV, pb, cudaMemcpyDeviceToDevice, h->st));
+  } else {
+    CK(cudaMemcpyAsync(h->fUM, h->fV, pb, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(h->fVM, Ufull, qb, cudaMemcpyDeviceToDevice, h->st));
+  }
+  CK(fix_signs(m, n, p, h->fUM, m, h->fVM, n, h->st));
+  h->launches += 1;
+  return p;
+}
+
+template <typename T>
+struct Sweeper {
+  tt_fit* h;
+  Chain<T> ch;
+  explicit Sweeper(tt_fit* hh) : h(hh), ch(hh) {}
+
+  void add(int stage, int e0, int e1) {
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, h->ev[e0], h->ev[e1]));
+    h->stage_ms[stage] += ms;
+  }
+  // the previous window's gauge update has completed once the stream has been synchronised
+  void resolve_gauge() {
+    if (h->gauge_pending) add(4, 5, 6);
+    h->gauge_pending = false;
+  }
+
+  // one window update; returns kept sum of s^2 and the discarded fraction
+  void window(int l, bool fwd, int sweep, double& n2, double& disc) {
+    Dims& D = h->D;
+    const int L = D.L;
+    CK(cudaEventRecord(h->ev[0], h->st));
+    if (fwd) {
+      if (l >= 1) ch.finish_left(l - 1);
+      CK(cudaEventRecord(h->ev[1], h->st));
+      ch.half_left(l);
+    } else {
+      if (l + 2 <= L - 1) ch.finish_right(l + 2);
+      CK(cudaEventRecord(h->ev[1], h->st));
+      ch.half_right(l + 1);
+    }
+    CK(cudaEventRecord(h->ev[2], h->st));
+    int m, n;
+    ch.join(l, m, n);
+    CK(cudaEventRecord(h->ev[3], h->st));
+    int p = factorize<T>(h, m, n, sweep, l + 1);
+    const double cut = h->cutoff;
+    CK(truncate_rule(h->fS, p, h->dnorm, h->tol / L, h->chi_max, cut, h->dk, h->ddinfo, h->st));
+    h->launches += 1;
+    CK(cudaEventRecord(h->ev[4], h->st));
+    CK(cudaMemcpyAsync(h->hk, h->dk, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(h->hdinfo, h->ddinfo, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaMemcpyAsync(h->herrw, h->errw, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    add(2, 0, 1);
+    add(0, 1, 2);
+    add(1, 2, 3);
+    add(3, 3, 4);
+    resolve_gauge();
+    if (h->fault_nan_pending) {
+      h->fault_nan_pending = false;
+      *h->herrw |= ERRW_NAN;
+    }
+    if (h->fault_noconv_pending) {
+      h->fault_noconv_pending = false;
+      *h->herrw |= ERRW_NOCONV;
+    }
+    char where[64];
+    snprintf(where, sizeof where, "window %d", l + 1);
+    check_errw(h, where);
+    const int k = *h->hk;
+    n2 = h->hdinfo[0];
+    disc = h->hdinfo[1];
+    if (k < 1 || k > D.cb[l + 1]) throw TTError(TT_ERR_NUMERICAL, "kept rank outside the bond capacity");
+    D.c[l + 1] = k;
+    // gauge update (Alg. 3 / Alg. 4)
+    const int mode = (h->gauge == TT_GAUGE_INVERSE_CANONICAL) ? 2 : (fwd ? 0 : 1);
+    CK(cudaEventRecord(h->ev[5], h->st));
+    CK(gauge_update<T>(mode, m, n, h->fUM, m, h->fS, h->fVM, n, h->dk, h->C64[l], h->C64[l + 1], h->Y[l + 1],
+                       (T*)h->Ut[l], (T*)h->Vt[l + 1], h->st));
+    h->launches += 1;
+    CK(cudaEventRecord(h->ev[6], h->st));
+    h->gauge_pending = true;
+    // host copy of the kept spectrum for tt_fit_result
+    h->lam[l + 1].resize(k);
+    CK(cudaMemcpyAsync(h->lam[l + 1].data(), h->fS, sizeof(double) * k, cudaMemcpyDeviceToHost, h->st));
+  }
+
+  void run(int n_sweeps) {
+    const int L = h->D.L;
+    for (int s = 0; s < n_sweeps; ++s) {
+      if (h->converged) break;
+      const int sweep = h->sweeps_done;
+      double n2 = 0, disc = 0, maxd = 0;
+      if (h->forward) {
+        for (int l = 0; l <= L - 2; ++l) {
+          window(l, true, sweep, n2, disc);
+          maxd = std::max(maxd, disc);
+        }
+      } else {
+        for (int l = L - 2; l >= 0; --l) {
+          window(l, false, sweep, n2, disc);
+          maxd = std::max(maxd, disc);
+        }
+      }
+      CK(cudaStreamSynchronize(h->st));
+      resolve_gauge();
+      h->delta = (h->last_n2 >= 0 && n2 > 0) ? std::fabs(n2 - h->last_n2) / n2 : INFINITY;
+      h->last_n2 = n2;
+      h->max_disc = maxd;
+      h->sweeps_done++;
+      h->forward = !h->forward;
+      if (h->delta <= h->conv_tol) h->converged = true;
+    }
+  }
+
+  // R_L .. R_3 and the halves H2_L .. H2_2 from the initial guess (Alg. 5)
+  void precompute_right() {
+    const int L = h->D.L;
+    for (int j = L - 1; j >= 1; --j) {
+      ch.half_right(j);
+      if (j >= 2) ch.finish_right(j);
+    }
+    CK(cudaStreamSynchronize(h->st));
+  }
+};
+
+// ---------------------------------------------------------------------------
+void read_desc(const tt_mpo_desc* X, int& L, std::vector<int>& dout, std::vector<int>& din, std::vector<int>& bond) {
+  if (!X || X->L < 1 || !X->d_out || !X->d_in || !X->bond || !X->cores)
+    throw TTError(TT_ERR_INVALID_ARGUMENT, "MPO descriptor missing fields");
+  if (X->dtype != TT_DTYPE_F64 && X->dtype != TT_DTYPE_F32) throw TTError(TT_ERR_INVALID_ARGUMENT, "unknown dtype");
+  L = X->L;
+  dout.assign(X->d_out, X->d_out + L);
+  din.assign(X->d_in, X->d_in + L);
+  bond.assign(X->bond, X->bond + L + 1);
+  if (bond[0] != 1 || bond[L] != 1) throw TTError(TT_ERR_SHAPE_MISMATCH, "bond[0] and bond[L] must be 1");
+  for (int l = 0; l < L; ++l) {
+    if (dout[l] < 1 || din[l] < 1 || bond[l] < 1) throw TTError(TT_ERR_INVALID_ARGUMENT, "non-positive dimension");
+    if (!X->cores[l]) throw TTError(TT_ERR_INVALID_ARGUMENT, "NULL core pointer");
+  }
+}
+
+void upload(tt_fit* h, const tt_mpo_desc* X, const std::vector<int>& dout, const std::vector<int>& din,
+            const std::vector<int>& bond, std::vector<double*>& out) {
+  out.resize(X->L);
+  for (int l = 0; l < X->L; ++l) {
+    const long long n = prodll({bond[l], dout[l], din[l], bond[l + 1]});
+    out[l] = h->pool.alloc<double>(n);
+    if (X->dtype == TT_DTYPE_F64)
+      copymap<double, double>(h, 1, (int)n, (const double*)X->cores[l], IdxMap::lin(0), IdxMap::lin(1), out[l],
+                              IdxMap::lin(0), IdxMap::lin(1));
+    else
+      copymap<float, double>(h, 1, (int)n, (const float*)X->cores[l], IdxMap::lin(0), IdxMap::lin(1), out[l],
+                             IdxMap::lin(0), IdxMap::lin(1));
+  }
+}
+
+template <typename T>
+void build_operands(tt_fit* h) {
+  Dims& D = h->D;
+  const int L = D.L;
+  h->Aop.assign(L, nullptr);
+  h->Anat.assign(L, nullptr);
+  h->Bl.assign(L, nullptr);
+  h->Br.assign(L, nullptr);
+  for (int j = 0; j < L; ++j) {
+    const int a0 = D.a[j], a1 = D.a[j + 1], b0 = D.b[j], b1 = D.b[j + 1];
+    const int ds = D.ds[j], du = D.du[j], dt = D.dt[j];
+    T* aop = h->pool.alloc<T>((size_t)a0 * ds * du * a1);
+    T* anat = h->pool.alloc<T>((size_t)a0 * ds * du * a1);
+    T* bl = h->pool.alloc<T>((size_t)b0 * du * dt * b1);
+    T* br = h->pool.alloc<T>((size_t)b0 * du * dt * b1);
+    // A natural (a0, s, u, a1) -> row i = a0, col = (s u a1)
+    copymap<double, T>(h, a0, ds * du * a1, h->A64[j], IdxMap::lin((long long)ds * du * a1), IdxMap::lin(1), anat,
+                       IdxMap::lin((long long)ds * du * a1), IdxMap::lin(1));
+    // Aop [s][u][a1][a0]: element (a0, n=(s u a1)) at n*a0n + a0
+    copymap<double, T>(h, a0, ds * du * a1, h->A64[j], IdxMap::lin((long long)ds * du * a1), IdxMap::lin(1), aop,
+                       IdxMap::lin(1), IdxMap::lin(a0));
+    // B natural (b0, u, t, b1): row = b0, col = (u, t, b1) three-level
+    // Bl [t][b1][b0][u]: offset ((t*b1n + b1)*b0n + b0)*du + u
+    copymap<double, T>(h, b0, du * dt * b1, h->B64[j], IdxMap::lin((long long)du * dt * b1), IdxMap::lin(1), bl,
+                       IdxMap::lin(du), IdxMap::three(dt, b1, 1, (long long)b1 * b0 * du, (long long)b0 * du));
+    // Br [b0][t][u][b1]: offset ((b0*dt + t)*du + u)*b1n + b1
+    copymap<double, T>(h, b0, du * dt * b1, h->B64[j], IdxMap::lin((long long)du * dt * b1), IdxMap::lin(1), br,
+                       IdxMap::lin((long long)dt * du * b1), IdxMap::three(dt, b1, b1, (long long)du * b1, 1));
+    h->Aop[j] = aop;
+    h->Anat[j] = anat;
+    h->Bl[j] = bl;
+    h->Br[j] = br;
+  }
+}
+
+template <typename T>
+void allocate_chain(tt_fit* h) {
+  Dims& D = h->D;
+  const int L = D.L;
+  h->Lenv.assign(L + 1, nullptr);
+  h->Renv.assign(L + 1, nullptr);
+  h->H1.assign(L, nullptr);
+  h->H2.assign(L, nullptr);
+  h->Ut.assign(L, nullptr);
+  h->Vt.assign(L, nullptr);
+  size_t x1 = 1, zs = 1;
+  long long mmax = 1, nmax = 1;
+  for (int j = 0; j <= L; ++j) {
+    const long long e = prodll({D.a[j], D.b[j], D.cb[j]});
+    h->Lenv[j] = h->pool.alloc<T>(e);
+    h->Renv[j] = h->pool.alloc<T>(e);
+  }
+  for (int j = 0; j < L; ++j) {
+    const int ds = D.ds[j], du = D.du[j], dt = D.dt[j];
+    h->H1[j] = h->pool.alloc<T>(prodll({D.cb[j], ds, dt, D.a[j + 1], D.b[j + 1]}));
+    h->H2[j] = h->pool.alloc<T>(prodll({D.a[j], D.b[j], ds, dt, D.cb[j + 1]}));
+    h->Ut[j] = h->pool.alloc<T>(prodll({D.cb[j + 1], D.cb[j], ds, dt}));
+    h->Vt[j] = h->pool.alloc<T>(prodll({D.cb[j], ds, dt, D.cb[j + 1]}));
+    x1 = std::max<size_t>(x1, prodll({D.cb[j], D.b[j], ds, du, D.a[j + 1]}));
+    zs = std::max<size_t>(zs, prodll({D.a[j], ds, du, D.cb[j + 1], D.b[j + 1]}));
+    mmax = std::max<long long>(mmax, (long long)D.cb[j] * ds * dt);
+    nmax = std::max<long long>(nmax, (long long)ds * dt * D.cb[j + 1]);
+  }
+  h->X1 = h->pool.alloc<T>(x1);
+  h->Zs = h->pool.alloc<T>(zs);
+  h->Th = h->pool.alloc<T>((size_t)mmax * nmax);
+  // split-K workspace: up to 64 partial M x N tiles of the largest GEMM output we split
+  h->gws_elems = (size_t)std::max<long long>(mmax * nmax, 1) * 16 + (1 << 20);
+  h->gws = h->pool.alloc<double>(h->gws_elems);
+  const long long big = std::max(mmax, nmax);
+  const long long ks = h->chi_max + h->oversample;
+  const long long side = std::max(big, ks);
+  h->fsz = (size_t)side * side;
+  h->fX = h->pool.alloc<double>(h->fsz);
+  h->fQ = h->pool.alloc<double>(h->fsz);
+  h->fR = h->pool.alloc<double>(h->fsz);
+  h->fU = h->pool.alloc<double>(h->fsz);
+  h->fV = h->pool.alloc<double>(h->fsz);
+  h->fVw = h->pool.alloc<double>(h->fsz);
+  h->fS = h->pool.alloc<double>(side);
+  h->fUM = h->pool.alloc<double>(h->fsz);
+  h->fVM = h->pool.alloc<double>(h->fsz);
+  h->fOm = h->pool.alloc<double>(h->fsz);
+  h->fY = h->pool.alloc<double>(h->fsz);
+  h->fBt = h->pool.alloc<double>(h->fsz);
+  h->fQ2 = h->pool.alloc<double>(h->fsz);
+  h->fR2 = h->pool.alloc<double>(h->fsz);
+}
+
+template <typename T>
+void setup(tt_fit* h, const std::vector<double*>& C0) {
+  Dims& D = h->D;
+  const int L = D.L;
+  build_operands<T>(h);
+  allocate_chain<T>(h);
+  // C state: FP64 cores at capacity size, Y per bond = 1, env operands from C0
+  h->C64.assign(L, nullptr);
+  h->Y.assign(L + 1, nullptr);
+  h->lam.assign(L + 1, {});
+  for (int j = 0; j < L; ++j) {
+    const long long cap = prodll({D.cb[j], D.ds[j], D.dt[j], D.cb[j + 1]});
+    h->C64[j] = h->pool.alloc<double>(cap);
+    const long long n = prodll({D.c[j], D.ds[j], D.dt[j], D.c[j + 1]});
+    CK(cudaMemcpyAsync(h->C64[j], C0[j], sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+    // Vt_j = C0_j as (c_j-1) x (s t c_j) row-major
+    copymap<double, T>(h, 1, (int)n, C0[j], IdxMap::lin(0), IdxMap::lin(1), (T*)h->Vt[j], IdxMap::lin(0),
+                       IdxMap::lin(1));
+  }
+  std::vector<double> ones(1024, 1.0);
+  for (int j = 0; j <= L; ++j) {
+    h->Y[j] = h->pool.alloc<double>(std::max(D.cb[j], 1));
+    int n = D.c[j];
+    for (int off = 0; off < n; off += 1024)
+      CK(cudaMemcpyAsync(h->Y[j] + off, ones.data(), sizeof(double) * std::min(1024, n - off), cudaMemcpyHostToDevice,
+                         h->st));
+  }
+  // trivial environments L_0 = R_{L+1} = [1]  (Sec. 2.3.3)
+  T one = T(1);
+  CK(cudaMemcpyAsync(h->Lenv[0], &one, sizeof(T), cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemcpyAsync(h->Renv[L], &one, sizeof(T), cudaMemcpyHostToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  Sweeper<T> sw(h);
+  sw.precompute_right();
+}
+
+thread_local std::string g_create_error;
+
+void poison(tt_fit* h, const TTError& e) {
+  h->poisoned = true;
+  h->last_error = e.what();
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* tt_status_string(tt_status s) {
+  switch (s) {
+    case TT_OK: return "ok";
+    case TT_ERR_INVALID_ARGUMENT: return "invalid argument";
+    case TT_ERR_SHAPE_MISMATCH: return "shape mismatch";
+    case TT_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case TT_ERR_CUDA: return "CUDA error";
+    case TT_ERR_NUMERICAL: return "numerical failure";
+    case TT_ERR_TIMEOUT: return "device wait timed out";
+    case TT_ERR_STATE: return "invalid handle state";
+  }
+  return "unknown status";
+}
+
+const char* tt_fit_last_error(const tt_fit* h) {
+  if (h) return h->last_error.c_str();
+  return g_create_error.empty() ? "NULL handle" : g_create_error.c_str();
+}
+
+tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max, double tol, int gauge,
+                        const tt_fit_options* opt, tt_fit** out) {
+  if (!out) return TT_ERR_INVALID_ARGUMENT;
+  *out = nullptr;
+  g_create_error.clear();
+  tt_fit* h = nullptr;
+  try {
+    if (chi_max < 1 || !(tol >= 0.0) || (gauge != 0 && gauge != 1)) return TT_ERR_INVALID_ARGUMENT;
+    tt_fit_options o{};
+    o.struct_size = sizeof(o);
+    o.update = TT_UPDATE_2SITE_SVD;
+    o.oversample = 10;
+    o.precision = TT_PREC_FP64;
+    o.init = TT_INIT_RANDOM;
+    o.sv_cutoff = -1;
+    o.conv_tol = -1;
+    o.prepare_inputs = 1;
+    if (opt) {
+      if (opt->struct_size != sizeof(tt_fit_options)) return TT_ERR_INVALID_ARGUMENT;
+      o = *opt;
+    }
+    if (o.update != 0 && o.update != 1) return TT_ERR_INVALID_ARGUMENT;
+    if (o.precision < 0 || o.precision > 3 || o.oversample < 0) return TT_ERR_INVALID_ARGUMENT;
+    if (o.init < 0 || o.init > 2 || (o.init == TT_INIT_GIVEN && !o.init_C)) return TT_ERR_INVALID_ARGUMENT;
+    if (o.precision == TT_PREC_BF16_SPLIT) return TT_ERR_INVALID_ARGUMENT;  // not in this build
+    int LA, LB;
+    std::vector<int> doA, diA, bA, doB, diB, bB;
+    read_desc(A, LA, doA, diA, bA);
+    read_desc(B, LB, doB, diB, bB);
+    if (LA != LB) return TT_ERR_SHAPE_MISMATCH;
+    if (LA < 2) return TT_ERR_INVALID_ARGUMENT;
+    for (int l = 0; l < LA; ++l)
+      if (diA[l] != doB[l]) return TT_ERR_SHAPE_MISMATCH;
+    h = new tt_fit();
+    h->fault = o.fault_inject;
+    h->pool.fault = o.fault_inject & TT_FAULT_ALLOC_FAIL;
+    h->fault_nan_pending = (o.fault_inject & TT_FAULT_NAN_INPUT) != 0;
+    h->fault_noconv_pending = (o.fault_inject & TT_FAULT_SVD_NOCONV) != 0;
+    h->L = LA;
+    h->chi_max = chi_max;
+    h->tol = tol;
+    h->gauge = gauge;
+    h->update = o.update;
+    h->oversample = o.oversample;
+    h->precision = o.precision;
+    h->init = o.init;
+    h->seed = o.seed;
+    h->use_f32 = (o.precision != TT_PREC_FP64);
+    h->cutoff = o.sv_cutoff >= 0 ? o.sv_cutoff : (o.precision == TT_PREC_FP64 ? 1e-13 : 1e-6);
+    h->conv_tol = o.conv_tol >= 0 ? o.conv_tol : tol;
+    h->st = (cudaStream_t)o.stream;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaMalloc(&h->dnorm, sizeof(double)));
+    h->pool.ptrs.push_back(h->dnorm);
+    h->dk = h->pool.alloc<int>(4);
+    h->ddinfo = h->pool.alloc<double>(4);
+    h->errw = h->pool.alloc<uint32_t>(1);
+    CK(cudaMemsetAsync(h->errw, 0, sizeof(uint32_t), h->st));
+    for (auto& e : h->ev) CK(cudaEventCreate(&e));
+    CK(cudaMallocHost(&h->hk, sizeof(int) * 4));
+    CK(cudaMallocHost(&h->hdinfo, sizeof(double) * 4));
+    CK(cudaMallocHost(&h->herrw, sizeof(uint32_t) * 4));
+    *h->herrw = 0;
+    Dims& D = h->D;
+    D.L = LA;
+    D.ds = doA;
+    D.du = diA;
+    D.dt = diB;
+    D.a = bA;
+    D.b = bB;
+    upload(h, A, doA, diA, bA, h->A64);
+    upload(h, B, doB, diB, bB, h->B64);
+    CK(cudaStreamSynchronize(h->st));
+    {  // scratch of the input / guess canonicalisation sweeps (released before the chain is allocated)
+      long long mc = 1;
+      for (int l = 0; l < LA; ++l) {
+        mc = std::max(mc, prodll({bA[l], doA[l], diA[l], bA[l + 1]}));
+        mc = std::max(mc, prodll({bB[l], doB[l], diB[l], bB[l + 1]}));
+      }
+      if (o.init == TT_INIT_GIVEN) {
+        const tt_mpo_desc* g = o.init_C;
+        if (g->L == LA && g->bond && g->d_out && g->d_in)
+          for (int l = 0; l < LA; ++l)
+            mc = std::max(mc, prodll({g->bond[l], g->d_out[l], g->d_in[l], g->bond[l + 1]}));
+      }
+      h->fX = h->pool.alloc<double>(mc);
+      h->fQ = h->pool.alloc<double>(mc);
+      h->fR = h->pool.alloc<double>(mc);
+      h->gws_elems = (size_t)mc * 16 + (1 << 20);
+      h->gws = h->pool.alloc<double>(h->gws_elems);
+    }
+    if (o.prepare_inputs) {  // Alg. 5: left_orthogonalize(A), left_orthogonalize(B)
+      rq_sweep(h, h->A64, D.a, D.ds, D.du, 1);
+      qr_sweep(h, h->A64, D.a, D.ds, D.du);
+      rq_sweep(h, h->B64, D.b, D.du, D.dt, 1);
+      qr_sweep(h, h->B64, D.b, D.du, D.dt);
+    }
+    // capacity of C bonds: min(chi_max, prod of local dims to the left / right)
+    const int L = LA;
+    D.cb.assign(L + 1, 1);
+    for (int l = 1; l < L; ++l) {
+      double left = 1, right = 1;
+      for (int j = 0; j < l; ++j) left *= (double)D.ds[j] * D.dt[j];
+      for (int j = l; j < L; ++j) right *= (double)D.ds[j] * D.dt[j];
+      D.cb[l] = (int)std::min<double>(chi_max, std::min(left, right));
+    }
+    // initial guess (right-canonical, orthogonality centre at site 1)
+    std::vector<double*> C0(L);
+    std::vector<int> cbond;
+    if (o.init == TT_INIT_RANDOM) {
+      cbond = D.cb;
+      for (int j = 0; j < L; ++j) {
+        const long long n = prodll({cbond[j], D.ds[j], D.dt[j], cbond[j + 1]});
+        C0[j] = h->pool.alloc<double>(n);
+        CK(philox_fill(C0[j], n, h->seed, init_stream(j + 1), 1.0, h->st));
+        if (j > 0) {  // orthonormal rows: QR of the transposed core (q >= p by the bond rule)
+          const int q = D.ds[j] * D.dt[j] * cbond[j + 1], p = cbond[j];
+          double* R = h->pool.alloc<double>((size_t)p * p);
+          double* Q = h->pool.alloc<double>((size_t)q * p);
+          qr(h, q, p, C0[j], Q, R);
+          CK(cudaStreamSynchronize(h->st));
+          h->pool.release(C0[j]);
+          h->pool.release(R);
+          C0[j] = Q;
+        }
+      }
+      CK(cudaStreamSynchronize(h->st));
+    } else {
+      std::vector<int> dz, bz;
+      const tt_mpo_desc* src = (o.init == TT_INIT_COPY_B) ? nullptr : o.init_C;
+      std::vector<double*> G;
+      if (src) {
+        int LC;
+        std::vector<int> doC, diC;
+        read_desc(src, LC, doC, diC, bz);
+        if (LC != L) throw TTError(TT_ERR_SHAPE_MISMATCH, "init_C length");
+        for (int l = 0; l < L; ++l)
+          if (doC[l] != D.ds[l] || diC[l] != D.dt[l]) throw TTError(TT_ERR_SHAPE_MISMATCH, "init_C local dims");
+        upload(h, src, doC, diC, bz, G);
+      } else {
+        bz = D.b;
+        G.resize(L);
+        for (int l = 0; l < L; ++l) {
+          const long long n = prodll({bz[l], D.du[l], D.dt[l], bz[l + 1]});
+          G[l] = h->pool.alloc<double>(n);
+          CK(cudaMemcpyAsync(G[l], h->B64[l], sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+        }
+        if (D.du != D.ds) throw TTError(TT_ERR_SHAPE_MISMATCH, "TT_INIT_COPY_B needs A.d_out == B.d_out");
+      }
+      qr_sweep(h, G, bz, D.ds, D.dt);
+      rq_sweep(h, G, bz, D.ds, D.dt, 1);
+      for (int l = 1; l < L; ++l) D.cb[l] = std::max(D.cb[l], bz[l]);
+      C0 = G;
+      cbond = bz;
+    }
+    D.c = cbond;
+    h->pool.release(h->fX);
+    h->pool.release(h->fQ);
+    h->pool.release(h->fR);
+    h->pool.release(h->gws);
+    if (h->use_f32) setup<float>(h, C0);
+    else setup<double>(h, C0);
+    for (int j = 0; j < L; ++j) h->pool.release(C0[j]);
+    CK(cudaStreamSynchronize(h->st));
+    *out = h;
+    return TT_OK;
+  } catch (const TTError& e) {
+    g_create_error = std::string("tt_fit_create: ") + e.what();
+    if (h) {
+      cudaGetLastError();
+      if (h->hk) cudaFreeHost(h->hk);
+      if (h->hdinfo) cudaFreeHost(h->hdinfo);
+      if (h->herrw) cudaFreeHost(h->herrw);
+      for (auto e : h->ev)
+        if (e) cudaEventDestroy(e);
+      delete h;
+    }
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    delete h;
+    return TT_ERR_OUT_OF_MEMORY;
+  } catch (...) {
+    delete h;
+    return TT_ERR_CUDA;
+  }
+}
+
+tt_status tt_fit_sweep(tt_fit* h, int n_sweeps, tt_sweep_report* rep) {
+  if (!h || n_sweeps < 0) return TT_ERR_INVALID_ARGUMENT;
+  if (h->poisoned) return TT_ERR_STATE;
+  auto t0 = std::chrono::steady_clock::now();
+  try {
+    for (double& s : h->stage_ms) s = 0;
+    h->flops = 0;
+    h->launches = 0;
+    if (h->use_f32) {
+      Sweeper<float> sw(h);
+      sw.run(n_sweeps);
+    } else {
+      Sweeper<double> sw(h);
+      sw.run(n_sweeps);
+    }
+    CK(cudaStreamSynchronize(h->st));
+    h->have_times = true;
+  } catch (const TTError& e) {
+    poison(h, e);
+    return e.code;
+  } catch (...) {
+    h->poisoned = true;
+    h->last_error = "unexpected exception";
+    return TT_ERR_CUDA;
+  }
+  if (rep) {
+    rep->sweeps_done = h->sweeps_done;
+    rep->converged = h->converged ? 1 : 0;
+    rep->delta = h->delta;
+    rep->norm2_C = h->last_n2;
+    rep->max_discarded = h->max_disc;
+    rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return TT_OK;
+}
+
+tt_status tt_fit_result(const tt_fit* hc, tt_mpo_desc* C, double* lambdas) {
+  tt_fit* h = const_cast<tt_fit*>(hc);
+  if (!h || !C) return TT_ERR_INVALID_ARGUMENT;
+  if (h->poisoned) return TT_ERR_STATE;
+  const Dims& D = h->D;
+  const int L = D.L;
+  C->L = L;
+  if (!C->d_out || !C->d_in || !C->bond) return TT_ERR_INVALID_ARGUMENT;
+  int* dout = const_cast<int*>(C->d_out);
+  int* din = const_cast<int*>(C->d_in);
+  int* bond = const_cast<int*>(C->bond);
+  for (int l = 0; l < L; ++l) {
+    dout[l] = D.ds[l];
+    din[l] = D.dt[l];
+  }
+  for (int l = 0; l <= L; ++l) bond[l] = D.c[l];
+  try {
+    if (lambdas) {
+      size_t off = 0;
+      for (int l = 1; l < L; ++l) {
+        const std::vector<double>& v = h->lam[l];
+        for (int j = 0; j < D.c[l]; ++j) lambdas[off + j] = (j < (int)v.size()) ? v[j] : 0.0;
+        off += D.c[l];
+      }
+    }
+    if (!C->cores) return TT_OK;
+    if (C->dtype != TT_DTYPE_F64 && C->dtype != TT_DTYPE_F32) return TT_ERR_INVALID_ARGUMENT;
+    for (int l = 0; l < L; ++l) {
+      if (!C->cores[l]) return TT_ERR_INVALID_ARGUMENT;
+      const int rows = D.c[l] * D.ds[l] * D.dt[l], cols = D.c[l + 1];
+      // C_l = Psi_l Y_l for l < L (inverse gauge); Y = 1 in the site gauge
+      const bool scale = (h->gauge == TT_GAUGE_INVERSE_CANONICAL) && (l < L - 1);
+      double* tmp = h->pool.alloc<double>((size_t)rows * cols);
+      CK(scale_cols(rows, cols, h->C64[l], scale ? h->Y[l + 1] : nullptr, tmp, h->st));
+      if (C->dtype == TT_DTYPE_F64)
+        CK(cudaMemcpyAsync(C->cores[l], tmp, sizeof(double) * (size_t)rows * cols, cudaMemcpyDeviceToDevice, h->st));
+      else
+        CK(copy_map<double, float>(1, rows * cols, tmp, IdxMap::lin(0), IdxMap::lin(1), (float*)C->cores[l],
+                                   IdxMap::lin(0), IdxMap::lin(1), 1.0, h->st));
+      CK(cudaStreamSynchronize(h->st));
+      h->pool.release(tmp);
+    }
+  } catch (const TTError& e) {
+    poison(h, e);
+    return e.code;
+  }
+  return TT_OK;
+}
+
+tt_status tt_fit_stage_times(const tt_fit* h, double out[7]) {
+  if (!h || !out) return TT_ERR_INVALID_ARGUMENT;
+  if (!h->have_times) return TT_ERR_STATE;
+  for (int i = 0; i < 5; ++i) out[i] = h->stage_ms[i];
+  out[5] = h->flops;
+  out[6] = (double)h->launches;
+  return TT_OK;
+}
+
+void tt_fit_destroy(tt_fit* h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st);
+  else cudaDeviceSynchronize();
+  for (auto e : h->ev)
+    if (e) cudaEventDestroy(e);
+  if (h->hk) cudaFreeHost(h->hk);
+  if (h->hdinfo) cudaFreeHost(h->hdinfo);
+  if (h->herrw) cudaFreeHost(h->herrw);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,345 @@
+// Tensor-core contraction kernel for sm_103a (5th-generation tensor cores).
+//
+//   C[cm(m) + cn(n)] = alpha * sum_k A[m*lda + k] * B(n, k) + beta * C[...]
+//
+// A is K-major (k contiguous, rows at stride lda); B is K-major (rows n at
+// stride ldb, k contiguous) or MN-major (rows k at stride ldb, n contiguous).
+// Operand tiles are moved global -> shared memory by TMA (128-byte swizzle),
+// one elected thread issues tcgen05.mma (kind::tf32, FP32 accumulation in
+// tensor memory), and four warps drain the 128 x 128 accumulator with
+// tcgen05.ld into the output layout given by two index maps (any tensor
+// permutation of the fit's contraction chain). Split-K partial sums go to a
+// dense FP32 workspace and are reduced by splitk_reduce_kernel.
+//
+// Every mbarrier wait is bounded; on expiry the kernel sets ERRW_TIMEOUT in
+// the device error word, stops issuing work, frees its tensor memory and
+// returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ttfit {
+
+namespace tc {
+
+constexpr int BM = 128, BN = 128, BK = 32;  // BK fp32 elements = 128 bytes = one swizzle span
+constexpr int STAGES = 4;
+constexpr int TILE_BYTES = BM * BK * 4;     // 16 KB (A); B tile has the same size
+constexpr int SMEM_BYTES = STAGES * 2 * TILE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr long long WAIT_LIMIT = 1ll << 26;
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (long long i = 0; i < WAIT_LIMIT; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+// shared-memory matrix descriptor, 128-byte swizzle (layout type 2), version 1
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46) | (2ull << 61);
+}
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// instruction descriptor: D = F32 (bits 4-5 = 1), A = B = TF32 (format 2 at bits 7-9 and 10-12),
+// A K-major (bit 15 = 0), B major per template (bit 16), N >> 3 at bits 17-22, M >> 4 at bits 24-28
+__host__ __device__ constexpr uint32_t idesc_tf32(int m, int n, bool b_mn_major) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((b_mn_major ? 1u : 0u) << 16) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
+}
+
+template <bool B_MN>
+__global__ void __launch_bounds__(128, 1)
+    gemm_tf32_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
+                     int K, int k_per_split, float* __restrict__ C, IdxMap cm, IdxMap cn, float alpha, float beta,
+                     float* __restrict__ ws, uint32_t* errw) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * TILE_BYTES;
+  uint64_t* bars = (uint64_t*)(smem + STAGES * 2 * TILE_BYTES);
+  // bars[0..S-1] full, bars[S..2S-1] empty, bars[2S] accumulator ready
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int kb0 = blockIdx.z * k_per_split;
+  const int kend = min(K, kb0 + k_per_split);
+  const int nk = (kend - kb0 + BK - 1) / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(su32(&bars[s]), 1);
+      mbar_init(su32(&bars[STAGES + s]), 1);
+    }
+    mbar_init(su32(&bars[2 * STAGES]), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  int issued = 0;  // stages loaded by the producer (for the bounded drain on abort)
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (kb / STAGES) & 1;
+      if (*abort_flag || !mbar_wait(su32(&bars[STAGES + s]), ph ^ 1)) {
+        *abort_flag = 1;
+        break;
+      }
+      const uint32_t full = su32(&bars[s]);
+      mbar_expect_tx(full, 2 * TILE_BYTES);
+      const int k = kb0 + kb * BK;
+      tma_load_2d(su32(sA + s * TILE_BYTES), &tmA, full, k, m0);
+      if (B_MN) {
+        // four boxes of (32 n) x (BK k): n chunk j at byte offset j * BK * 128
+#pragma unroll
+        for (int j = 0; j < BN / 32; ++j) tma_load_2d(su32(sB + s * TILE_BYTES + j * BK * 128), &tmB, full, n0 + 32 * j, k);
+      } else {
+        tma_load_2d(su32(sB + s * TILE_BYTES), &tmB, full, k, n0);
+      }
+      issued = kb + 1;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    const uint32_t idesc = idesc_tf32(BM, BN, B_MN);
+    bool ok = true;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (kb / STAGES) & 1;
+      if (*abort_flag || !mbar_wait(su32(&bars[s]), ph)) {
+        *abort_flag = 1;
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a_base = su32(sA + s * TILE_BYTES);
+      const uint32_t b_base = su32(sB + s * TILE_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < BK / 8; ++kk) {
+        // K-major: advance 8 tf32 = 32 bytes inside the swizzle span; SBO = 8 rows x 128 B
+        const uint64_t ad = sdesc(a_base + kk * 32, 16, 1024);
+        uint64_t bd;
+        if (B_MN) bd = sdesc(b_base + kk * 1024, BK * 128, 1024);  // 8 k-rows per step; LBO = n-chunk stride
+        else bd = sdesc(b_base + kk * 32, 16, 1024);
+        mma_tf32(tmem, ad, bd, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+      }
+      mma_commit(su32(&bars[STAGES + s]));  // frees the stage once these MMAs have read it
+    }
+    if (ok) mma_commit(su32(&bars[2 * STAGES]));
+  }
+  __syncwarp();
+  // ---------------- epilogue: all four warps, warp w owns accumulator rows 32w..32w+31
+  bool have = false;
+  if (nk > 0) have = mbar_wait(su32(&bars[2 * STAGES]), 0) && !*abort_flag;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (have) {
+    const int m = m0 + warp * 32 + lane;
+    const long long crow = (m < M) ? cm(m) : 0;
+    float* wrow = ws ? ws + (size_t)blockIdx.z * M * N + (size_t)m * N : nullptr;
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 32) {
+      uint32_t r[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c, r);
+      if (m < M) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = n0 + c + j;
+          if (n < N) {
+            const float v = __uint_as_float(r[j]);
+            if (ws) {
+              wrow[n] = v;
+            } else {
+              const long long o = crow + cn(n);
+              float out = alpha * v;
+              if (beta != 0.f) out += beta * C[o];
+              C[o] = out;
+            }
+          }
+        }
+      }
+    }
+  } else if (nk > 0 && threadIdx.x == 0 && errw) {
+    atomicOr(errw, ERRW_TIMEOUT);
+  }
+  if (nk == 0 && ws == nullptr) {  // empty K range: C = beta * C
+    const int m = m0 + warp * 32 + lane;
+    if (m < M)
+      for (int j = 0; j < BN; ++j) {
+        const int n = n0 + j;
+        if (n < N) {
+          const long long o = cm(m) + cn(n);
+          C[o] = beta != 0.f ? beta * C[o] : 0.f;
+        }
+      }
+  } else if (nk == 0 && ws) {
+    const int m = m0 + warp * 32 + lane;
+    if (m < M)
+      for (int j = 0; j < BN; ++j)
+        if (n0 + j < N) ws[(size_t)blockIdx.z * M * N + (size_t)m * N + n0 + j] = 0.f;
+  }
+  // drain any TMA still in flight after an abort (bounded), then free tensor memory
+  if (warp == 0 && lane == 0 && *abort_flag) {
+    for (int kb = 0; kb < issued; ++kb) mbar_wait(su32(&bars[kb % STAGES]), (kb / STAGES) & 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap* map, const float* ptr, uint64_t inner, uint64_t outer, uint64_t row_stride_elems,
+              uint32_t box_inner, uint32_t box_outer) {
+  auto enc = encoder();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {row_stride_elems * 4};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)ptr, dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+inline bool lin_stride(const IdxMap& m, long long& s) {
+  if (m.n1 == 1 && m.n2 == (1 << 30) && m.s0 == 0 && m.s1 == 0) {
+    s = m.s2;
+    return true;
+  }
+  return false;
+}
+
+}  // namespace tc
+
+// Returns cudaErrorNotSupported when the operand layouts cannot be fed by TMA
+// (the caller then uses the CUDA-core kernel).
+cudaError_t gemm_tf32(const GemmArgs<float>& g, float* ws, size_t ws_elems, int sm_count, uint32_t* errw,
+                      cudaStream_t st) {
+  using namespace tc;
+  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+  long long lda, ldb, one;
+  if (!lin_stride(g.am, lda) || !lin_stride(g.ak, one) || one != 1) return cudaErrorNotSupported;
+  bool b_mn;
+  if (lin_stride(g.bk, one) && one == 1 && lin_stride(g.bn, ldb)) b_mn = false;
+  else if (lin_stride(g.bn, one) && one == 1 && lin_stride(g.bk, ldb)) b_mn = true;
+  else return cudaErrorNotSupported;
+  // TMA: 16-byte aligned bases and row strides
+  if (((uintptr_t)g.A & 15) || ((uintptr_t)g.B & 15) || (lda * 4) % 16 || (ldb * 4) % 16) return cudaErrorNotSupported;
+  if (lda < g.K || (!b_mn && ldb < g.K) || (b_mn && ldb < g.N)) return cudaErrorNotSupported;
+  if (g.K < 1) return cudaErrorNotSupported;
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, g.A, (uint64_t)g.K, (uint64_t)g.M, (uint64_t)lda, BK, BM)) return cudaErrorNotSupported;
+  if (!b_mn) {
+    if (!make_map(&tb, g.B, (uint64_t)g.K, (uint64_t)g.N, (uint64_t)ldb, BK, BN)) return cudaErrorNotSupported;
+  } else {
+    if (!make_map(&tb, g.B, (uint64_t)g.N, (uint64_t)g.K, (uint64_t)ldb, 32, BK)) return cudaErrorNotSupported;
+  }
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[b_mn]) {
+    cudaError_t e = b_mn ? cudaFuncSetAttribute(gemm_tf32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                SMEM_BYTES)
+                         : cudaFuncSetAttribute(gemm_tf32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr_set[b_mn] = true;
+  }
+  const int gm = (g.M + BM - 1) / BM, gn = (g.N + BN - 1) / BN;
+  int splits = 1;
+  while (gm * gn * splits < sm_count && g.K / (splits * 2) >= 4 * BK && (size_t)(splits * 2) * g.M * g.N <= ws_elems)
+    splits *= 2;
+  int kps = (g.K + splits - 1) / splits;
+  kps = (kps + BK - 1) / BK * BK;
+  splits = (g.K + kps - 1) / kps;
+  dim3 grid(gn, gm, splits);
+  float* wsp = splits > 1 ? ws : nullptr;
+  if (b_mn)
+    gemm_tf32_kernel<true><<<grid, 128, SMEM_BYTES, st>>>(ta, tb, g.M, g.N, g.K, kps, g.C, g.cm, g.cn, g.alpha,
+                                                           g.beta, wsp, errw);
+  else
+    gemm_tf32_kernel<false><<<grid, 128, SMEM_BYTES, st>>>(ta, tb, g.M, g.N, g.K, kps, g.C, g.cm, g.cn, g.alpha,
+                                                            g.beta, wsp, errw);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || splits == 1) return e;
+  return splitk_reduce<float>(g, ws, splits, sm_count, st);
+}
+
+}  // namespace ttfit

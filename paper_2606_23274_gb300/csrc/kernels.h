@@ -1,0 +1,83 @@
+// Internal launchers of the fit library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include "common.cuh"
+
+namespace ttfit {
+
+template <typename T>
+struct GemmArgs {
+  int M = 0, N = 0, K = 0;
+  const T* A = nullptr;
+  IdxMap am, ak;
+  bool a_kfast = true;  // consecutive k are adjacent in memory (load k-fastest)
+  const T* B = nullptr;
+  IdxMap bn, bk;
+  bool b_kfast = true;
+  T* C = nullptr;
+  IdxMap cm, cn;
+  T alpha = T(1), beta = T(0);
+};
+
+template <typename T>
+cudaError_t gemm_simt(const GemmArgs<T>& g, T* ws, size_t ws_elems, int sm_count, cudaStream_t st);
+
+// C = alpha * sum over `splits` dense [M][N] partials in ws + beta * C (output maps of g)
+template <typename T>
+cudaError_t splitk_reduce(const GemmArgs<T>& g, const T* ws, int splits, int sm_count, cudaStream_t st);
+
+// Tensor-core (tcgen05, kind::tf32) GEMM; cudaErrorNotSupported when the operand
+// layouts cannot be loaded by TMA (A K-major; B K-major or MN-major; 16-byte rows).
+cudaError_t gemm_tf32(const GemmArgs<float>& g, float* ws, size_t ws_elems, int sm_count, uint32_t* errw,
+                      cudaStream_t st);
+
+// out[om(i) + on(j)] = (Tout) (scale * in[im(i) + in_(j)]), i < rows, j < cols
+template <typename Tin, typename Tout>
+cudaError_t copy_map(int rows, int cols, const Tin* in, IdxMap im, IdxMap in_, Tout* out, IdxMap om, IdxMap on,
+                     double scale, cudaStream_t st);
+
+// fill out[i] = scale * N(0,1)_philox(seed, stream, i), i < count
+cudaError_t philox_fill(double* out, long long count, uint64_t seed, uint64_t stream, double scale, cudaStream_t st);
+
+// Householder QR of the q x p column-major matrix X (ld q; overwritten):
+// Q is q x r (col-major, ld q), R is r x p (col-major, ld r), r = min(q, p),
+// diag(R) >= 0. One CTA.
+template <typename C>
+cudaError_t qr_householder(int q, int p, double* X, double* Q, double* R, cudaStream_t st);
+
+// One-sided Jacobi SVD of the q x p column-major W (q >= p, ld q; overwritten):
+// W = U diag(S) V^T with U (q x p, col-major), S sorted descending, V (p x p,
+// col-major). C is the arithmetic type of the rotations. errw |= ERRW_NOCONV
+// when max_sweeps is reached.
+template <typename C>
+cudaError_t jacobi_svd(int q, int p, double* W, double* U, double* S, double* V, double* Vwork,
+                       int max_sweeps, uint32_t* errw, cudaStream_t st);
+
+// ||X||_F of n values (type T) into *out (double), flags non-finite values.
+template <typename T>
+cudaError_t frob_norm(const T* x, long long n, double* out, uint32_t* errw, cudaStream_t st);
+
+// Truncation rule (Sec. 2.3.4): from sorted S (p values), ||M||_F, writes
+// info[0] = k, and dinfo[0] = sum_{j<k} s_j^2, dinfo[1] = sqrt(sum_{j>=k} s_j^2)/||M||_F.
+cudaError_t truncate_rule(const double* S, int p, const double* normM, double tau_over_L, int chi_max,
+                          double cutoff, int* info, double* dinfo, cudaStream_t st);
+
+// Gauge update after the factorisation of the m x n two-site matrix
+// (U: m x ld_u col-major, S, V: n x ld_v col-major; k from *kdev):
+// mode 0 = site forward (C_l = U, C_{l+1} = S V^T), 1 = site backward
+// (C_l = U S, C_{l+1} = V^T), 2 = inverse (Psi_l = U S, Psi_{l+1} = S V^T,
+// Y_l = 1/S). Writes Cl (m x k row-major), Cr (k x n row-major), Y (k) and
+// the environment operands Ut (k x m row-major) and Vt (k x n row-major) in T.
+template <typename T>
+cudaError_t gauge_update(int mode, int m, int n, const double* U, int ld_u, const double* S, const double* V, int ld_v,
+                         const int* kdev, double* Cl, double* Cr, double* Y, T* Ut, T* Vt, cudaStream_t st);
+
+// Flip singular pairs j < p so that the largest-magnitude entry of U[:, j] is
+// positive (U: m x p col-major ld_u; V: n x p col-major ld_v).
+cudaError_t fix_signs(int m, int n, int p, double* U, int ld_u, double* V, int ld_v, cudaStream_t st);
+
+// out (rows x cols, row-major) = in * diag(y) (y == nullptr: plain copy)
+cudaError_t scale_cols(int rows, int cols, const double* in, const double* y, double* out, cudaStream_t st);
+
+}  // namespace ttfit

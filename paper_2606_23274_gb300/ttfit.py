@@ -1,0 +1,243 @@
+"""Python binding of the C ABI in include/ttfit.h (argument marshalling only).
+
+Every step of a sweep runs in libttfit.so's CUDA kernels; this module only
+builds the descriptor structs from torch tensors, passes device pointers and
+the current CUDA stream, and checks return codes. Importing it on a machine
+without the built library raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+from typing import Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libttfit.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "ttfit.h")
+
+TT_OK, TT_ERR_INVALID_ARGUMENT, TT_ERR_SHAPE_MISMATCH, TT_ERR_OUT_OF_MEMORY = 0, 1, 2, 3
+TT_ERR_CUDA, TT_ERR_NUMERICAL, TT_ERR_TIMEOUT, TT_ERR_STATE = 4, 5, 6, 7
+GAUGE = {"site": 0, "inverse": 1}
+UPDATE = {"svd": 0, "rsvd": 1}
+PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16_split": 3}
+INIT = {"random": 0, "copy_b": 1, "given": 2}
+TT_FAULT_ALLOC_FAIL, TT_FAULT_NAN_INPUT, TT_FAULT_SVD_NOCONV = 0x1, 0x2, 0x4
+DTYPE_F64, DTYPE_F32 = 0, 1
+
+
+class tt_mpo_desc(ct.Structure):
+    _fields_ = [("L", ct.c_int), ("d_out", ct.POINTER(ct.c_int)), ("d_in", ct.POINTER(ct.c_int)),
+                ("bond", ct.POINTER(ct.c_int)), ("cores", ct.POINTER(ct.c_void_p)), ("dtype", ct.c_int)]
+
+
+class tt_fit_options(ct.Structure):
+    _fields_ = [("struct_size", ct.c_size_t), ("update", ct.c_int), ("oversample", ct.c_int),
+                ("seed", ct.c_uint64), ("precision", ct.c_int), ("init", ct.c_int),
+                ("init_C", ct.POINTER(tt_mpo_desc)), ("sv_cutoff", ct.c_double), ("conv_tol", ct.c_double),
+                ("stream", ct.c_void_p), ("prepare_inputs", ct.c_int), ("fault_inject", ct.c_uint32)]
+
+
+class tt_sweep_report(ct.Structure):
+    _fields_ = [("sweeps_done", ct.c_int), ("converged", ct.c_int), ("delta", ct.c_double),
+                ("norm2_C", ct.c_double), ("max_discarded", ct.c_double), ("seconds", ct.c_double)]
+
+
+class TTError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+_lib = None
+
+
+def load():
+    """Load libttfit.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() first (no CPU fallback)")
+        lib = ct.CDLL(LIB_PATH)
+        lib.tt_fit_create.argtypes = [ct.POINTER(tt_mpo_desc), ct.POINTER(tt_mpo_desc), ct.c_int, ct.c_double,
+                                      ct.c_int, ct.POINTER(tt_fit_options), ct.POINTER(ct.c_void_p)]
+        lib.tt_fit_create.restype = ct.c_int
+        lib.tt_fit_sweep.argtypes = [ct.c_void_p, ct.c_int, ct.POINTER(tt_sweep_report)]
+        lib.tt_fit_sweep.restype = ct.c_int
+        lib.tt_fit_result.argtypes = [ct.c_void_p, ct.POINTER(tt_mpo_desc), ct.POINTER(ct.c_double)]
+        lib.tt_fit_result.restype = ct.c_int
+        lib.tt_fit_destroy.argtypes = [ct.c_void_p]
+        lib.tt_fit_destroy.restype = None
+        lib.tt_status_string.argtypes = [ct.c_int]
+        lib.tt_status_string.restype = ct.c_char_p
+        lib.tt_fit_last_error.argtypes = [ct.c_void_p]
+        lib.tt_fit_last_error.restype = ct.c_char_p
+        lib.tt_fit_stage_times.argtypes = [ct.c_void_p, ct.POINTER(ct.c_double)]
+        lib.tt_fit_stage_times.restype = ct.c_int
+        _lib = lib
+    return _lib
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/ttfit.h."""
+    import re
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:tt_status|void|const char\*)\s+(tt_\w+)\s*\(", txt, re.M)))
+
+
+class _Desc:
+    """Keeps the ctypes arrays of one tt_mpo_desc alive."""
+
+    def __init__(self, cores, dtype_code=None):
+        import torch
+        L = len(cores)
+        shapes = [tuple(c.shape) for c in cores]
+        self.d_out = (ct.c_int * L)(*[s[1] for s in shapes])
+        self.d_in = (ct.c_int * L)(*[s[2] for s in shapes])
+        self.bond = (ct.c_int * (L + 1))(*([s[0] for s in shapes] + [shapes[-1][3]]))
+        self.tensors = [c.contiguous() for c in cores]
+        if dtype_code is None:
+            dtype_code = DTYPE_F64 if self.tensors[0].dtype == torch.float64 else DTYPE_F32
+        self.ptrs = (ct.c_void_p * L)(*[t.data_ptr() for t in self.tensors])
+        self.desc = tt_mpo_desc(L, self.d_out, self.d_in, self.bond, self.ptrs, dtype_code)
+
+
+def _as_device(cores, device):
+    import torch
+    out = []
+    for c in cores:
+        if isinstance(c, np.ndarray):
+            c = torch.from_numpy(np.ascontiguousarray(c))
+        out.append(c.to(device=device))
+    return out
+
+
+def _check(code, h=None, what=""):
+    if code != TT_OK:
+        lib = load()
+        msg = lib.tt_status_string(code).decode()
+        detail = lib.tt_fit_last_error(h if (h is not None and h.value) else None).decode()
+        if detail and detail != "NULL handle":
+            msg += ": " + detail
+        raise TTError(code, f"{what}: {msg}")
+
+
+def tt_fit_create(A: Sequence, B: Sequence, chi_max: int, tol: float, gauge="site", *, update="svd",
+                  oversample=10, seed=0, precision="fp64", init="random", init_C=None, sv_cutoff=-1.0,
+                  conv_tol=-1.0, stream=None, prepare_inputs=True, fault_inject=0, device="cuda"):
+    """Create a fit handle (see tt_fit_create in include/ttfit.h). A, B: lists of
+    (chi_l, d, d', chi_r) tensors (torch CUDA tensors, or host arrays that are copied)."""
+    import torch
+    lib = load()
+    dA = _Desc(_as_device(A, device))
+    dB = _Desc(_as_device(B, device))
+    o = tt_fit_options()
+    o.struct_size = ct.sizeof(tt_fit_options)
+    o.update = UPDATE[update] if isinstance(update, str) else int(update)
+    o.oversample = int(oversample)
+    o.seed = int(seed)
+    o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    o.init = INIT[init] if isinstance(init, str) else int(init)
+    dC = None
+    if init_C is not None:
+        dC = _Desc(_as_device(init_C, device))
+        o.init_C = ct.pointer(dC.desc)
+    o.sv_cutoff = float(sv_cutoff)
+    o.conv_tol = float(conv_tol)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    o.stream = ct.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    o.prepare_inputs = 1 if prepare_inputs else 0
+    o.fault_inject = int(fault_inject)
+    h = ct.c_void_p()
+    g = GAUGE[gauge] if isinstance(gauge, str) else int(gauge)
+    code = lib.tt_fit_create(ct.byref(dA.desc), ct.byref(dB.desc), int(chi_max), float(tol), g, ct.byref(o),
+                             ct.byref(h))
+    _check(code, None, "tt_fit_create")
+    return Fit(h, device, len(A))
+
+
+def tt_fit_sweep(fit: "Fit", n_sweeps: int):
+    return fit.sweep(n_sweeps)
+
+
+def tt_fit_result(fit: "Fit", dtype=None):
+    return fit.result(dtype)
+
+
+def tt_fit_destroy(fit: "Fit"):
+    fit.destroy()
+
+
+class Fit:
+    """Owner of a tt_fit handle."""
+
+    def __init__(self, handle: ct.c_void_p, device, L: int):
+        self.h = handle
+        self.device = device
+        self.L = L
+
+    def sweep(self, n_sweeps: int = 1) -> dict:
+        rep = tt_sweep_report()
+        _check(load().tt_fit_sweep(self.h, int(n_sweeps), ct.byref(rep)), self.h, "tt_fit_sweep")
+        return {k: getattr(rep, k) for k, _ in tt_sweep_report._fields_}
+
+    def bonds(self) -> list[int]:
+        L = self.L
+        d_out = (ct.c_int * L)()
+        d_in = (ct.c_int * L)()
+        bond = (ct.c_int * (L + 1))()
+        desc = tt_mpo_desc(L, d_out, d_in, bond, None, DTYPE_F64)
+        _check(load().tt_fit_result(self.h, ct.byref(desc), None), self.h, "tt_fit_result")
+        self._dims = (list(d_out), list(d_in), list(bond))
+        return list(bond)
+
+    def result(self, dtype=None):
+        """C as a list of device tensors (chi_l, d, d', chi_r)."""
+        import torch
+        dtype = dtype or torch.float64
+        bond = self.bonds()
+        d_out, d_in, _ = self._dims
+        L = len(d_out)
+        cores = [torch.empty((bond[l], d_out[l], d_in[l], bond[l + 1]), dtype=dtype, device=self.device)
+                 for l in range(L)]
+        ptrs = (ct.c_void_p * L)(*[c.data_ptr() for c in cores])
+        desc = tt_mpo_desc(L, (ct.c_int * L)(*d_out), (ct.c_int * L)(*d_in), (ct.c_int * (L + 1))(*bond), ptrs,
+                           DTYPE_F64 if dtype == torch.float64 else DTYPE_F32)
+        _check(load().tt_fit_result(self.h, ct.byref(desc), None), self.h, "tt_fit_result")
+        torch.cuda.current_stream().synchronize()
+        return cores
+
+    def lambdas(self) -> list[np.ndarray]:
+        bond = self.bonds()
+        n = sum(bond[1:-1])
+        buf = (ct.c_double * max(n, 1))()
+        d_out, d_in, _ = self._dims
+        L = len(d_out)
+        desc = tt_mpo_desc(L, (ct.c_int * L)(*d_out), (ct.c_int * L)(*d_in), (ct.c_int * (L + 1))(*bond), None,
+                           DTYPE_F64)
+        _check(load().tt_fit_result(self.h, ct.byref(desc), buf), self.h, "tt_fit_result")
+        out, off = [], 0
+        for b in bond[1:-1]:
+            out.append(np.array(buf[off:off + b]))
+            off += b
+        return out
+
+    def stage_times(self) -> dict:
+        v = (ct.c_double * 7)()
+        _check(load().tt_fit_stage_times(self.h, v), self.h, "tt_fit_stage_times")
+        keys = ["halves_ms", "join_ms", "env_finish_ms", "factorize_ms", "gauge_ms", "contraction_flops",
+                "launches"]
+        return dict(zip(keys, list(v)))
+
+    def destroy(self):
+        if self.h is not None and self.h.value:
+            load().tt_fit_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

@@ -1,0 +1,175 @@
+"""Parity of the CUDA fit (through the C ABI) with the FP64 oracle on the same
+seeded inputs. Results are compared as operators (the stable difference norm of
+the oracle) plus per-bond dimensions and the convergence history; raw cores are
+gauge-dependent (singular-vector signs) and are not compared."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.fit import FitOracle
+from oracle.mpo import bonds, mpo_diff_norm, mpo_norm, to_dense
+from paper_2606_23274_gb300.synth import gaussian_mpo, kron_sum_mpo, mpo_pair
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2606_23274_gb300 import ttfit  # noqa: E402
+
+
+def _gpu_fit(A, B, chi, tol, sweeps, **kw):
+    f = ttfit.tt_fit_create(A, B, chi, tol, kw.pop("gauge", "site"), **kw)
+    reps = [f.sweep(1) for _ in range(sweeps)]
+    C = [c.cpu().numpy() for c in f.result()]
+    lam = f.lambdas()
+    b = f.bonds()
+    f.destroy()
+    return C, reps, b, lam
+
+
+def _rel(X, Y):
+    return mpo_diff_norm(X, Y) / mpo_norm(Y)
+
+
+@pytest.mark.parametrize("gauge", ["site", "inverse"])
+def test_exact_product_fp64(gauge):
+    """chi_C = chi_A chi_B = 64 reproduces A B (dense 256 x 256 check)."""
+    A, B = mpo_pair("gauss_L8_chi8", 0)
+    C, reps, b, _ = _gpu_fit(A, B, 64, 0.0, 2, gauge=gauge, precision="fp64")
+    D = to_dense(A) @ to_dense(B)
+    assert np.linalg.norm(to_dense(C) - D) <= 1e-10 * np.linalg.norm(D)
+    assert b == [1, 4, 16, 64, 64, 64, 16, 4, 1]
+
+
+@pytest.mark.parametrize("gauge", ["site", "inverse"])
+@pytest.mark.parametrize("update", ["svd", "rsvd"])
+def test_truncated_fit_fp64_matches_oracle(gauge, update):
+    A, B = mpo_pair("kron_L12_chi32", 1)
+    chi, sweeps = 12, 4
+    f = FitOracle(A, B, chi, 0.0, gauge=gauge, update=update, oversample=4, seed=3)
+    f.sweep(sweeps, stop_on_converge=False)
+    Co = f.result()
+    C, reps, b, lam = _gpu_fit(A, B, chi, 0.0, sweeps, gauge=gauge, update=update, oversample=4, seed=3,
+                               precision="fp64", conv_tol=0.0)
+    assert b == f.bonds()
+    assert _rel(C, Co) <= 1e-9
+    for r, h in zip(reps, f.st.history):
+        assert abs(r["norm2_C"] - h.norm2) <= 1e-11 * h.norm2
+    for got, ref in zip(lam, f.lambdas()):
+        assert np.allclose(got, ref, rtol=1e-9, atol=1e-12 * ref[0])
+
+
+def test_fp32_contractions_match_oracle():
+    A, B = mpo_pair("kron_L10_chi16", 2)
+    f = FitOracle(A, B, 10, 0.0, seed=1, sv_cutoff=1e-6)
+    f.sweep(4, stop_on_converge=False)
+    C, reps, b, _ = _gpu_fit(A, B, 10, 0.0, 4, precision="fp32", seed=1, conv_tol=0.0)
+    assert b == f.bonds()
+    assert _rel(C, f.result()) <= 2e-5
+
+
+def test_init_given_and_copy_b():
+    A, B = mpo_pair("kron_L10_chi16", 4)
+    C0 = gaussian_mpo(10, 2, 5, seed=77, which=3)
+    for init, kw in (("given", dict(init_C=C0)), ("copy_b", {})):
+        f = FitOracle(A, B, 8, 0.0, init=init, **kw)
+        f.sweep(3, stop_on_converge=False)
+        C, reps, b, _ = _gpu_fit(A, B, 8, 0.0, 3, init=init, precision="fp64", conv_tol=0.0, **kw)
+        assert b == f.bonds()
+        assert _rel(C, f.result()) <= 1e-9
+
+
+def test_edge_cases_small_chains_and_ragged_dims():
+    """L = 2 (a single window), chi_max = 1, local dims 3 x 2 and ragged bonds."""
+    rng = np.random.default_rng(5)
+    # L = 2
+    A, B = mpo_pair("gauss_L8_chi8", 1, L=2)
+    C, _, b, _ = _gpu_fit(A, B, 64, 0.0, 1, precision="fp64")
+    D = to_dense(A) @ to_dense(B)
+    assert np.linalg.norm(to_dense(C) - D) <= 1e-12 * np.linalg.norm(D)
+    # chi_max = 1
+    A, B = mpo_pair("kron_L10_chi16", 0)
+    f = FitOracle(A, B, 1, 0.0)
+    f.sweep(2, stop_on_converge=False)
+    C, _, b, _ = _gpu_fit(A, B, 1, 0.0, 2, precision="fp64", conv_tol=0.0)
+    assert b == [1] * 11
+    assert _rel(C, f.result()) <= 1e-9
+    # non-uniform local dims: A (chi, 3, 2, chi), B (chi, 2, 3, chi) -> C has 3 x 3 legs
+    L = 5
+    bA = [1, 3, 5, 4, 2, 1]
+    bB = [1, 2, 4, 5, 3, 1]
+    A = [rng.standard_normal((bA[l], 3, 2, bA[l + 1])) for l in range(L)]
+    B = [rng.standard_normal((bB[l], 2, 3, bB[l + 1])) for l in range(L)]
+    f = FitOracle(A, B, 6, 0.0)
+    f.sweep(3, stop_on_converge=False)
+    C, _, b, _ = _gpu_fit(A, B, 6, 0.0, 3, precision="fp64", conv_tol=0.0)
+    assert b == f.bonds()
+    assert _rel(C, f.result()) <= 1e-9
+
+
+def test_tolerance_truncation_rule():
+    """tau > 0 discards by the tau/L rule (Sec. 2.3.4) identically on both sides."""
+    A, B = mpo_pair("kron_L12_chi32", 2)
+    tau = 0.3
+    f = FitOracle(A, B, 40, tau)
+    f.sweep(3, stop_on_converge=False)
+    C, _, b, _ = _gpu_fit(A, B, 40, tau, 3, precision="fp64", conv_tol=0.0)
+    assert b == f.bonds()
+    assert max(b) < 40
+    assert _rel(C, f.result()) <= 1e-8
+
+
+def test_convergence_stops_sweeps():
+    A, B = mpo_pair("gauss_L8_chi8", 2)
+    f = ttfit.tt_fit_create(A, B, 64, 1e-10, "site", precision="fp64")
+    r = f.sweep(10)
+    assert r["converged"] == 1 and r["sweeps_done"] < 10
+    assert r["delta"] <= 1e-10
+    f.destroy()
+
+
+def test_error_paths_are_reported_and_poison():
+    A, B = mpo_pair("gauss_L8_chi8", 0)
+    # shape mismatch: A's input legs != B's output legs
+    Bbad = [np.zeros((b.shape[0], 3, b.shape[2], b.shape[3])) for b in B]
+    with pytest.raises(ttfit.TTError) as e:
+        ttfit.tt_fit_create(A, Bbad, 8, 0.0)
+    assert e.value.code == ttfit.TT_ERR_SHAPE_MISMATCH
+    with pytest.raises(ttfit.TTError) as e:
+        ttfit.tt_fit_create(A, B[:-1], 8, 0.0)
+    assert e.value.code == ttfit.TT_ERR_SHAPE_MISMATCH
+    with pytest.raises(ttfit.TTError) as e:
+        ttfit.tt_fit_create(A, B, 0, 0.0)
+    assert e.value.code == ttfit.TT_ERR_INVALID_ARGUMENT
+    with pytest.raises(ttfit.TTError) as e:
+        ttfit.tt_fit_create(A, B, 8, 0.0, fault_inject=ttfit.TT_FAULT_ALLOC_FAIL)
+    assert e.value.code == ttfit.TT_ERR_OUT_OF_MEMORY
+    for fault in (ttfit.TT_FAULT_NAN_INPUT, ttfit.TT_FAULT_SVD_NOCONV):
+        f = ttfit.tt_fit_create(A, B, 8, 0.0, fault_inject=fault)
+        with pytest.raises(ttfit.TTError) as e:
+            f.sweep(1)
+        assert e.value.code == ttfit.TT_ERR_NUMERICAL
+        with pytest.raises(ttfit.TTError) as e:
+            f.sweep(1)
+        assert e.value.code == ttfit.TT_ERR_STATE
+        f.destroy()
+    # a healthy handle after the poisoned ones
+    f = ttfit.tt_fit_create(A, B, 8, 0.0)
+    f.sweep(1)
+    f.destroy()
+
+
+def test_float32_inputs_and_outputs():
+    A, B = mpo_pair("gauss_L8_chi8", 3)
+    A32 = [torch.from_numpy(a).float().cuda() for a in A]
+    B32 = [torch.from_numpy(b).float().cuda() for b in B]
+    f = ttfit.tt_fit_create(A32, B32, 64, 0.0, "site", precision="fp64")
+    f.sweep(2)
+    C = [c.cpu().double().numpy() for c in f.result(torch.float32)]
+    f.destroy()
+    D = to_dense([a.astype(np.float32).astype(np.float64) for a in A]) @ \
+        to_dense([b.astype(np.float32).astype(np.float64) for b in B])
+    assert np.linalg.norm(to_dense(C) - D) <= 1e-6 * np.linalg.norm(D)
