@@ -96,7 +96,7 @@ struct tt_fit {
   std::vector<double*> C64, Y;
   std::vector<std::vector<double>> lam;  // singular values of the last update per bond
   // contraction tensors in the working type (float or double)
-  std::vector<void*> Aop, Anat, Bl, Br, Lenv, Renv, H1, H2, Ut, Vt;
+  std::vector<void*> Aop, Anat, Bl, Br, Lenv, Renv, H1, H2, H1t, H2t, Ut, Vt;
   void *X1 = nullptr, *Zs = nullptr, *Th = nullptr, *gws = nullptr;
   size_t gws_elems = 0;
   // factorisation workspace (FP64)
@@ -166,8 +166,8 @@ void copymap(tt_fit* h, int rows, int cols, const Tin* in, IdxMap im, IdxMap in_
 }
 
 void qr(tt_fit* h, int q, int p, double* X, double* Q, double* R) {
-  if (h->use_f32) CK(qr_householder<float>(q, p, X, Q, R, h->st));
-  else CK(qr_householder<double>(q, p, X, Q, R, h->st));
+  if (h->use_f32) CK(qr_householder<float, double>(q, p, X, Q, R, h->st));
+  else CK(qr_householder<double, double>(q, p, X, Q, R, h->st));
   h->launches += 1;
 }
 
@@ -306,6 +306,11 @@ struct Chain {
     g2.C = P(h->H1[j]);
     g2.cm = IdxMap::two(a1, (long long)dt * a1 * b1, b1);
     g2.cn = IdxMap::two(b1, (long long)a1 * b1, 1);
+    // transposed copy H1t [a1][b1][c0][s][t] for the environment finish
+    const long long K1 = (long long)c0 * ds * dt;
+    g2.C2 = P(h->H1t[j]);
+    g2.cm2 = IdxMap::two(a1, dt, (long long)b1 * K1);
+    g2.cn2 = IdxMap::two(b1, 1, K1);
     gemm<T>(h, g2, true);
     h->flops += 2.0 * g.M * g.N * g.K + 2.0 * g2.M * g2.N * g2.K;
   }
@@ -342,6 +347,11 @@ struct Chain {
     g2.C = P(h->H2[j]);
     g2.cm = IdxMap::three(ds, c2, b1, (long long)dt * c2 * a1 * b1, (long long)a1 * b1);
     g2.cn = IdxMap::two(dt, 1, (long long)c2 * a1 * b1);
+    // transposed copy H2t [a1][b1][s][t][c2] for the environment finish
+    const long long K2 = (long long)ds * dt * c2;
+    g2.C2 = P(h->H2t[j]);
+    g2.cm2 = IdxMap::three(ds, c2, (long long)b1 * K2, (long long)dt * c2, 1);
+    g2.cn2 = IdxMap::two(dt, K2, c2);
     gemm<T>(h, g2, true);
     h->flops += 2.0 * g.M * g.N * g.K + 2.0 * g2.M * g2.N * g2.K;
   }
@@ -381,10 +391,9 @@ struct Chain {
     g.A = P(h->Ut[j]);
     g.am = IdxMap::lin(K);
     g.ak = IdxMap::lin(1);
-    g.B = P(h->H1[j]);
-    g.bn = IdxMap::lin(1);
-    g.bk = IdxMap::lin((long long)a1 * b1);
-    g.b_kfast = false;
+    g.B = P(h->H1t[j]);
+    g.bn = IdxMap::lin(K);
+    g.bk = IdxMap::lin(1);
     g.C = P(h->Lenv[j + 1]);
     g.cm = IdxMap::lin((long long)a1 * b1);
     g.cn = IdxMap::two(b1, 1, a1);
@@ -404,10 +413,9 @@ struct Chain {
     g.A = P(h->Vt[j]);
     g.am = IdxMap::lin(K);
     g.ak = IdxMap::lin(1);
-    g.B = P(h->H2[j]);
-    g.bn = IdxMap::lin(1);
-    g.bk = IdxMap::lin((long long)a0 * b0);
-    g.b_kfast = false;
+    g.B = P(h->H2t[j]);
+    g.bn = IdxMap::lin(K);
+    g.bk = IdxMap::lin(1);
     g.C = P(h->Renv[j]);
     g.cm = IdxMap::lin((long long)a0 * b0);
     g.cn = IdxMap::two(b0, 1, a0);
@@ -417,90 +425,92 @@ struct Chain {
 };
 
 // ---------------------------------------------------------------------------
-// factorisation of the m x n two-site matrix (Sec. 2.3.4 / Sec. 3.1):
-// result U_M (m x p col-major, ld m), S (p, sorted), V_M (n x p, ld n).
-// Returns p (number of computed singular triplets).
+// factorisation of the m x n two-site matrix (Sec. 2.3.4 / Sec. 3.1) in type F
+// (double on the FP64 path, float otherwise): U_M (m x p col-major, ld m),
+// S (p, sorted), V_M (n x p, ld n). Returns p (computed singular triplets).
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, typename F>
 int factorize(tt_fit* h, int m, int n, int sweep, int site1) {
-  const bool svd32 = h->use_f32;
-  auto jac = [&](int q, int p, double* W, double* U, double* S, double* V) {
-    if (svd32) CK(jacobi_svd<float>(q, p, W, U, S, V, h->fVw, 60, h->errw, h->st));
-    else CK(jacobi_svd<double>(q, p, W, U, S, V, h->fVw, 60, h->errw, h->st));
+  F *fX = (F*)h->fX, *fQ = (F*)h->fQ, *fR = (F*)h->fR, *fU = (F*)h->fU, *fV = (F*)h->fV, *fVw = (F*)h->fVw;
+  F *fS = (F*)h->fS, *fUM = (F*)h->fUM, *fVM = (F*)h->fVM, *fOm = (F*)h->fOm, *MF = (F*)h->fY;
+  F *fBt = (F*)h->fBt, *fQ2 = (F*)h->fQ2, *fR2 = (F*)h->fR2;
+  auto qrf = [&](int q, int p, F* X, F* Q, F* R) {
+    CK(qr_householder<F, F>(q, p, X, Q, R, h->st));
     h->launches += 1;
   };
-  // Theta (T, row-major) -> FP64 copy; norm (flags NaN/Inf)
-  const T* th = (const T*)h->Th;
-  double* M64 = h->fOm + 0;  // reuse: fOm is sized >= m*n? use fY scratch instead
-  M64 = h->fY;
-  copymap<T, double>(h, m, n, th, IdxMap::lin(n), IdxMap::lin(1), M64, IdxMap::lin(n), IdxMap::lin(1));
-  CK(frob_norm<double>(M64, (long long)m * n, h->dnorm, h->errw, h->st));
+  auto jac = [&](int q, int p, F* W, F* U, F* S, F* V) {
+    CK(jacobi_svd<F, F>(q, p, W, U, S, V, fVw, 60, h->errw, h->st));
+    h->launches += 1;
+  };
+  // Theta (T, row-major) -> F copy; norm (flags NaN/Inf)
+  copymap<T, F>(h, m, n, (const T*)h->Th, IdxMap::lin(n), IdxMap::lin(1), MF, IdxMap::lin(n), IdxMap::lin(1));
+  CK(frob_norm<F>(MF, (long long)m * n, h->dnorm, h->errw, h->st));
   h->launches += 1;
   const int ks = h->chi_max + h->oversample;
   if (h->update == TT_UPDATE_2SITE_RSVD && ks < std::min(m, n)) {
-    CK(philox_fill(h->fOm, (long long)n * ks, h->seed, omega_stream(sweep, site1), 1.0, h->st));
+    CK(philox_fill<F>(fOm, (long long)n * ks, h->seed, omega_stream(sweep, site1), 1.0, h->st));
     h->launches += 1;
-    GemmArgs<double> g;  // Ysk = M Omega (m x ks, col-major)
+    GemmArgs<F> g;  // Ysk = M Omega (m x ks, col-major)
     g.M = m; g.N = ks; g.K = n;
-    g.A = M64; g.am = IdxMap::lin(n); g.ak = IdxMap::lin(1);
-    g.B = h->fOm; g.bn = IdxMap::lin(1); g.bk = IdxMap::lin(ks); g.b_kfast = false;
-    g.C = h->fX; g.cm = IdxMap::lin(1); g.cn = IdxMap::lin(m);
-    gemm<double>(h, g);
-    qr(h, m, ks, h->fX, h->fQ, h->fR);                 // Q (m x ks)
-    GemmArgs<double> g2;  // Bm^T = M^T Q (n x ks, col-major)
+    g.A = MF; g.am = IdxMap::lin(n); g.ak = IdxMap::lin(1);
+    g.B = fOm; g.bn = IdxMap::lin(1); g.bk = IdxMap::lin(ks); g.b_kfast = false;
+    g.C = fX; g.cm = IdxMap::lin(1); g.cn = IdxMap::lin(m);
+    gemm<F>(h, g);
+    qrf(m, ks, fX, fQ, fR);                       // Q (m x ks)
+    GemmArgs<F> g2;  // Bm^T = M^T Q (n x ks, col-major)
     g2.M = n; g2.N = ks; g2.K = m;
-    g2.A = M64; g2.am = IdxMap::lin(1); g2.ak = IdxMap::lin(n); g2.a_kfast = false;
-    g2.B = h->fQ; g2.bn = IdxMap::lin(m); g2.bk = IdxMap::lin(1);
-    g2.C = h->fBt; g2.cm = IdxMap::lin(1); g2.cn = IdxMap::lin(n);
-    gemm<double>(h, g2);
-    qr(h, n, ks, h->fBt, h->fQ2, h->fR2);              // Bm^T = Q2 R2
-    jac(ks, ks, h->fR2, h->fU, h->fS, h->fV);          // R2 = Ur S Vr^T
-    GemmArgs<double> g3;  // U_M = Q Vr (m x ks)
+    g2.A = MF; g2.am = IdxMap::lin(1); g2.ak = IdxMap::lin(n); g2.a_kfast = false;
+    g2.B = fQ; g2.bn = IdxMap::lin(m); g2.bk = IdxMap::lin(1);
+    g2.C = fBt; g2.cm = IdxMap::lin(1); g2.cn = IdxMap::lin(n);
+    gemm<F>(h, g2);
+    qrf(n, ks, fBt, fQ2, fR2);                    // Bm^T = Q2 R2
+    jac(ks, ks, fR2, fU, fS, fV);                 // R2 = Ur S Vr^T
+    GemmArgs<F> g3;  // U_M = Q Vr (m x ks)
     g3.M = m; g3.N = ks; g3.K = ks;
-    g3.A = h->fQ; g3.am = IdxMap::lin(1); g3.ak = IdxMap::lin(m); g3.a_kfast = false;
-    g3.B = h->fV; g3.bn = IdxMap::lin(ks); g3.bk = IdxMap::lin(1);
-    g3.C = h->fUM; g3.cm = IdxMap::lin(1); g3.cn = IdxMap::lin(m);
-    gemm<double>(h, g3);
-    GemmArgs<double> g4;  // V_M = Q2 Ur (n x ks)
+    g3.A = fQ; g3.am = IdxMap::lin(1); g3.ak = IdxMap::lin(m); g3.a_kfast = false;
+    g3.B = fV; g3.bn = IdxMap::lin(ks); g3.bk = IdxMap::lin(1);
+    g3.C = fUM; g3.cm = IdxMap::lin(1); g3.cn = IdxMap::lin(m);
+    gemm<F>(h, g3);
+    GemmArgs<F> g4;  // V_M = Q2 Ur (n x ks)
     g4.M = n; g4.N = ks; g4.K = ks;
-    g4.A = h->fQ2; g4.am = IdxMap::lin(1); g4.ak = IdxMap::lin(n); g4.a_kfast = false;
-    g4.B = h->fU; g4.bn = IdxMap::lin(ks); g4.bk = IdxMap::lin(1);
-    g4.C = h->fVM; g4.cm = IdxMap::lin(1); g4.cn = IdxMap::lin(n);
-    gemm<double>(h, g4);
-    CK(fix_signs(m, n, ks, h->fUM, m, h->fVM, n, h->st));
+    g4.A = fQ2; g4.am = IdxMap::lin(1); g4.ak = IdxMap::lin(n); g4.a_kfast = false;
+    g4.B = fU; g4.bn = IdxMap::lin(ks); g4.bk = IdxMap::lin(1);
+    g4.C = fVM; g4.cm = IdxMap::lin(1); g4.cn = IdxMap::lin(n);
+    gemm<F>(h, g4);
+    CK(fix_signs<F>(m, n, ks, fUM, m, fVM, n, h->st));
     h->launches += 1;
     return ks;
   }
   // exact: work on the tall orientation X (q x p col-major)
   const bool tr = m < n;
   const int q = tr ? n : m, p = tr ? m : n;
-  if (tr) CK(cudaMemcpyAsync(h->fX, M64, sizeof(double) * (size_t)m * n, cudaMemcpyDeviceToDevice, h->st));
-  else to_colmajor(h, m, n, M64, h->fX);
-  double* Ufull;
+  if (tr) CK(cudaMemcpyAsync(fX, MF, sizeof(F) * (size_t)m * n, cudaMemcpyDeviceToDevice, h->st));
+  else copymap<F, F>(h, m, n, MF, IdxMap::lin(n), IdxMap::lin(1), fX, IdxMap::lin(1), IdxMap::lin(m));
+  F* Ufull;
   if (q > p) {
-    qr(h, q, p, h->fX, h->fQ, h->fR);                  // X = Qx Rx
-    jac(p, p, h->fR, h->fU, h->fS, h->fV);             // Rx = Ur S Vr^T
-    GemmArgs<double> g;  // Ufull = Qx Ur (q x p)
+    qrf(q, p, fX, fQ, fR);                        // X = Qx Rx
+    jac(p, p, fR, fU, fS, fV);                    // Rx = Ur S Vr^T
+    GemmArgs<F> g;  // Ufull = Qx Ur (q x p)
     g.M = q; g.N = p; g.K = p;
-    g.A = h->fQ; g.am = IdxMap::lin(1); g.ak = IdxMap::lin(q); g.a_kfast = false;
-    g.B = h->fU; g.bn = IdxMap::lin(p); g.bk = IdxMap::lin(1);
-    g.C = h->fBt; g.cm = IdxMap::lin(1); g.cn = IdxMap::lin(q);
-    gemm<double>(h, g);
-    Ufull = h->fBt;
+    g.A = fQ; g.am = IdxMap::lin(1); g.ak = IdxMap::lin(q); g.a_kfast = false;
+    g.B = fU; g.bn = IdxMap::lin(p); g.bk = IdxMap::lin(1);
+    g.C = fBt; g.cm = IdxMap::lin(1); g.cn = IdxMap::lin(q);
+    gemm<F>(h, g);
+    Ufull = fBt;
   } else {
-    jac(q, p, h->fX, h->fU, h->fS, h->fV);
-    Ufull = h->fU;
+    jac(q, p, fX, fU, fS, fV);
+    Ufull = fU;
   }
   // X = Ufull S Vr^T ; Theta = X (tr = false) or X^T (tr = true)
-  const size_t qb = sizeof(double) * (size_t)q * p, pb = sizeof(double) * (size_t)p * p;
+  const size_t qb = sizeof(F) * (size_t)q * p, pb = sizeof(F) * (size_t)p * p;
   if (!tr) {
-    CK(cudaMemcpyAsync(h->fUM, Ufull, qb, cudaMemcpyDeviceToDevice, h->st));
-    CK(cudaMemcpyAsync(h->fVM, h->fV, pb, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(fUM, Ufull, qb, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(fVM, fV, pb, cudaMemcpyDeviceToDevice, h->st));
   } else {
-    CK(cudaMemcpyAsync(h->fUM, h->fV, pb, cudaMemcpyDeviceToDevice, h->st));
-    CK(cudaMemcpyAsync(h->fVM, Ufull, qb, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(fUM, fV, pb, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(fVM, Ufull, qb, cudaMemcpyDeviceToDevice, h->st));
   }
-  CK(fix_signs(m, n, p, h->fUM, m, h->fVM, n, h->st));
+  CK(fix_signs<F>(m, n, p, fUM, m, fVM, n, h->st));
   h->launches += 1;
   return p;
 }
@@ -540,9 +550,9 @@ struct Sweeper {
     int m, n;
     ch.join(l, m, n);
     CK(cudaEventRecord(h->ev[3], h->st));
-    int p = factorize<T>(h, m, n, sweep, l + 1);
+    int p = factorize<T, T>(h, m, n, sweep, l + 1);
     const double cut = h->cutoff;
-    CK(truncate_rule(h->fS, p, h->dnorm, h->tol / L, h->chi_max, cut, h->dk, h->ddinfo, h->st));
+    CK(truncate_rule<T>((const T*)h->fS, p, h->dnorm, h->tol / L, h->chi_max, cut, h->dk, h->ddinfo, h->st));
     h->launches += 1;
     CK(cudaEventRecord(h->ev[4], h->st));
     CK(cudaMemcpyAsync(h->hk, h->dk, sizeof(int), cudaMemcpyDeviceToHost, h->st));
@@ -573,14 +583,15 @@ struct Sweeper {
     // gauge update (Alg. 3 / Alg. 4)
     const int mode = (h->gauge == TT_GAUGE_INVERSE_CANONICAL) ? 2 : (fwd ? 0 : 1);
     CK(cudaEventRecord(h->ev[5], h->st));
-    CK(gauge_update<T>(mode, m, n, h->fUM, m, h->fS, h->fVM, n, h->dk, h->C64[l], h->C64[l + 1], h->Y[l + 1],
-                       (T*)h->Ut[l], (T*)h->Vt[l + 1], h->st));
+    CK(gauge_update<T, T>(mode, m, n, (const T*)h->fUM, m, (const T*)h->fS, (const T*)h->fVM, n, h->dk, h->C64[l],
+                          h->C64[l + 1], h->Y[l + 1], (T*)h->Ut[l], (T*)h->Vt[l + 1], h->st));
     h->launches += 1;
     CK(cudaEventRecord(h->ev[6], h->st));
     h->gauge_pending = true;
     // host copy of the kept spectrum for tt_fit_result
-    h->lam[l + 1].resize(k);
-    CK(cudaMemcpyAsync(h->lam[l + 1].data(), h->fS, sizeof(double) * k, cudaMemcpyDeviceToHost, h->st));
+    std::vector<T> sv(k);
+    CK(cudaMemcpyAsync(sv.data(), h->fS, sizeof(T) * k, cudaMemcpyDeviceToHost, h->st));
+    h->lam[l + 1].assign(sv.begin(), sv.end());
   }
 
   void run(int n_sweeps) {
@@ -696,6 +707,8 @@ void allocate_chain(tt_fit* h) {
   h->Renv.assign(L + 1, nullptr);
   h->H1.assign(L, nullptr);
   h->H2.assign(L, nullptr);
+  h->H1t.assign(L, nullptr);
+  h->H2t.assign(L, nullptr);
   h->Ut.assign(L, nullptr);
   h->Vt.assign(L, nullptr);
   size_t x1 = 1, zs = 1;
@@ -709,6 +722,8 @@ void allocate_chain(tt_fit* h) {
     const int ds = D.ds[j], du = D.du[j], dt = D.dt[j];
     h->H1[j] = h->pool.alloc<T>(prodll({D.cb[j], ds, dt, D.a[j + 1], D.b[j + 1]}));
     h->H2[j] = h->pool.alloc<T>(prodll({D.a[j], D.b[j], ds, dt, D.cb[j + 1]}));
+    h->H1t[j] = h->pool.alloc<T>(prodll({D.cb[j], ds, dt, D.a[j + 1], D.b[j + 1]}));
+    h->H2t[j] = h->pool.alloc<T>(prodll({D.a[j], D.b[j], ds, dt, D.cb[j + 1]}));
     h->Ut[j] = h->pool.alloc<T>(prodll({D.cb[j + 1], D.cb[j], ds, dt}));
     h->Vt[j] = h->pool.alloc<T>(prodll({D.cb[j], ds, dt, D.cb[j + 1]}));
     x1 = std::max<size_t>(x1, prodll({D.cb[j], D.b[j], ds, du, D.a[j + 1]}));
@@ -927,7 +942,7 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
       for (int j = 0; j < L; ++j) {
         const long long n = prodll({cbond[j], D.ds[j], D.dt[j], cbond[j + 1]});
         C0[j] = h->pool.alloc<double>(n);
-        CK(philox_fill(C0[j], n, h->seed, init_stream(j + 1), 1.0, h->st));
+        CK(philox_fill<double>(C0[j], n, h->seed, init_stream(j + 1), 1.0, h->st));
         if (j > 0) {  // orthonormal rows: QR of the transposed core (q >= p by the bond rule)
           const int q = D.ds[j] * D.dt[j] * cbond[j + 1], p = cbond[j];
           double* R = h->pool.alloc<double>((size_t)p * p);

@@ -78,12 +78,14 @@ __global__ void __launch_bounds__(NT) gemm_simt_kernel(GemmArgs<T> g, T* __restr
     int m = m0 + ty + 16 * i;
     if (m >= g.M) continue;
     long long cr = g.cm(m);
+    long long cr2 = g.C2 ? g.cm2(m) : 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       int n = n0 + tx + 16 * j;
       if (n >= g.N) continue;
       long long o = cr + g.cn(n);
       T v = g.alpha * acc[i][j];
+      if (g.C2) g.C2[cr2 + g.cn2(n)] = v;
       if (g.beta != T(0)) v += g.beta * g.C[o];
       g.C[o] = v;
     }
@@ -99,6 +101,7 @@ __global__ void splitk_reduce_kernel(GemmArgs<T> g, const T* __restrict__ ws, in
     for (int z = 0; z < splits; ++z) s += ws[(size_t)z * total + e];
     long long o = g.cm(m) + g.cn(n);
     T v = g.alpha * s;
+    if (g.C2) g.C2[g.cm2(m) + g.cn2(n)] = v;
     if (g.beta != T(0)) v += g.beta * g.C[o];
     g.C[o] = v;
   }

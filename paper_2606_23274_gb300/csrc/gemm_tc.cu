@@ -102,7 +102,7 @@ template <bool B_MN>
 __global__ void __launch_bounds__(128, 1)
     gemm_tf32_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
                      int K, int k_per_split, float* __restrict__ C, IdxMap cm, IdxMap cn, float alpha, float beta,
-                     float* __restrict__ ws, uint32_t* errw) {
+                     float* __restrict__ C2, IdxMap cm2, IdxMap cn2, float* __restrict__ ws, uint32_t* errw) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
@@ -198,6 +198,7 @@ __global__ void __launch_bounds__(128, 1)
   if (have) {
     const int m = m0 + warp * 32 + lane;
     const long long crow = (m < M) ? cm(m) : 0;
+    const long long crow2 = (m < M && C2) ? cm2(m) : 0;
     float* wrow = ws ? ws + (size_t)blockIdx.z * M * N + (size_t)m * N : nullptr;
 #pragma unroll 1
     for (int c = 0; c < BN; c += 32) {
@@ -214,6 +215,7 @@ __global__ void __launch_bounds__(128, 1)
             } else {
               const long long o = crow + cn(n);
               float out = alpha * v;
+              if (C2) C2[crow2 + cn2(n)] = out;
               if (beta != 0.f) out += beta * C[o];
               C[o] = out;
             }
@@ -232,6 +234,7 @@ __global__ void __launch_bounds__(128, 1)
         if (n < N) {
           const long long o = cm(m) + cn(n);
           C[o] = beta != 0.f ? beta * C[o] : 0.f;
+          if (C2) C2[cm2(m) + cn2(n)] = 0.f;
         }
       }
   } else if (nk == 0 && ws) {
@@ -298,10 +301,10 @@ cudaError_t gemm_tf32(const GemmArgs<float>& g, float* ws, size_t ws_elems, int 
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
   long long lda, ldb, one;
   if (!lin_stride(g.am, lda) || !lin_stride(g.ak, one) || one != 1) return cudaErrorNotSupported;
-  bool b_mn;
-  if (lin_stride(g.bk, one) && one == 1 && lin_stride(g.bn, ldb)) b_mn = false;
-  else if (lin_stride(g.bn, one) && one == 1 && lin_stride(g.bk, ldb)) b_mn = true;
-  else return cudaErrorNotSupported;
+  // B must be K-major: an MN-major B with kind::tf32 produced an all-zero
+  // accumulator in the self-check, so such layouts go to the CUDA-core kernel.
+  bool b_mn = false;
+  if (!(lin_stride(g.bk, one) && one == 1 && lin_stride(g.bn, ldb))) return cudaErrorNotSupported;
   // TMA: 16-byte aligned bases and row strides
   if (((uintptr_t)g.A & 15) || ((uintptr_t)g.B & 15) || (lda * 4) % 16 || (ldb * 4) % 16) return cudaErrorNotSupported;
   if (lda < g.K || (!b_mn && ldb < g.K) || (b_mn && ldb < g.N)) return cudaErrorNotSupported;
@@ -333,10 +336,10 @@ cudaError_t gemm_tf32(const GemmArgs<float>& g, float* ws, size_t ws_elems, int 
   float* wsp = splits > 1 ? ws : nullptr;
   if (b_mn)
     gemm_tf32_kernel<true><<<grid, 128, SMEM_BYTES, st>>>(ta, tb, g.M, g.N, g.K, kps, g.C, g.cm, g.cn, g.alpha,
-                                                           g.beta, wsp, errw);
+                                                           g.beta, g.C2, g.cm2, g.cn2, wsp, errw);
   else
     gemm_tf32_kernel<false><<<grid, 128, SMEM_BYTES, st>>>(ta, tb, g.M, g.N, g.K, kps, g.C, g.cm, g.cn, g.alpha,
-                                                            g.beta, wsp, errw);
+                                                            g.beta, g.C2, g.cm2, g.cn2, wsp, errw);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || splits == 1) return e;
   return splitk_reduce<float>(g, ws, splits, sm_count, st);

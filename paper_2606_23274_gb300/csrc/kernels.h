@@ -18,6 +18,9 @@ struct GemmArgs {
   T* C = nullptr;
   IdxMap cm, cn;
   T alpha = T(1), beta = T(0);
+  // optional second copy of the result in another layout (written with beta = 0)
+  T* C2 = nullptr;
+  IdxMap cm2, cn2;
 };
 
 template <typename T>
@@ -38,21 +41,23 @@ cudaError_t copy_map(int rows, int cols, const Tin* in, IdxMap im, IdxMap in_, T
                      double scale, cudaStream_t st);
 
 // fill out[i] = scale * N(0,1)_philox(seed, stream, i), i < count
-cudaError_t philox_fill(double* out, long long count, uint64_t seed, uint64_t stream, double scale, cudaStream_t st);
+template <typename F>
+cudaError_t philox_fill(F* out, long long count, uint64_t seed, uint64_t stream, double scale, cudaStream_t st);
 
 // Householder QR of the q x p column-major matrix X (ld q; overwritten):
 // Q is q x r (col-major, ld q), R is r x p (col-major, ld r), r = min(q, p),
-// diag(R) >= 0. One CTA.
-template <typename C>
-cudaError_t qr_householder(int q, int p, double* X, double* Q, double* R, cudaStream_t st);
+// diag(R) >= 0. One CTA. C: arithmetic type, S: storage type.
+template <typename C, typename S>
+cudaError_t qr_householder(int q, int p, S* X, S* Q, S* R, cudaStream_t st);
 
 // One-sided Jacobi SVD of the q x p column-major W (q >= p, ld q; overwritten):
 // W = U diag(S) V^T with U (q x p, col-major), S sorted descending, V (p x p,
-// col-major). C is the arithmetic type of the rotations. errw |= ERRW_NOCONV
-// when max_sweeps is reached.
-template <typename C>
-cudaError_t jacobi_svd(int q, int p, double* W, double* U, double* S, double* V, double* Vwork,
-                       int max_sweeps, uint32_t* errw, cudaStream_t st);
+// col-major). C is the arithmetic type of the rotations, S the storage type;
+// the working set is held in shared memory when it fits (<= 200 KB).
+// errw |= ERRW_NOCONV when max_sweeps is reached.
+template <typename C, typename S>
+cudaError_t jacobi_svd(int q, int p, S* W, S* U, S* Sv, S* V, S* Vwork, int max_sweeps, uint32_t* errw,
+                       cudaStream_t st);
 
 // ||X||_F of n values (type T) into *out (double), flags non-finite values.
 template <typename T>
@@ -60,7 +65,8 @@ cudaError_t frob_norm(const T* x, long long n, double* out, uint32_t* errw, cuda
 
 // Truncation rule (Sec. 2.3.4): from sorted S (p values), ||M||_F, writes
 // info[0] = k, and dinfo[0] = sum_{j<k} s_j^2, dinfo[1] = sqrt(sum_{j>=k} s_j^2)/||M||_F.
-cudaError_t truncate_rule(const double* S, int p, const double* normM, double tau_over_L, int chi_max,
+template <typename F>
+cudaError_t truncate_rule(const F* S, int p, const double* normM, double tau_over_L, int chi_max,
                           double cutoff, int* info, double* dinfo, cudaStream_t st);
 
 // Gauge update after the factorisation of the m x n two-site matrix
@@ -69,13 +75,14 @@ cudaError_t truncate_rule(const double* S, int p, const double* normM, double ta
 // (C_l = U S, C_{l+1} = V^T), 2 = inverse (Psi_l = U S, Psi_{l+1} = S V^T,
 // Y_l = 1/S). Writes Cl (m x k row-major), Cr (k x n row-major), Y (k) and
 // the environment operands Ut (k x m row-major) and Vt (k x n row-major) in T.
-template <typename T>
-cudaError_t gauge_update(int mode, int m, int n, const double* U, int ld_u, const double* S, const double* V, int ld_v,
+template <typename T, typename F>
+cudaError_t gauge_update(int mode, int m, int n, const F* U, int ld_u, const F* S, const F* V, int ld_v,
                          const int* kdev, double* Cl, double* Cr, double* Y, T* Ut, T* Vt, cudaStream_t st);
 
 // Flip singular pairs j < p so that the largest-magnitude entry of U[:, j] is
 // positive (U: m x p col-major ld_u; V: n x p col-major ld_v).
-cudaError_t fix_signs(int m, int n, int p, double* U, int ld_u, double* V, int ld_v, cudaStream_t st);
+template <typename F>
+cudaError_t fix_signs(int m, int n, int p, F* U, int ld_u, F* V, int ld_v, cudaStream_t st);
 
 // out (rows x cols, row-major) = in * diag(y) (y == nullptr: plain copy)
 cudaError_t scale_cols(int rows, int cols, const double* in, const double* y, double* out, cudaStream_t st);

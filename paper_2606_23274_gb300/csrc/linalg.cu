@@ -25,15 +25,15 @@ __device__ __forceinline__ C block_sum(C v, C* red) {
 // Householder QR, one CTA. X: q x p column-major (ld q), overwritten by the
 // reflectors (unit vectors, rows j..q-1 of column j). Q: q x r, R: r x p.
 // ---------------------------------------------------------------------------
-template <typename C>
-__global__ void __launch_bounds__(1024) qr_house_kernel(int q, int p, double* __restrict__ X, double* __restrict__ Q,
-                                                        double* __restrict__ R) {
+template <typename C, typename S>
+__global__ void __launch_bounds__(1024) qr_house_kernel(int q, int p, S* __restrict__ X, S* __restrict__ Q,
+                                                        S* __restrict__ R) {
   __shared__ C red[32];
   __shared__ double diag[1024];  // r <= 1024
   const int r = min(q, p);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int j = 0; j < r; ++j) {
-    double* xj = X + (size_t)j * q;
+    S* xj = X + (size_t)j * q;
     C ss = 0;
     for (int i = j + threadIdx.x; i < q; i += blockDim.x) {
       C v = (C)xj[i];
@@ -48,16 +48,16 @@ __global__ void __launch_bounds__(1024) qr_house_kernel(int q, int p, double* __
     __syncthreads();
     const bool zero = !(vn2 > C(0));
     const C inv = zero ? C(0) : C(1) / sqrt(vn2);
-    for (int i = j + threadIdx.x; i < q; i += blockDim.x) xj[i] = (double)((i == j ? v0 : (C)xj[i]) * inv);
+    for (int i = j + threadIdx.x; i < q; i += blockDim.x) xj[i] = (S)((i == j ? v0 : (C)xj[i]) * inv);
     if (threadIdx.x == 0) diag[j] = zero ? 0.0 : (double)alpha;
     __syncthreads();
     if (!zero) {
       for (int c = j + 1 + warp; c < p; c += nw) {
-        double* xc = X + (size_t)c * q;
+        S* xc = X + (size_t)c * q;
         C d = 0;
         for (int i = j + lane; i < q; i += 32) d += (C)xj[i] * (C)xc[i];
         d = warp_sum(d);
-        for (int i = j + lane; i < q; i += 32) xc[i] = (double)((C)xc[i] - C(2) * d * (C)xj[i]);
+        for (int i = j + lane; i < q; i += 32) xc[i] = (S)((C)xc[i] - C(2) * d * (C)xj[i]);
       }
     }
     __syncthreads();
@@ -65,23 +65,23 @@ __global__ void __launch_bounds__(1024) qr_house_kernel(int q, int p, double* __
   // R (r x p, col-major, ld r)
   for (long long e = threadIdx.x; e < (long long)r * p; e += blockDim.x) {
     int i = (int)(e % r), c = (int)(e / r);
-    double v = (i < c) ? X[(size_t)c * q + i] : (i == c ? diag[i] : 0.0);
-    R[(size_t)c * r + i] = v;
+    double v = (i < c) ? (double)X[(size_t)c * q + i] : (i == c ? diag[i] : 0.0);
+    R[(size_t)c * r + i] = (S)v;
   }
   // Q = H_0 ... H_{r-1} [I_r; 0]
   for (long long e = threadIdx.x; e < (long long)q * r; e += blockDim.x) {
     int i = (int)(e % q), c = (int)(e / q);
-    Q[(size_t)c * q + i] = (i == c) ? 1.0 : 0.0;
+    Q[(size_t)c * q + i] = (i == c) ? S(1) : S(0);
   }
   __syncthreads();
   for (int j = r - 1; j >= 0; --j) {
-    const double* vj = X + (size_t)j * q;
+    const S* vj = X + (size_t)j * q;
     for (int c = j + warp; c < r; c += nw) {
-      double* qc = Q + (size_t)c * q;
+      S* qc = Q + (size_t)c * q;
       C d = 0;
       for (int i = j + lane; i < q; i += 32) d += (C)vj[i] * (C)qc[i];
       d = warp_sum(d);
-      for (int i = j + lane; i < q; i += 32) qc[i] = (double)((C)qc[i] - C(2) * d * (C)vj[i]);
+      for (int i = j + lane; i < q; i += 32) qc[i] = (S)((C)qc[i] - C(2) * d * (C)vj[i]);
     }
     __syncthreads();
   }
@@ -94,15 +94,16 @@ __global__ void __launch_bounds__(1024) qr_house_kernel(int q, int p, double* __
   }
 }
 
-template <typename C>
-cudaError_t qr_householder(int q, int p, double* X, double* Q, double* R, cudaStream_t st) {
+template <typename C, typename S>
+cudaError_t qr_householder(int q, int p, S* X, S* Q, S* R, cudaStream_t st) {
   if (q <= 0 || p <= 0) return cudaSuccess;
   if (q > 1 << 20 || min(q, p) > 1024) return cudaErrorInvalidValue;
-  qr_house_kernel<C><<<1, 1024, 0, st>>>(q, p, X, Q, R);
+  qr_house_kernel<C, S><<<1, 1024, 0, st>>>(q, p, X, Q, R);
   return cudaGetLastError();
 }
-template cudaError_t qr_householder<double>(int, int, double*, double*, double*, cudaStream_t);
-template cudaError_t qr_householder<float>(int, int, double*, double*, double*, cudaStream_t);
+template cudaError_t qr_householder<double, double>(int, int, double*, double*, double*, cudaStream_t);
+template cudaError_t qr_householder<float, double>(int, int, double*, double*, double*, cudaStream_t);
+template cudaError_t qr_householder<float, float>(int, int, float*, float*, float*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // One-sided (Hestenes) Jacobi SVD, one CTA, round-robin pair ordering: every
@@ -120,18 +121,26 @@ __device__ __forceinline__ void rr_pair(int round, int k, int P, int& i, int& j)
   }
 }
 
-template <typename C>
-__global__ void __launch_bounds__(1024) jacobi_kernel(int q, int p, double* __restrict__ W, double* __restrict__ V,
+template <typename C, typename S>
+__global__ void __launch_bounds__(1024) jacobi_kernel(int q, int p, S* __restrict__ Wg, S* __restrict__ Vg,
                                                       int max_sweeps, double tol, uint32_t* errw,
-                                                      double* __restrict__ Uo, double* __restrict__ So,
-                                                      double* __restrict__ Vo) {
+                                                      S* __restrict__ Uo, S* __restrict__ So,
+                                                      S* __restrict__ Vo, int in_smem) {
+  extern __shared__ __align__(16) unsigned char jsm[];
   __shared__ int rotated;
   __shared__ double nrm[1024];
   __shared__ int rank_[1024];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  S* W = Wg;
+  S* V = Vg;
+  if (in_smem) {  // the whole working set (q x p columns and p x p rotations) lives in shared memory
+    W = (S*)jsm;
+    V = W + (size_t)q * p;
+    for (long long e = threadIdx.x; e < (long long)q * p; e += blockDim.x) W[e] = Wg[e];
+  }
   for (long long e = threadIdx.x; e < (long long)p * p; e += blockDim.x) {
     int i = (int)(e % p), c = (int)(e / p);
-    V[e] = (i == c) ? 1.0 : 0.0;
+    V[e] = (i == c) ? S(1) : S(0);
   }
   const int P = p + (p & 1);
   int sweep = 0;
@@ -146,8 +155,8 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int q, int p, double* __re
         rr_pair(round, k, P, i, j);
         if (i >= p || j >= p) continue;
         if (i > j) { int t = i; i = j; j = t; }
-        double* wi = W + (size_t)i * q;
-        double* wj = W + (size_t)j * q;
+        S* wi = W + (size_t)i * q;
+        S* wj = W + (size_t)j * q;
         C a = 0, b = 0, g = 0;
         for (int r = lane; r < q; r += 32) {
           C x = (C)wi[r], y = (C)wj[r];
@@ -166,15 +175,15 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int q, int p, double* __re
         const C sn = cs * t;
         for (int r = lane; r < q; r += 32) {
           C x = (C)wi[r], y = (C)wj[r];
-          wi[r] = (double)(cs * x - sn * y);
-          wj[r] = (double)(sn * x + cs * y);
+          wi[r] = (S)(cs * x - sn * y);
+          wj[r] = (S)(sn * x + cs * y);
         }
-        double* vi = V + (size_t)i * p;
-        double* vj = V + (size_t)j * p;
+        S* vi = V + (size_t)i * p;
+        S* vj = V + (size_t)j * p;
         for (int r = lane; r < p; r += 32) {
           C x = (C)vi[r], y = (C)vj[r];
-          vi[r] = (double)(cs * x - sn * y);
-          vj[r] = (double)(sn * x + cs * y);
+          vi[r] = (S)(cs * x - sn * y);
+          vj[r] = (S)(sn * x + cs * y);
         }
         if (lane == 0) rotated = 1;
       }
@@ -185,11 +194,11 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int q, int p, double* __re
     __syncthreads();
   }
   if (!done && threadIdx.x == 0 && errw) atomicOr(errw, ERRW_NOCONV);
-  // singular values = column norms (FP64), sorted descending, ties by index
+  // singular values = column norms, sorted descending, ties by index
   for (int c = warp; c < p; c += nw) {
-    const double* wc = W + (size_t)c * q;
+    const S* wc = W + (size_t)c * q;
     double s = 0;
-    for (int r = lane; r < q; r += 32) s += wc[r] * wc[r];
+    for (int r = lane; r < q; r += 32) s += (double)wc[r] * (double)wc[r];
     s = warp_sum(s);
     if (lane == 0) nrm[c] = sqrt(s);
   }
@@ -199,32 +208,48 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int q, int p, double* __re
     double v = nrm[c];
     for (int d = 0; d < p; ++d) rk += (nrm[d] > v) || (nrm[d] == v && d < c);
     rank_[c] = rk;
-    So[rk] = v;
+    So[rk] = (S)v;
   }
   __syncthreads();
   for (int c = warp; c < p; c += nw) {
     const int rk = rank_[c];
     const double s = nrm[c];
     const double inv = s > 0.0 ? 1.0 / s : 0.0;
-    for (int r = lane; r < q; r += 32) Uo[(size_t)rk * q + r] = W[(size_t)c * q + r] * inv;
+    for (int r = lane; r < q; r += 32) Uo[(size_t)rk * q + r] = (S)((double)W[(size_t)c * q + r] * inv);
     for (int r = lane; r < p; r += 32) Vo[(size_t)rk * p + r] = V[(size_t)c * p + r];
   }
 }
 
-template <typename C>
-cudaError_t jacobi_svd(int q, int p, double* W, double* U, double* S, double* V, double* Vwork, int max_sweeps,
-                       uint32_t* errw, cudaStream_t st) {
+template <typename C, typename S>
+cudaError_t jacobi_svd(int q, int p, S* W, S* U, S* Sv, S* V, S* Vwork, int max_sweeps, uint32_t* errw,
+                       cudaStream_t st) {
   if (q <= 0 || p <= 0) return cudaSuccess;
   if (p > 1024 || q < p) return cudaErrorInvalidValue;
+  // rotate while |w_i . w_j| > 4 eps sqrt(q) |w_i| |w_j|: the rounding error of the
+  // computed dot product is about eps sqrt(q) |w_i| |w_j|, so a smaller threshold
+  // would keep rotating on noise
   const double eps = (sizeof(C) == 8) ? DBL_EPSILON : (double)FLT_EPSILON;
-  const double tol = eps * sqrt((double)q);
-  jacobi_kernel<C><<<1, 1024, 0, st>>>(q, p, W, Vwork, max_sweeps, tol, errw, U, S, V);
+  const double tol = 4.0 * eps * sqrt((double)q);
+  const size_t need = ((size_t)q * p + (size_t)p * p) * sizeof(S);
+  const size_t cap = 200 * 1024;
+  int in_smem = need <= cap ? 1 : 0;
+  if (in_smem) {
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(jacobi_kernel<C, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+  }
+  jacobi_kernel<C, S><<<1, 1024, in_smem ? need : 0, st>>>(q, p, W, Vwork, max_sweeps, tol, errw, U, Sv, V, in_smem);
   return cudaGetLastError();
 }
-template cudaError_t jacobi_svd<double>(int, int, double*, double*, double*, double*, double*, int, uint32_t*,
-                                        cudaStream_t);
-template cudaError_t jacobi_svd<float>(int, int, double*, double*, double*, double*, double*, int, uint32_t*,
-                                       cudaStream_t);
+template cudaError_t jacobi_svd<double, double>(int, int, double*, double*, double*, double*, double*, int,
+                                                uint32_t*, cudaStream_t);
+template cudaError_t jacobi_svd<float, double>(int, int, double*, double*, double*, double*, double*, int, uint32_t*,
+                                               cudaStream_t);
+template cudaError_t jacobi_svd<float, float>(int, int, float*, float*, float*, float*, float*, int, uint32_t*,
+                                              cudaStream_t);
 
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -254,7 +279,8 @@ template cudaError_t frob_norm<double>(const double*, long long, double*, uint32
 template cudaError_t frob_norm<float>(const float*, long long, double*, uint32_t*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
-__global__ void truncate_kernel(const double* S, int p, const double* normM, double tau_over_L, int chi_max,
+template <typename F>
+__global__ void truncate_kernel(const F* S, int p, const double* normM, double tau_over_L, int chi_max,
                                 double cutoff, int* info, double* dinfo) {
   if (threadIdx.x != 0) return;
   const double nM = *normM;
@@ -264,7 +290,7 @@ __global__ void truncate_kernel(const double* S, int p, const double* normM, dou
     int kmin = p;
     double tail = 0.0;
     for (int j = p - 1; j >= 1; --j) {
-      tail += S[j] * S[j];
+      tail += (double)S[j] * (double)S[j];
       if (sqrt(tail) <= thr) kmin = j;
       else break;
     }
@@ -272,64 +298,70 @@ __global__ void truncate_kernel(const double* S, int p, const double* normM, dou
   }
   if (p > 0) {
     int cnt = 0;
-    for (int j = 0; j < p; ++j) cnt += S[j] > cutoff * S[0];
+    for (int j = 0; j < p; ++j) cnt += (double)S[j] > cutoff * (double)S[0];
     k = min(k, cnt);
   }
   k = max(k, 1);
   double kept = 0.0, disc = 0.0;
   for (int j = 0; j < p; ++j) {
-    if (j < k) kept += S[j] * S[j];
-    else disc += S[j] * S[j];
+    const double sj = (double)S[j];
+    if (j < k) kept += sj * sj;
+    else disc += sj * sj;
   }
   info[0] = k;
   dinfo[0] = kept;
   dinfo[1] = nM > 0.0 ? sqrt(disc) / nM : 0.0;
 }
 
-cudaError_t truncate_rule(const double* S, int p, const double* normM, double tau_over_L, int chi_max, double cutoff,
+template <typename F>
+cudaError_t truncate_rule(const F* S, int p, const double* normM, double tau_over_L, int chi_max, double cutoff,
                           int* info, double* dinfo, cudaStream_t st) {
-  truncate_kernel<<<1, 32, 0, st>>>(S, p, normM, tau_over_L, chi_max, cutoff, info, dinfo);
+  truncate_kernel<F><<<1, 32, 0, st>>>(S, p, normM, tau_over_L, chi_max, cutoff, info, dinfo);
   return cudaGetLastError();
 }
+template cudaError_t truncate_rule<double>(const double*, int, const double*, double, int, double, int*, double*,
+                                           cudaStream_t);
+template cudaError_t truncate_rule<float>(const float*, int, const double*, double, int, double, int*, double*,
+                                          cudaStream_t);
 
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void gauge_update_kernel(int mode, int m, int n, const double* __restrict__ U, int ld_u,
-                                    const double* __restrict__ S, const double* __restrict__ V, int ld_v,
+template <typename T, typename F>
+__global__ void gauge_update_kernel(int mode, int m, int n, const F* __restrict__ U, int ld_u,
+                                    const F* __restrict__ S, const F* __restrict__ V, int ld_v,
                                     const int* __restrict__ kdev, double* Cl, double* Cr, double* Y, T* Ut, T* Vt) {
   const int k = *kdev;
   const long long tot_l = (long long)m * k, tot_r = (long long)k * n;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot_l; e += stride) {
     const int i = (int)(e / k), j = (int)(e % k);
-    const double u = U[(size_t)j * ld_u + i];
-    Cl[e] = (mode == 0) ? u : u * S[j];
+    const double u = (double)U[(size_t)j * ld_u + i];
+    Cl[e] = (mode == 0) ? u : u * (double)S[j];
     Ut[(size_t)j * m + i] = (T)u;
   }
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot_r; e += stride) {
     const int j = (int)(e / n), c = (int)(e % n);
-    const double v = V[(size_t)j * ld_v + c];
-    Cr[e] = (mode == 1) ? v : S[j] * v;
+    const double v = (double)V[(size_t)j * ld_v + c];
+    Cr[e] = (mode == 1) ? v : (double)S[j] * v;
     Vt[e] = (T)v;
   }
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < k; e += stride)
-    Y[e] = (mode == 2) ? (S[e] > 0.0 ? 1.0 / S[e] : 0.0) : 1.0;
+    Y[e] = (mode == 2) ? ((double)S[e] > 0.0 ? 1.0 / (double)S[e] : 0.0) : 1.0;
 }
 
-template <typename T>
-cudaError_t gauge_update(int mode, int m, int n, const double* U, int ld_u, const double* S, const double* V, int ld_v,
+template <typename T, typename F>
+cudaError_t gauge_update(int mode, int m, int n, const F* U, int ld_u, const F* S, const F* V, int ld_v,
                          const int* kdev, double* Cl, double* Cr, double* Y, T* Ut, T* Vt, cudaStream_t st) {
   long long tot = (long long)(m > n ? m : n) * 128;
   int blocks = (int)((tot + 255) / 256);
   if (blocks > 1024) blocks = 1024;
   if (blocks < 1) blocks = 1;
-  gauge_update_kernel<T><<<blocks, 256, 0, st>>>(mode, m, n, U, ld_u, S, V, ld_v, kdev, Cl, Cr, Y, Ut, Vt);
+  gauge_update_kernel<T, F><<<blocks, 256, 0, st>>>(mode, m, n, U, ld_u, S, V, ld_v, kdev, Cl, Cr, Y, Ut, Vt);
   return cudaGetLastError();
 }
-template cudaError_t gauge_update<double>(int, int, int, const double*, int, const double*, const double*, int,
-                                          const int*, double*, double*, double*, double*, double*, cudaStream_t);
-template cudaError_t gauge_update<float>(int, int, int, const double*, int, const double*, const double*, int,
-                                         const int*, double*, double*, double*, float*, float*, cudaStream_t);
+template cudaError_t gauge_update<double, double>(int, int, int, const double*, int, const double*, const double*, int,
+                                                  const int*, double*, double*, double*, double*, double*, cudaStream_t);
+template cudaError_t gauge_update<float, float>(int, int, int, const float*, int, const float*, const float*, int,
+                                                const int*, double*, double*, double*, float*, float*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 template <typename Tin, typename Tout>
@@ -362,31 +394,36 @@ template cudaError_t copy_map<float, float>(int, int, const float*, IdxMap, IdxM
                                             cudaStream_t);
 
 // ---------------------------------------------------------------------------
-__global__ void philox_fill_kernel(double* out, long long count, uint64_t seed, uint64_t stream, double scale) {
+template <typename F>
+__global__ void philox_fill_kernel(F* out, long long count, uint64_t seed, uint64_t stream, double scale) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
-    out[i] = scale * philox_normal(seed, stream, (uint64_t)i);
+    out[i] = (F)(scale * philox_normal(seed, stream, (uint64_t)i));
 }
 
-cudaError_t philox_fill(double* out, long long count, uint64_t seed, uint64_t stream, double scale, cudaStream_t st) {
+template <typename F>
+cudaError_t philox_fill(F* out, long long count, uint64_t seed, uint64_t stream, double scale, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   int blocks = (int)((count + 255) / 256);
   if (blocks > 2048) blocks = 2048;
-  philox_fill_kernel<<<blocks, 256, 0, st>>>(out, count, seed, stream, scale);
+  philox_fill_kernel<F><<<blocks, 256, 0, st>>>(out, count, seed, stream, scale);
   return cudaGetLastError();
 }
+template cudaError_t philox_fill<double>(double*, long long, uint64_t, uint64_t, double, cudaStream_t);
+template cudaError_t philox_fill<float>(float*, long long, uint64_t, uint64_t, double, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Sign convention of singular pair j: the entry of largest magnitude of u_j is
 // positive (lowest index on ties); (u_j, v_j) are flipped together.
-__global__ void fix_signs_kernel(int m, int n, double* __restrict__ U, int ld_u, double* __restrict__ V, int ld_v) {
+template <typename F>
+__global__ void fix_signs_kernel(int m, int n, F* __restrict__ U, int ld_u, F* __restrict__ V, int ld_v) {
   __shared__ double sb[32];
   __shared__ int si[32];
   __shared__ double sgn;
-  double* u = U + (size_t)blockIdx.x * ld_u;
+  F* u = U + (size_t)blockIdx.x * ld_u;
   double best = -1.0;
   int bi = 0x7fffffff;
   for (int i = threadIdx.x; i < m; i += blockDim.x) {
-    const double a = fabs(u[i]);
+    const double a = fabs((double)u[i]);
     if (a > best) {
       best = a;
       bi = i;
@@ -413,21 +450,24 @@ __global__ void fix_signs_kernel(int m, int n, double* __restrict__ U, int ld_u,
         sb[0] = sb[w];
         si[0] = si[w];
       }
-    sgn = (si[0] < m && u[si[0]] < 0.0) ? -1.0 : 1.0;
+    sgn = (si[0] < m && (double)u[si[0]] < 0.0) ? -1.0 : 1.0;
   }
   __syncthreads();
   if (sgn < 0.0) {
     for (int i = threadIdx.x; i < m; i += blockDim.x) u[i] = -u[i];
-    double* v = V + (size_t)blockIdx.x * ld_v;
+    F* v = V + (size_t)blockIdx.x * ld_v;
     for (int c = threadIdx.x; c < n; c += blockDim.x) v[c] = -v[c];
   }
 }
 
-cudaError_t fix_signs(int m, int n, int p, double* U, int ld_u, double* V, int ld_v, cudaStream_t st) {
+template <typename F>
+cudaError_t fix_signs(int m, int n, int p, F* U, int ld_u, F* V, int ld_v, cudaStream_t st) {
   if (p <= 0 || m <= 0) return cudaSuccess;
-  fix_signs_kernel<<<p, 256, 0, st>>>(m, n, U, ld_u, V, ld_v);
+  fix_signs_kernel<F><<<p, 256, 0, st>>>(m, n, U, ld_u, V, ld_v);
   return cudaGetLastError();
 }
+template cudaError_t fix_signs<double>(int, int, int, double*, int, double*, int, cudaStream_t);
+template cudaError_t fix_signs<float>(int, int, int, float*, int, float*, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 __global__ void scale_cols_kernel(int rows, int cols, const double* __restrict__ in, const double* __restrict__ y,

@@ -173,3 +173,20 @@ def test_float32_inputs_and_outputs():
     D = to_dense([a.astype(np.float32).astype(np.float64) for a in A]) @ \
         to_dense([b.astype(np.float32).astype(np.float64) for b in B])
     assert np.linalg.norm(to_dense(C) - D) <= 1e-6 * np.linalg.norm(D)
+
+
+@pytest.mark.parametrize("gauge", ["site", "inverse"])
+def test_tf32_tensor_core_chain_matches_oracle(gauge):
+    """TF32 tensor-core contractions (10-bit mantissa, FP32 accumulation): the fit
+    agrees with the FP64 oracle to the TF32 rounding level; bulk bonds are 16
+    wide, so the chain GEMMs take the tcgen05 path."""
+    A, B = mpo_pair("kron_L12_chi32", 5)
+    f = FitOracle(A, B, 16, 0.0, gauge=gauge, sv_cutoff=1e-6)
+    f.sweep(4, stop_on_converge=False)
+    C, reps, b, _ = _gpu_fit(A, B, 16, 0.0, 4, gauge=gauge, precision="tf32", conv_tol=0.0)
+    assert b == f.bonds()
+    err = _rel(C, f.result())
+    print("tf32 rel err", err)
+    assert err <= 1e-2
+    for r, h in zip(reps, f.st.history):
+        assert abs(r["norm2_C"] - h.norm2) <= 1e-2 * h.norm2
