@@ -53,11 +53,21 @@ typedef enum { TT_GAUGE_SITE_CANONICAL = 0, TT_GAUGE_INVERSE_CANONICAL = 1 } tt_
 typedef enum { TT_UPDATE_2SITE_SVD = 0, TT_UPDATE_2SITE_RSVD = 1 } tt_update;
 
 /* Arithmetic of the contractions (environments, halves, two-site tensor).
- * FP64: FP64 CUDA-core kernels. FP32: FP32 CUDA-core kernels.
- * TF32 / BF16_SPLIT: tensor-core kernels (tcgen05) with FP32 accumulation;
- * BF16_SPLIT uses hi+lo BF16 operand pairs (three products).
- * The factorisation stage always returns FP64 factors. */
-typedef enum { TT_PREC_FP64 = 0, TT_PREC_FP32 = 1, TT_PREC_TF32 = 2, TT_PREC_BF16_SPLIT = 3 } tt_precision;
+ * FP64: FP64 CUDA-core kernels; FP64 factorisation (the 1e-10 parity path).
+ * FP32: FP32 CUDA-core kernels. TF32: tensor-core kernels (tcgen05, TF32
+ * operands, FP32 accumulation in tensor memory). TF32_SPLIT: the same with
+ * each operand split into a TF32 high part and an FP32 remainder, three
+ * products (hi*hi + hi*lo + lo*hi): about FP32 accuracy. BF16_SPLIT: reserved,
+ * rejected with TT_ERR_INVALID_ARGUMENT. The non-FP64 paths factorise in
+ * FP32 and make the kept singular vectors an FP64 isometry (one
+ * Newton-Schulz step) before the gauge update; C is returned in FP64. */
+typedef enum {
+  TT_PREC_FP64 = 0,
+  TT_PREC_FP32 = 1,
+  TT_PREC_TF32 = 2,
+  TT_PREC_BF16_SPLIT = 3,
+  TT_PREC_TF32_SPLIT = 4
+} tt_precision;
 
 /* Initial guess (Sec. 2.3.5). RANDOM: right-canonical MPO from a Philox4x32-10
  * Gaussian stream (core 1 Gaussian, core l>=2 the orthonormal-row factor of a

@@ -101,6 +101,7 @@ struct tt_fit {
   size_t gws_elems = 0;
   // factorisation workspace (FP64)
   double *fX, *fQ, *fR, *fU, *fV, *fVw, *fS, *fUM, *fVM, *fOm, *fY, *fBt, *fQ2, *fR2;
+  double *pU = nullptr, *pV = nullptr, *pG = nullptr, *pT = nullptr, *pP = nullptr, *dn2 = nullptr;  // FP64 polish
   size_t fsz = 0;
   double* dnorm = nullptr;
   int* dk = nullptr;
@@ -144,8 +145,10 @@ template <typename T>
 void gemm(tt_fit* h, const GemmArgs<T>& g, bool chain = false) {
   const size_t wse = h->gws_elems * sizeof(double) / sizeof(T);
   if constexpr (sizeof(T) == 4) {
-    if (chain && h->precision == TT_PREC_TF32 && (long long)g.M * g.N * g.K >= (1ll << 18)) {
-      cudaError_t e = gemm_tf32(g, (float*)h->gws, wse, h->sm_count, h->errw, h->st);
+    const bool tc = h->precision == TT_PREC_TF32 || h->precision == TT_PREC_TF32_SPLIT;
+    if (chain && tc && (long long)g.M * g.N * g.K >= (1ll << 18)) {
+      cudaError_t e = gemm_tf32(g, (float*)h->gws, wse, h->sm_count, h->errw, h->st,
+                                h->precision == TT_PREC_TF32_SPLIT);
       if (e == cudaSuccess) {
         h->launches += 2;
         h->tc_launches += 1;
@@ -165,9 +168,11 @@ void copymap(tt_fit* h, int rows, int cols, const Tin* in, IdxMap im, IdxMap in_
   h->launches += 1;
 }
 
+// QR on FP64 storage (input preparation and the guess): FP64 arithmetic; mixing
+// FP32 arithmetic with FP64 storage is slower on this GPU (conversions run on
+// the FP64 pipe).
 void qr(tt_fit* h, int q, int p, double* X, double* Q, double* R) {
-  if (h->use_f32) CK(qr_householder<float, double>(q, p, X, Q, R, h->st));
-  else CK(qr_householder<double, double>(q, p, X, Q, R, h->st));
+  CK(qr_householder<double, double>(q, p, X, Q, R, h->st));
   h->launches += 1;
 }
 
@@ -176,19 +181,42 @@ void to_colmajor(tt_fit* h, int rows, int cols, const double* in, double* out) {
   copymap<double, double>(h, rows, cols, in, IdxMap::lin(cols), IdxMap::lin(1), out, IdxMap::lin(1), IdxMap::lin(rows));
 }
 
-// Right-to-left RQ sweep (each core the orthonormal-row factor, bond trimmed to
-// min(rows, cols)); X's cores are replaced. bond updated.
-void rq_sweep(tt_fit* h, std::vector<double*>& X, std::vector<int>& bond, const std::vector<int>& dA,
-              const std::vector<int>& dB, int upto) {
+// Input / guess preparation runs on its own stream with its own scratch, so
+// that A and B are prepared concurrently; buffers that die during a sweep are
+// released after the final synchronisation.
+struct Prep {
+  cudaStream_t st = nullptr;
+  double *X = nullptr, *Q = nullptr, *R = nullptr, *ws = nullptr;
+  size_t ws_elems = 0;
+  std::vector<void*> dead;
+};
+
+void prep_qr(tt_fit* h, Prep& P, int q, int p) {
+  CK(qr_householder<double, double>(q, p, P.X, P.Q, P.R, P.st));
+  h->launches += 1;
+}
+
+void prep_gemm(tt_fit* h, Prep& P, const GemmArgs<double>& g) {
+  CK(gemm_simt<double>(g, P.ws, P.ws_elems, h->sm_count, P.st));
+  h->launches += 2;
+}
+
+// Right-to-left RQ sweep: each core becomes the orthonormal-row factor of its
+// transposed QR and the bond shrinks to min(rows, cols). With trim_only the
+// sweep stops at the first step that trims nothing (bonds further left are
+// then already within their bounds; the operator is the same either way).
+void rq_sweep(tt_fit* h, Prep& P, std::vector<double*>& X, std::vector<int>& bond, const std::vector<int>& dA,
+              const std::vector<int>& dB, int upto, bool trim_only) {
   const int L = (int)X.size();
   for (int j = L - 1; j >= upto; --j) {
     const int bl = bond[j], br = bond[j + 1], dd = dA[j] * dB[j];
     const int q = dd * br, p = bl, r = std::min(q, p);
+    if (trim_only && r == bl) break;
     // core j row-major (bl x q) == column-major q x bl: QR of X_j^T
-    CK(cudaMemcpyAsync(h->fX, X[j], sizeof(double) * (size_t)q * p, cudaMemcpyDeviceToDevice, h->st));
-    qr(h, q, p, h->fX, h->fQ, h->fR);
+    CK(cudaMemcpyAsync(P.X, X[j], sizeof(double) * (size_t)q * p, cudaMemcpyDeviceToDevice, P.st));
+    prep_qr(h, P, q, p);
     double* nc = h->pool.alloc<double>((size_t)r * q);
-    CK(cudaMemcpyAsync(nc, h->fQ, sizeof(double) * (size_t)q * r, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(nc, P.Q, sizeof(double) * (size_t)q * r, cudaMemcpyDeviceToDevice, P.st));
     if (j > 0) {
       const int bl2 = bond[j - 1], dd2 = dA[j - 1] * dB[j - 1];
       double* np = h->pool.alloc<double>((size_t)bl2 * dd2 * r);
@@ -199,37 +227,36 @@ void rq_sweep(tt_fit* h, std::vector<double*>& X, std::vector<int>& bond, const 
       g.A = X[j - 1];
       g.am = IdxMap::lin(bl);
       g.ak = IdxMap::lin(1);
-      g.B = h->fR;
+      g.B = P.R;
       g.bn = IdxMap::lin(1);
       g.bk = IdxMap::lin(r);
       g.b_kfast = false;
       g.C = np;
       g.cm = IdxMap::lin(r);
       g.cn = IdxMap::lin(1);
-      gemm<double>(h, g);
-      CK(cudaStreamSynchronize(h->st));
-      h->pool.release(X[j - 1]);
+      prep_gemm(h, P, g);
+      P.dead.push_back(X[j - 1]);
       X[j - 1] = np;
-    } else {
-      CK(cudaStreamSynchronize(h->st));
     }
-    h->pool.release(X[j]);
+    P.dead.push_back(X[j]);
     X[j] = nc;
     bond[j] = r;
   }
 }
 
 // Left-to-right QR sweep (Alg. 5 left_orthogonalize), bonds trimmed.
-void qr_sweep(tt_fit* h, std::vector<double*>& X, std::vector<int>& bond, const std::vector<int>& dA,
+void qr_sweep(tt_fit* h, Prep& P, std::vector<double*>& X, std::vector<int>& bond, const std::vector<int>& dA,
               const std::vector<int>& dB) {
   const int L = (int)X.size();
   for (int j = 0; j < L - 1; ++j) {
     const int bl = bond[j], br = bond[j + 1], dd = dA[j] * dB[j];
     const int q = bl * dd, p = br, r = std::min(q, p);
-    to_colmajor(h, q, p, X[j], h->fX);
-    qr(h, q, p, h->fX, h->fQ, h->fR);
+    CK(copy_map<double, double>(q, p, X[j], IdxMap::lin(p), IdxMap::lin(1), P.X, IdxMap::lin(1), IdxMap::lin(q), 1.0,
+                                P.st));
+    prep_qr(h, P, q, p);
     double* nc = h->pool.alloc<double>((size_t)q * r);
-    copymap<double, double>(h, q, r, h->fQ, IdxMap::lin(1), IdxMap::lin(q), nc, IdxMap::lin(r), IdxMap::lin(1));
+    CK(copy_map<double, double>(q, r, P.Q, IdxMap::lin(1), IdxMap::lin(q), nc, IdxMap::lin(r), IdxMap::lin(1), 1.0,
+                                P.st));
     const int dd2 = dA[j + 1] * dB[j + 1], br2 = bond[j + 2];
     const int N = dd2 * br2;
     double* nn = h->pool.alloc<double>((size_t)r * N);
@@ -237,7 +264,7 @@ void qr_sweep(tt_fit* h, std::vector<double*>& X, std::vector<int>& bond, const 
     g.M = r;
     g.N = N;
     g.K = br;
-    g.A = h->fR;
+    g.A = P.R;
     g.am = IdxMap::lin(1);
     g.ak = IdxMap::lin(r);
     g.a_kfast = false;
@@ -248,14 +275,37 @@ void qr_sweep(tt_fit* h, std::vector<double*>& X, std::vector<int>& bond, const 
     g.C = nn;
     g.cm = IdxMap::lin(N);
     g.cn = IdxMap::lin(1);
-    gemm<double>(h, g);
-    CK(cudaStreamSynchronize(h->st));
-    h->pool.release(X[j]);
-    h->pool.release(X[j + 1]);
+    prep_gemm(h, P, g);
+    P.dead.push_back(X[j]);
+    P.dead.push_back(X[j + 1]);
     X[j] = nc;
     X[j + 1] = nn;
     bond[j + 1] = r;
+    h->launches += 2;
   }
+}
+
+Prep make_prep(tt_fit* h, long long max_core) {
+  Prep P;
+  CK(cudaStreamCreateWithFlags(&P.st, cudaStreamNonBlocking));
+  P.X = h->pool.alloc<double>(max_core);
+  P.Q = h->pool.alloc<double>(max_core);
+  P.R = h->pool.alloc<double>(max_core);
+  P.ws_elems = (size_t)max_core * 16 + (1 << 20);
+  P.ws = h->pool.alloc<double>(P.ws_elems);
+  return P;
+}
+
+void finish_prep(tt_fit* h, Prep& P) {
+  CK(cudaStreamSynchronize(P.st));
+  for (void* d : P.dead) h->pool.release(d);
+  h->pool.release(P.X);
+  h->pool.release(P.Q);
+  h->pool.release(P.R);
+  h->pool.release(P.ws);
+  P.dead.clear();
+  cudaStreamDestroy(P.st);
+  P.st = nullptr;
 }
 
 void check_errw(tt_fit* h, const char* where) {
@@ -515,6 +565,94 @@ int factorize(tt_fit* h, int m, int n, int sweep, int site1) {
   return p;
 }
 
+// ---------------------------------------------------------------------------
+// Gauge update of the non-FP64 paths. The FP32 factorisation gives singular
+// vectors accurate to the FP32 level; one Newton-Schulz step in FP64,
+// X <- X (3 I - X^T X) / 2, makes the kept ones an isometry to ~1e-12, and the
+// other factor is the projection of the two-site tensor on it (the optimal
+// factor for that isometry, Eq. fit_pde). Because ||C||^2 is stationary under
+// small rotations of the kept subspace, the FP32 rounding of the subspace
+// enters ||C||^2 only at second order. Writes ||C_window||^2 to dn2[l].
+// ---------------------------------------------------------------------------
+template <typename T>
+void ns_orthonormalize(tt_fit* h, const T* X32, int rows, int k, double* X64) {
+  double* G = h->pG;
+  copymap<T, double>(h, rows, k, X32, IdxMap::lin(1), IdxMap::lin(rows), h->pT, IdxMap::lin(1), IdxMap::lin(rows));
+  GemmArgs<double> g;  // G = X^T X (k x k)
+  g.M = k; g.N = k; g.K = rows;
+  g.A = h->pT; g.am = IdxMap::lin(rows); g.ak = IdxMap::lin(1);
+  g.B = h->pT; g.bn = IdxMap::lin(rows); g.bk = IdxMap::lin(1);
+  g.C = G; g.cm = IdxMap::lin(k); g.cn = IdxMap::lin(1);
+  gemm<double>(h, g);
+  CK(cudaMemcpyAsync(X64, h->pT, sizeof(double) * (size_t)rows * k, cudaMemcpyDeviceToDevice, h->st));
+  GemmArgs<double> g2;  // X64 = 1.5 X - 0.5 X G
+  g2.M = rows; g2.N = k; g2.K = k;
+  g2.A = h->pT; g2.am = IdxMap::lin(1); g2.ak = IdxMap::lin(rows); g2.a_kfast = false;
+  g2.B = G; g2.bn = IdxMap::lin(k); g2.bk = IdxMap::lin(1);
+  g2.C = X64; g2.cm = IdxMap::lin(1); g2.cn = IdxMap::lin(rows);
+  g2.alpha = -0.5;
+  g2.beta = 1.5;
+  gemm<double>(h, g2);
+}
+
+template <typename T>
+void polish_update(tt_fit* h, int mode, int m, int n, int k, int l) {
+  const T* Th = (const T*)h->Th;
+  T* Ut = (T*)h->Ut[l];
+  T* Vt = (T*)h->Vt[l + 1];
+  T* P = (T*)h->pP;  // m x k (or k x n) projection, then the k x k block
+  const int side = std::max(m, n);
+  if (mode != 1) {  // left isometry U (m x k)
+    ns_orthonormalize<T>(h, (const T*)h->fUM, m, k, h->pU);
+    // Ut (k x m row-major) = U^T : same memory order as U column-major
+    copymap<double, T>(h, 1, m * k, h->pU, IdxMap::lin(0), IdxMap::lin(1), Ut, IdxMap::lin(0), IdxMap::lin(1));
+  }
+  if (mode != 0) {  // right isometry V (n x k)
+    ns_orthonormalize<T>(h, (const T*)h->fVM, n, k, h->pV);
+    copymap<double, T>(h, 1, n * k, h->pV, IdxMap::lin(0), IdxMap::lin(1), Vt, IdxMap::lin(0), IdxMap::lin(1));
+  }
+  if (mode == 0) {  // site, forward: C_l = U, C_{l+1} = U^T Theta
+    copymap<double, double>(h, m, k, h->pU, IdxMap::lin(1), IdxMap::lin(m), h->C64[l], IdxMap::lin(k), IdxMap::lin(1));
+    GemmArgs<T> g;
+    g.M = k; g.N = n; g.K = m;
+    g.A = Ut; g.am = IdxMap::lin(m); g.ak = IdxMap::lin(1);
+    g.B = Th; g.bn = IdxMap::lin(1); g.bk = IdxMap::lin(n); g.b_kfast = false;
+    g.C = P; g.cm = IdxMap::lin(n); g.cn = IdxMap::lin(1);
+    gemm<T>(h, g);
+    copymap<T, double>(h, 1, k * n, P, IdxMap::lin(0), IdxMap::lin(1), h->C64[l + 1], IdxMap::lin(0), IdxMap::lin(1));
+    CK(frob_norm<T>(P, (long long)k * n, h->dn2 + l, nullptr, h->st));
+  } else if (mode == 1) {  // site, backward: C_{l+1} = V^T, C_l = Theta V
+    copymap<double, double>(h, 1, n * k, h->pV, IdxMap::lin(0), IdxMap::lin(1), h->C64[l + 1], IdxMap::lin(0),
+                            IdxMap::lin(1));
+    GemmArgs<T> g;
+    g.M = m; g.N = k; g.K = n;
+    g.A = Th; g.am = IdxMap::lin(n); g.ak = IdxMap::lin(1);
+    g.B = Vt; g.bn = IdxMap::lin(n); g.bk = IdxMap::lin(1);
+    g.C = P; g.cm = IdxMap::lin(k); g.cn = IdxMap::lin(1);
+    gemm<T>(h, g);
+    copymap<T, double>(h, 1, m * k, P, IdxMap::lin(0), IdxMap::lin(1), h->C64[l], IdxMap::lin(0), IdxMap::lin(1));
+    CK(frob_norm<T>(P, (long long)m * k, h->dn2 + l, nullptr, h->st));
+  } else {  // inverse: Psi_l = U s, Psi_{l+1} = s V^T, Y_l = 1/s with s = diag(U^T Theta V)
+    GemmArgs<T> g;  // X = Theta V (m x k)
+    g.M = m; g.N = k; g.K = n;
+    g.A = Th; g.am = IdxMap::lin(n); g.ak = IdxMap::lin(1);
+    g.B = Vt; g.bn = IdxMap::lin(n); g.bk = IdxMap::lin(1);
+    g.C = P; g.cm = IdxMap::lin(k); g.cn = IdxMap::lin(1);
+    gemm<T>(h, g);
+    T* Pk = P + (size_t)side * k;
+    GemmArgs<T> g2;  // Pk = U^T X (k x k)
+    g2.M = k; g2.N = k; g2.K = m;
+    g2.A = Ut; g2.am = IdxMap::lin(m); g2.ak = IdxMap::lin(1);
+    g2.B = P; g2.bn = IdxMap::lin(1); g2.bk = IdxMap::lin(k); g2.b_kfast = false;
+    g2.C = Pk; g2.cm = IdxMap::lin(k); g2.cn = IdxMap::lin(1);
+    gemm<T>(h, g2);
+    CK(inverse_gauge_update<T>(m, n, k, h->pU, h->pV, Pk, h->C64[l], h->C64[l + 1], h->Y[l + 1], h->st));
+    CK(frob_norm<T>(Pk, (long long)k * k, h->dn2 + l, nullptr, h->st));
+    h->launches += 2;
+  }
+  h->launches += 1;
+}
+
 template <typename T>
 struct Sweeper {
   tt_fit* h;
@@ -583,9 +721,13 @@ struct Sweeper {
     // gauge update (Alg. 3 / Alg. 4)
     const int mode = (h->gauge == TT_GAUGE_INVERSE_CANONICAL) ? 2 : (fwd ? 0 : 1);
     CK(cudaEventRecord(h->ev[5], h->st));
-    CK(gauge_update<T, T>(mode, m, n, (const T*)h->fUM, m, (const T*)h->fS, (const T*)h->fVM, n, h->dk, h->C64[l],
-                          h->C64[l + 1], h->Y[l + 1], (T*)h->Ut[l], (T*)h->Vt[l + 1], h->st));
-    h->launches += 1;
+    if (h->precision == TT_PREC_FP64) {
+      CK(gauge_update<T, T>(mode, m, n, (const T*)h->fUM, m, (const T*)h->fS, (const T*)h->fVM, n, h->dk, h->C64[l],
+                            h->C64[l + 1], h->Y[l + 1], (T*)h->Ut[l], (T*)h->Vt[l + 1], h->st));
+      h->launches += 1;
+    } else {
+      polish_update<T>(h, mode, m, n, k, l);
+    }
     CK(cudaEventRecord(h->ev[6], h->st));
     h->gauge_pending = true;
     // host copy of the kept spectrum for tt_fit_result
@@ -613,6 +755,12 @@ struct Sweeper {
       }
       CK(cudaStreamSynchronize(h->st));
       resolve_gauge();
+      if (h->precision != TT_PREC_FP64) {  // ||C||^2 from the FP64-orthonormal projection of the last window
+        const int lw = h->forward ? L - 2 : 0;
+        double nr = 0;
+        CK(cudaMemcpy(&nr, h->dn2 + lw, sizeof(double), cudaMemcpyDeviceToHost));
+        n2 = nr * nr;
+      }
       h->delta = (h->last_n2 >= 0 && n2 > 0) ? std::fabs(n2 - h->last_n2) / n2 : INFINITY;
       h->last_n2 = n2;
       h->max_disc = maxd;
@@ -755,6 +903,12 @@ void allocate_chain(tt_fit* h) {
   h->fBt = h->pool.alloc<double>(h->fsz);
   h->fQ2 = h->pool.alloc<double>(h->fsz);
   h->fR2 = h->pool.alloc<double>(h->fsz);
+  h->pU = h->pool.alloc<double>(h->fsz);
+  h->pV = h->pool.alloc<double>(h->fsz);
+  h->pG = h->pool.alloc<double>(h->fsz);
+  h->pT = h->pool.alloc<double>(h->fsz);
+  h->pP = h->pool.alloc<double>((size_t)side * ks + (size_t)ks * ks + 64);
+  h->dn2 = h->pool.alloc<double>(L + 1);
 }
 
 template <typename T>
@@ -848,7 +1002,7 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
       o = *opt;
     }
     if (o.update != 0 && o.update != 1) return TT_ERR_INVALID_ARGUMENT;
-    if (o.precision < 0 || o.precision > 3 || o.oversample < 0) return TT_ERR_INVALID_ARGUMENT;
+    if (o.precision < 0 || o.precision > 4 || o.oversample < 0) return TT_ERR_INVALID_ARGUMENT;
     if (o.init < 0 || o.init > 2 || (o.init == TT_INIT_GIVEN && !o.init_C)) return TT_ERR_INVALID_ARGUMENT;
     if (o.precision == TT_PREC_BF16_SPLIT) return TT_ERR_INVALID_ARGUMENT;  // not in this build
     int LA, LB;
@@ -884,8 +1038,8 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
     h->pool.ptrs.push_back(h->dnorm);
     h->dk = h->pool.alloc<int>(4);
     h->ddinfo = h->pool.alloc<double>(4);
-    h->errw = h->pool.alloc<uint32_t>(1);
-    CK(cudaMemsetAsync(h->errw, 0, sizeof(uint32_t), h->st));
+    h->errw = h->pool.alloc<uint32_t>(4);  // [0] error bits, [1] max Jacobi sweeps (diagnostic)
+    CK(cudaMemsetAsync(h->errw, 0, 4 * sizeof(uint32_t), h->st));
     for (auto& e : h->ev) CK(cudaEventCreate(&e));
     CK(cudaMallocHost(&h->hk, sizeof(int) * 4));
     CK(cudaMallocHost(&h->hdinfo, sizeof(double) * 4));
@@ -901,29 +1055,24 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
     upload(h, A, doA, diA, bA, h->A64);
     upload(h, B, doB, diB, bB, h->B64);
     CK(cudaStreamSynchronize(h->st));
-    {  // scratch of the input / guess canonicalisation sweeps (released before the chain is allocated)
-      long long mc = 1;
-      for (int l = 0; l < LA; ++l) {
-        mc = std::max(mc, prodll({bA[l], doA[l], diA[l], bA[l + 1]}));
-        mc = std::max(mc, prodll({bB[l], doB[l], diB[l], bB[l + 1]}));
-      }
-      if (o.init == TT_INIT_GIVEN) {
-        const tt_mpo_desc* g = o.init_C;
-        if (g->L == LA && g->bond && g->d_out && g->d_in)
-          for (int l = 0; l < LA; ++l)
-            mc = std::max(mc, prodll({g->bond[l], g->d_out[l], g->d_in[l], g->bond[l + 1]}));
-      }
-      h->fX = h->pool.alloc<double>(mc);
-      h->fQ = h->pool.alloc<double>(mc);
-      h->fR = h->pool.alloc<double>(mc);
-      h->gws_elems = (size_t)mc * 16 + (1 << 20);
-      h->gws = h->pool.alloc<double>(h->gws_elems);
+    long long mc = 1;  // largest core of A, B (and a given guess): scratch of the preparation sweeps
+    for (int l = 0; l < LA; ++l) {
+      mc = std::max(mc, prodll({bA[l], doA[l], diA[l], bA[l + 1]}));
+      mc = std::max(mc, prodll({bB[l], doB[l], diB[l], bB[l + 1]}));
     }
-    if (o.prepare_inputs) {  // Alg. 5: left_orthogonalize(A), left_orthogonalize(B)
-      rq_sweep(h, h->A64, D.a, D.ds, D.du, 1);
-      qr_sweep(h, h->A64, D.a, D.ds, D.du);
-      rq_sweep(h, h->B64, D.b, D.du, D.dt, 1);
-      qr_sweep(h, h->B64, D.b, D.du, D.dt);
+    if (o.init == TT_INIT_GIVEN) {
+      const tt_mpo_desc* g = o.init_C;
+      if (g->L == LA && g->bond && g->d_out && g->d_in)
+        for (int l = 0; l < LA; ++l) mc = std::max(mc, prodll({g->bond[l], g->d_out[l], g->d_in[l], g->bond[l + 1]}));
+    }
+    if (o.prepare_inputs) {  // Alg. 5: left_orthogonalize(A), left_orthogonalize(B), concurrently
+      Prep PA = make_prep(h, mc), PB = make_prep(h, mc);
+      rq_sweep(h, PA, h->A64, D.a, D.ds, D.du, 1, true);
+      rq_sweep(h, PB, h->B64, D.b, D.du, D.dt, 1, true);
+      qr_sweep(h, PA, h->A64, D.a, D.ds, D.du);
+      qr_sweep(h, PB, h->B64, D.b, D.du, D.dt);
+      finish_prep(h, PA);
+      finish_prep(h, PB);
     }
     // capacity of C bonds: min(chi_max, prod of local dims to the left / right)
     const int L = LA;
@@ -939,22 +1088,34 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
     std::vector<int> cbond;
     if (o.init == TT_INIT_RANDOM) {
       cbond = D.cb;
+      // core l >= 2: orthonormal-row factor of a Gaussian matrix; the cores are
+      // independent, so their QRs run concurrently on a pool of streams
+      const int NS = 8;
+      cudaStream_t pool[NS];
+      for (auto& x : pool) CK(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+      std::vector<void*> dead;
+      CK(cudaStreamSynchronize(h->st));
       for (int j = 0; j < L; ++j) {
+        cudaStream_t sj = pool[j % NS];
         const long long n = prodll({cbond[j], D.ds[j], D.dt[j], cbond[j + 1]});
         C0[j] = h->pool.alloc<double>(n);
-        CK(philox_fill<double>(C0[j], n, h->seed, init_stream(j + 1), 1.0, h->st));
-        if (j > 0) {  // orthonormal rows: QR of the transposed core (q >= p by the bond rule)
+        CK(philox_fill<double>(C0[j], n, h->seed, init_stream(j + 1), 1.0, sj));
+        if (j > 0) {  // q >= p by the bond rule
           const int q = D.ds[j] * D.dt[j] * cbond[j + 1], p = cbond[j];
           double* R = h->pool.alloc<double>((size_t)p * p);
           double* Q = h->pool.alloc<double>((size_t)q * p);
-          qr(h, q, p, C0[j], Q, R);
-          CK(cudaStreamSynchronize(h->st));
-          h->pool.release(C0[j]);
-          h->pool.release(R);
+          CK(qr_householder<double, double>(q, p, C0[j], Q, R, sj));
+          h->launches += 2;
+          dead.push_back(C0[j]);
+          dead.push_back(R);
           C0[j] = Q;
         }
       }
-      CK(cudaStreamSynchronize(h->st));
+      for (auto& x : pool) {
+        CK(cudaStreamSynchronize(x));
+        cudaStreamDestroy(x);
+      }
+      for (void* d : dead) h->pool.release(d);
     } else {
       std::vector<int> dz, bz;
       const tt_mpo_desc* src = (o.init == TT_INIT_COPY_B) ? nullptr : o.init_C;
@@ -977,17 +1138,16 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
         }
         if (D.du != D.ds) throw TTError(TT_ERR_SHAPE_MISMATCH, "TT_INIT_COPY_B needs A.d_out == B.d_out");
       }
-      qr_sweep(h, G, bz, D.ds, D.dt);
-      rq_sweep(h, G, bz, D.ds, D.dt, 1);
+      CK(cudaStreamSynchronize(h->st));
+      Prep PC = make_prep(h, mc);
+      qr_sweep(h, PC, G, bz, D.ds, D.dt);
+      rq_sweep(h, PC, G, bz, D.ds, D.dt, 1, false);
+      finish_prep(h, PC);
       for (int l = 1; l < L; ++l) D.cb[l] = std::max(D.cb[l], bz[l]);
       C0 = G;
       cbond = bz;
     }
     D.c = cbond;
-    h->pool.release(h->fX);
-    h->pool.release(h->fQ);
-    h->pool.release(h->fR);
-    h->pool.release(h->gws);
     if (h->use_f32) setup<float>(h, C0);
     else setup<double>(h, C0);
     for (int j = 0; j < L; ++j) h->pool.release(C0[j]);

@@ -29,9 +29,14 @@ namespace ttfit {
 namespace tc {
 
 constexpr int BM = 128, BN = 128, BK = 32;  // BK fp32 elements = 128 bytes = one swizzle span
-constexpr int STAGES = 4;
 constexpr int TILE_BYTES = BM * BK * 4;     // 16 KB (A); B tile has the same size
-constexpr int SMEM_BYTES = STAGES * 2 * TILE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+// 1-pass TF32: 4 stages of (A, B); split (3xTF32): 3 stages of (A, B, A_lo, B_lo)
+template <bool SPLIT>
+struct Cfg {
+  static constexpr int STAGES = SPLIT ? 3 : 4;
+  static constexpr int TILES = SPLIT ? 4 : 2;
+  static constexpr int SMEM_BYTES = STAGES * TILES * TILE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+};
 constexpr long long WAIT_LIMIT = 1ll << 26;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -98,18 +103,21 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int m, int n, bool b_mn_major)
          ((uint32_t)(m >> 4) << 24);
 }
 
-template <bool B_MN>
+template <bool B_MN, bool SPLIT>
 __global__ void __launch_bounds__(128, 1)
     gemm_tf32_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
                      int K, int k_per_split, float* __restrict__ C, IdxMap cm, IdxMap cn, float alpha, float beta,
                      float* __restrict__ C2, IdxMap cm2, IdxMap cn2, float* __restrict__ ws, uint32_t* errw) {
+  constexpr int STAGES = Cfg<SPLIT>::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
   uint8_t* sB = smem + STAGES * TILE_BYTES;
-  uint64_t* bars = (uint64_t*)(smem + STAGES * 2 * TILE_BYTES);
-  // bars[0..S-1] full, bars[S..2S-1] empty, bars[2S] accumulator ready
-  uint32_t* tmem_slot = (uint32_t*)(bars + 2 * STAGES + 1);
+  uint8_t* sAl = smem + 2 * STAGES * TILE_BYTES;  // split only: low parts, same swizzled layout
+  uint8_t* sBl = smem + 3 * STAGES * TILE_BYTES;
+  uint64_t* bars = (uint64_t*)(smem + STAGES * Cfg<SPLIT>::TILES * TILE_BYTES);
+  // bars[0..S-1] full, [S..2S-1] empty, [2S] accumulator ready, [2S+1..3S] split done
+  uint32_t* tmem_slot = (uint32_t*)(bars + 3 * STAGES + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -123,6 +131,7 @@ __global__ void __launch_bounds__(128, 1)
       mbar_init(su32(&bars[STAGES + s]), 1);
     }
     mbar_init(su32(&bars[2 * STAGES]), 1);
+    for (int s = 0; s < STAGES; ++s) mbar_init(su32(&bars[2 * STAGES + 1 + s]), 2);  // two splitter warps
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
@@ -169,7 +178,8 @@ __global__ void __launch_bounds__(128, 1)
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES;
       const uint32_t ph = (kb / STAGES) & 1;
-      if (*abort_flag || !mbar_wait(su32(&bars[s]), ph)) {
+      const uint32_t ready = SPLIT ? su32(&bars[2 * STAGES + 1 + s]) : su32(&bars[s]);
+      if (*abort_flag || !mbar_wait(ready, ph)) {
         *abort_flag = 1;
         ok = false;
         break;
@@ -185,10 +195,53 @@ __global__ void __launch_bounds__(128, 1)
         if (B_MN) bd = sdesc(b_base + kk * 1024, BK * 128, 1024);  // 8 k-rows per step; LBO = n-chunk stride
         else bd = sdesc(b_base + kk * 32, 16, 1024);
         mma_tf32(tmem, ad, bd, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+        if (SPLIT) {  // + A_hi B_lo + A_lo B_hi (the tensor core truncates A, B to their TF32 high parts)
+          const uint64_t bdl = sdesc(su32(sBl + s * TILE_BYTES) + kk * 32, 16, 1024);
+          const uint64_t adl = sdesc(su32(sAl + s * TILE_BYTES) + kk * 32, 16, 1024);
+          mma_tf32(tmem, ad, bdl, idesc, 1u);
+          mma_tf32(tmem, adl, bd, idesc, 1u);
+        }
       }
       mma_commit(su32(&bars[STAGES + s]));  // frees the stage once these MMAs have read it
     }
     if (ok) mma_commit(su32(&bars[2 * STAGES]));
+  } else if (SPLIT && warp >= 2) {
+    // ---------------- splitters: lo = x - tf32(x) for the A and B tiles of each stage
+    const int t = threadIdx.x - 64;  // 0..63
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (kb / STAGES) & 1;
+      if (*abort_flag || !mbar_wait(su32(&bars[s]), ph)) {
+        *abort_flag = 1;
+        break;
+      }
+      const uint4* a = (const uint4*)(sA + s * TILE_BYTES);
+      const uint4* b = (const uint4*)(sB + s * TILE_BYTES);
+      float4* al = (float4*)(sAl + s * TILE_BYTES);
+      float4* bl = (float4*)(sBl + s * TILE_BYTES);
+#pragma unroll 4
+      for (int i = t; i < TILE_BYTES / 16; i += 64) {
+        const uint4 x = a[i], y = b[i];
+        float4 xl, yl;
+        xl.x = __uint_as_float(x.x) - __uint_as_float(x.x & 0xFFFFE000u);
+        xl.y = __uint_as_float(x.y) - __uint_as_float(x.y & 0xFFFFE000u);
+        xl.z = __uint_as_float(x.z) - __uint_as_float(x.z & 0xFFFFE000u);
+        xl.w = __uint_as_float(x.w) - __uint_as_float(x.w & 0xFFFFE000u);
+        yl.x = __uint_as_float(y.x) - __uint_as_float(y.x & 0xFFFFE000u);
+        yl.y = __uint_as_float(y.y) - __uint_as_float(y.y & 0xFFFFE000u);
+        yl.z = __uint_as_float(y.z) - __uint_as_float(y.z & 0xFFFFE000u);
+        yl.w = __uint_as_float(y.w) - __uint_as_float(y.w & 0xFFFFE000u);
+        al[i] = xl;
+        bl[i] = yl;
+      }
+      // generic-proxy writes -> visible to the tensor core (async proxy)
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if ((threadIdx.x & 31) == 0) {
+        uint64_t st;
+        asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(st) : "r"(su32(&bars[2 * STAGES + 1 + s])) : "memory");
+      }
+    }
   }
   __syncwarp();
   // ---------------- epilogue: all four warps, warp w owns accumulator rows 32w..32w+31
@@ -296,7 +349,7 @@ inline bool lin_stride(const IdxMap& m, long long& s) {
 // Returns cudaErrorNotSupported when the operand layouts cannot be fed by TMA
 // (the caller then uses the CUDA-core kernel).
 cudaError_t gemm_tf32(const GemmArgs<float>& g, float* ws, size_t ws_elems, int sm_count, uint32_t* errw,
-                      cudaStream_t st) {
+                      cudaStream_t st, bool split) {
   using namespace tc;
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
   long long lda, ldb, one;
@@ -316,15 +369,11 @@ cudaError_t gemm_tf32(const GemmArgs<float>& g, float* ws, size_t ws_elems, int 
   } else {
     if (!make_map(&tb, g.B, (uint64_t)g.N, (uint64_t)g.K, (uint64_t)ldb, 32, BK)) return cudaErrorNotSupported;
   }
-  static bool attr_set[2] = {false, false};
-  if (!attr_set[b_mn]) {
-    cudaError_t e = b_mn ? cudaFuncSetAttribute(gemm_tf32_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                SMEM_BYTES)
-                         : cudaFuncSetAttribute(gemm_tf32_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr_set[b_mn] = true;
-  }
+  cudaError_t ea = split ? cudaFuncSetAttribute(gemm_tf32_kernel<false, true>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<true>::SMEM_BYTES)
+                         : cudaFuncSetAttribute(gemm_tf32_kernel<false, false>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<false>::SMEM_BYTES);
+  if (ea != cudaSuccess) return ea;
   const int gm = (g.M + BM - 1) / BM, gn = (g.N + BN - 1) / BN;
   int splits = 1;
   while (gm * gn * splits < sm_count && g.K / (splits * 2) >= 4 * BK && (size_t)(splits * 2) * g.M * g.N <= ws_elems)
@@ -334,12 +383,12 @@ cudaError_t gemm_tf32(const GemmArgs<float>& g, float* ws, size_t ws_elems, int 
   splits = (g.K + kps - 1) / kps;
   dim3 grid(gn, gm, splits);
   float* wsp = splits > 1 ? ws : nullptr;
-  if (b_mn)
-    gemm_tf32_kernel<true><<<grid, 128, SMEM_BYTES, st>>>(ta, tb, g.M, g.N, g.K, kps, g.C, g.cm, g.cn, g.alpha,
-                                                           g.beta, g.C2, g.cm2, g.cn2, wsp, errw);
+  if (split)
+    gemm_tf32_kernel<false, true><<<grid, 128, Cfg<true>::SMEM_BYTES, st>>>(
+        ta, tb, g.M, g.N, g.K, kps, g.C, g.cm, g.cn, g.alpha, g.beta, g.C2, g.cm2, g.cn2, wsp, errw);
   else
-    gemm_tf32_kernel<false><<<grid, 128, SMEM_BYTES, st>>>(ta, tb, g.M, g.N, g.K, kps, g.C, g.cm, g.cn, g.alpha,
-                                                            g.beta, g.C2, g.cm2, g.cn2, wsp, errw);
+    gemm_tf32_kernel<false, false><<<grid, 128, Cfg<false>::SMEM_BYTES, st>>>(
+        ta, tb, g.M, g.N, g.K, kps, g.C, g.cm, g.cn, g.alpha, g.beta, g.C2, g.cm2, g.cn2, wsp, errw);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || splits == 1) return e;
   return splitk_reduce<float>(g, ws, splits, sm_count, st);

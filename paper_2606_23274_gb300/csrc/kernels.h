@@ -31,9 +31,10 @@ template <typename T>
 cudaError_t splitk_reduce(const GemmArgs<T>& g, const T* ws, int splits, int sm_count, cudaStream_t st);
 
 // Tensor-core (tcgen05, kind::tf32) GEMM; cudaErrorNotSupported when the operand
-// layouts cannot be loaded by TMA (A K-major; B K-major or MN-major; 16-byte rows).
+// layouts cannot be loaded by TMA (A and B K-major, 16-byte aligned rows).
+// split = true: 3xTF32 (hi*hi + hi*lo + lo*hi, about FP32 accuracy).
 cudaError_t gemm_tf32(const GemmArgs<float>& g, float* ws, size_t ws_elems, int sm_count, uint32_t* errw,
-                      cudaStream_t st);
+                      cudaStream_t st, bool split = false);
 
 // out[om(i) + on(j)] = (Tout) (scale * in[im(i) + in_(j)]), i < rows, j < cols
 template <typename Tin, typename Tout>
@@ -83,6 +84,11 @@ cudaError_t gauge_update(int mode, int m, int n, const F* U, int ld_u, const F* 
 // positive (U: m x p col-major ld_u; V: n x p col-major ld_v).
 template <typename F>
 cudaError_t fix_signs(int m, int n, int p, F* U, int ld_u, F* V, int ld_v, cudaStream_t st);
+
+// Alg. 4 from FP64 isometries and P = U^T Theta V (see linalg.cu)
+template <typename T>
+cudaError_t inverse_gauge_update(int m, int n, int k, const double* U, const double* V, const T* P, double* Cl,
+                                 double* Cr, double* Y, cudaStream_t st);
 
 // out (rows x cols, row-major) = in * diag(y) (y == nullptr: plain copy)
 cudaError_t scale_cols(int rows, int cols, const double* in, const double* y, double* out, cudaStream_t st);

@@ -23,71 +23,104 @@ __device__ __forceinline__ C block_sum(C v, C* red) {
 
 // ---------------------------------------------------------------------------
 // Householder QR, one CTA. X: q x p column-major (ld q), overwritten by the
-// reflectors (unit vectors, rows j..q-1 of column j). Q: q x r, R: r x p.
+// reflectors (unit vectors, rows j..q-1 of column j). Q: q x r, R: r x p,
+// r = min(q, p), diag(R) >= 0. The current reflector sits in shared memory;
+// each warp updates two trailing columns at a time, caching their RM rows per
+// lane in registers between the dot product and the update (q <= 32 RM).
+// All arithmetic is in C (no FP64 in the FP32 instantiation).
 // ---------------------------------------------------------------------------
-template <typename C, typename S>
+template <typename C, typename S, int RM>
+__device__ __forceinline__ void reflect_two(const C* __restrict__ v, int j, int q, S* xa, S* xb) {
+  const int lane = threadIdx.x & 31;
+  C ra[RM], rb[RM];
+  C da = 0, db = 0;
+#pragma unroll
+  for (int t = 0; t < RM; ++t) {
+    const int i = j + lane + 32 * t;
+    const bool in = i < q;
+    ra[t] = in ? (C)xa[i] : C(0);
+    rb[t] = (in && xb) ? (C)xb[i] : C(0);
+  }
+#pragma unroll
+  for (int t = 0; t < RM; ++t) {
+    const int i = j + lane + 32 * t;
+    const C vi = (i < q) ? v[i] : C(0);
+    da += ra[t] * vi;
+    db += rb[t] * vi;
+  }
+  da = warp_sum(da);
+  db = warp_sum(db);
+#pragma unroll
+  for (int t = 0; t < RM; ++t) {
+    const int i = j + lane + 32 * t;
+    if (i < q) {
+      const C vi = v[i];
+      xa[i] = (S)(ra[t] - C(2) * da * vi);
+      if (xb) xb[i] = (S)(rb[t] - C(2) * db * vi);
+    }
+  }
+}
+
+template <typename C, typename S, int RM>
 __global__ void __launch_bounds__(1024) qr_house_kernel(int q, int p, S* __restrict__ X, S* __restrict__ Q,
                                                         S* __restrict__ R) {
   __shared__ C red[32];
-  __shared__ double diag[1024];  // r <= 1024
+  __shared__ C diag[1024];  // r <= 1024
+  __shared__ C v[32 * RM];  // current reflector
   const int r = min(q, p);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int j = 0; j < r; ++j) {
     S* xj = X + (size_t)j * q;
     C ss = 0;
-    for (int i = j + threadIdx.x; i < q; i += blockDim.x) {
-      C v = (C)xj[i];
-      ss += v * v;
+    for (int i = threadIdx.x; i < q; i += blockDim.x) {
+      const C t = (i >= j) ? (C)xj[i] : C(0);
+      v[i] = t;
+      ss += t * t;
     }
     ss = block_sum(ss, red);
-    const C x0 = (C)xj[j];
+    const C x0 = v[j];
     const C nrm = sqrt(ss);
     const C alpha = (x0 >= C(0)) ? -nrm : nrm;
     const C v0 = x0 - alpha;
     const C vn2 = ss - x0 * x0 + v0 * v0;
-    __syncthreads();
     const bool zero = !(vn2 > C(0));
     const C inv = zero ? C(0) : C(1) / sqrt(vn2);
-    for (int i = j + threadIdx.x; i < q; i += blockDim.x) xj[i] = (S)((i == j ? v0 : (C)xj[i]) * inv);
-    if (threadIdx.x == 0) diag[j] = zero ? 0.0 : (double)alpha;
+    __syncthreads();
+    for (int i = j + threadIdx.x; i < q; i += blockDim.x) {
+      const C t = (i == j ? v0 : v[i]) * inv;
+      v[i] = t;
+      xj[i] = (S)t;
+    }
+    if (threadIdx.x == 0) diag[j] = zero ? C(0) : alpha;
     __syncthreads();
     if (!zero) {
-      for (int c = j + 1 + warp; c < p; c += nw) {
-        S* xc = X + (size_t)c * q;
-        C d = 0;
-        for (int i = j + lane; i < q; i += 32) d += (C)xj[i] * (C)xc[i];
-        d = warp_sum(d);
-        for (int i = j + lane; i < q; i += 32) xc[i] = (S)((C)xc[i] - C(2) * d * (C)xj[i]);
-      }
+      for (int c = j + 1 + 2 * warp; c < p; c += 2 * nw)
+        reflect_two<C, S, RM>(v, j, q, X + (size_t)c * q, (c + 1 < p) ? X + (size_t)(c + 1) * q : nullptr);
     }
     __syncthreads();
   }
   // R (r x p, col-major, ld r)
   for (long long e = threadIdx.x; e < (long long)r * p; e += blockDim.x) {
-    int i = (int)(e % r), c = (int)(e / r);
-    double v = (i < c) ? (double)X[(size_t)c * q + i] : (i == c ? diag[i] : 0.0);
-    R[(size_t)c * r + i] = (S)v;
+    const int i = (int)(e % r), c = (int)(e / r);
+    R[(size_t)c * r + i] = (i < c) ? X[(size_t)c * q + i] : (i == c ? (S)diag[i] : S(0));
   }
   // Q = H_0 ... H_{r-1} [I_r; 0]
   for (long long e = threadIdx.x; e < (long long)q * r; e += blockDim.x) {
-    int i = (int)(e % q), c = (int)(e / q);
+    const int i = (int)(e % q), c = (int)(e / q);
     Q[(size_t)c * q + i] = (i == c) ? S(1) : S(0);
   }
   __syncthreads();
   for (int j = r - 1; j >= 0; --j) {
-    const S* vj = X + (size_t)j * q;
-    for (int c = j + warp; c < r; c += nw) {
-      S* qc = Q + (size_t)c * q;
-      C d = 0;
-      for (int i = j + lane; i < q; i += 32) d += (C)vj[i] * (C)qc[i];
-      d = warp_sum(d);
-      for (int i = j + lane; i < q; i += 32) qc[i] = (S)((C)qc[i] - C(2) * d * (C)vj[i]);
-    }
+    for (int i = threadIdx.x; i < q; i += blockDim.x) v[i] = (i >= j) ? (C)X[(size_t)j * q + i] : C(0);
+    __syncthreads();
+    for (int c = j + 2 * warp; c < r; c += 2 * nw)
+      reflect_two<C, S, RM>(v, j, q, Q + (size_t)c * q, (c + 1 < r) ? Q + (size_t)(c + 1) * q : nullptr);
     __syncthreads();
   }
   // sign convention diag(R) >= 0
+  const int lane = threadIdx.x & 31;
   for (int j = warp; j < r; j += nw) {
-    if (diag[j] < 0.0) {
+    if (diag[j] < C(0)) {
       for (int c = j + lane; c < p; c += 32) R[(size_t)c * r + j] = -R[(size_t)c * r + j];
       for (int i = lane; i < q; i += 32) Q[(size_t)j * q + i] = -Q[(size_t)j * q + i];
     }
@@ -97,12 +130,15 @@ __global__ void __launch_bounds__(1024) qr_house_kernel(int q, int p, S* __restr
 template <typename C, typename S>
 cudaError_t qr_householder(int q, int p, S* X, S* Q, S* R, cudaStream_t st) {
   if (q <= 0 || p <= 0) return cudaSuccess;
-  if (q > 1 << 20 || min(q, p) > 1024) return cudaErrorInvalidValue;
-  qr_house_kernel<C, S><<<1, 1024, 0, st>>>(q, p, X, Q, R);
+  if (min(q, p) > 1024) return cudaErrorInvalidValue;
+  if (q <= 128) qr_house_kernel<C, S, 4><<<1, 1024, 0, st>>>(q, p, X, Q, R);
+  else if (q <= 256) qr_house_kernel<C, S, 8><<<1, 1024, 0, st>>>(q, p, X, Q, R);
+  else if (q <= 512) qr_house_kernel<C, S, 16><<<1, 1024, 0, st>>>(q, p, X, Q, R);
+  else if (q <= 1024) qr_house_kernel<C, S, 32><<<1, 1024, 0, st>>>(q, p, X, Q, R);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 template cudaError_t qr_householder<double, double>(int, int, double*, double*, double*, cudaStream_t);
-template cudaError_t qr_householder<float, double>(int, int, double*, double*, double*, cudaStream_t);
 template cudaError_t qr_householder<float, float>(int, int, float*, float*, float*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
@@ -121,14 +157,14 @@ __device__ __forceinline__ void rr_pair(int round, int k, int P, int& i, int& j)
   }
 }
 
-template <typename C, typename S>
+template <typename C, typename S, int NPW>
 __global__ void __launch_bounds__(1024) jacobi_kernel(int q, int p, S* __restrict__ Wg, S* __restrict__ Vg,
                                                       int max_sweeps, double tol, uint32_t* errw,
                                                       S* __restrict__ Uo, S* __restrict__ So,
                                                       S* __restrict__ Vo, int in_smem) {
   extern __shared__ __align__(16) unsigned char jsm[];
   __shared__ int rotated;
-  __shared__ double nrm[1024];
+  __shared__ C nrm[1024];
   __shared__ int rank_[1024];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   S* W = Wg;
@@ -143,6 +179,7 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int q, int p, S* __restric
     V[e] = (i == c) ? S(1) : S(0);
   }
   const int P = p + (p & 1);
+  const C ctol2 = (C)(tol * tol);
   int sweep = 0;
   bool done = (p < 2);
   __syncthreads();
@@ -150,40 +187,80 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int q, int p, S* __restric
     if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
     for (int round = 0; round < P - 1; ++round) {
-      for (int k = warp; k < P / 2; k += nw) {
-        int i, j;
-        rr_pair(round, k, P, i, j);
-        if (i >= p || j >= p) continue;
-        if (i > j) { int t = i; i = j; j = t; }
-        S* wi = W + (size_t)i * q;
-        S* wj = W + (size_t)j * q;
-        C a = 0, b = 0, g = 0;
-        for (int r = lane; r < q; r += 32) {
-          C x = (C)wi[r], y = (C)wj[r];
-          a += x * x;
-          b += y * y;
-          g += x * y;
+      // this warp's NPW pairs of the round, processed together so that their
+      // load / shuffle-reduction / rotation latencies overlap
+      int pi[NPW], pj[NPW];
+      bool act[NPW];
+#pragma unroll
+      for (int t = 0; t < NPW; ++t) {
+        const int k = warp + t * nw;
+        int i = p, j = p;
+        if (k < P / 2) rr_pair(round, k, P, i, j);
+        act[t] = (i < p && j < p);
+        if (i > j) { int x = i; i = j; j = x; }
+        pi[t] = act[t] ? i : 0;
+        pj[t] = act[t] ? j : 0;
+      }
+      C a[NPW], b[NPW], g[NPW];
+#pragma unroll
+      for (int t = 0; t < NPW; ++t) a[t] = b[t] = g[t] = C(0);
+      for (int r = lane; r < q; r += 32) {
+#pragma unroll
+        for (int t = 0; t < NPW; ++t) {
+          const C x = (C)W[(size_t)pi[t] * q + r], y = (C)W[(size_t)pj[t] * q + r];
+          a[t] += x * x;
+          b[t] += y * y;
+          g[t] += x * y;
         }
-        a = warp_sum(a);
-        b = warp_sum(b);
-        g = warp_sum(g);
-        if (!(a > C(0) && b > C(0))) continue;
-        if (!(fabs((double)g) > tol * sqrt((double)a) * sqrt((double)b))) continue;
-        const C zeta = (b - a) / (C(2) * g);
-        const C t = (zeta >= C(0) ? C(1) : C(-1)) / (fabs(zeta) + sqrt(C(1) + zeta * zeta));
-        const C cs = C(1) / sqrt(C(1) + t * t);
-        const C sn = cs * t;
-        for (int r = lane; r < q; r += 32) {
-          C x = (C)wi[r], y = (C)wj[r];
-          wi[r] = (S)(cs * x - sn * y);
-          wj[r] = (S)(sn * x + cs * y);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int t = 0; t < NPW; ++t) {
+          a[t] += __shfl_xor_sync(0xffffffffu, a[t], o);
+          b[t] += __shfl_xor_sync(0xffffffffu, b[t], o);
+          g[t] += __shfl_xor_sync(0xffffffffu, g[t], o);
         }
-        S* vi = V + (size_t)i * p;
-        S* vj = V + (size_t)j * p;
+      }
+      C cs[NPW], sn[NPW];
+      bool rot[NPW];
+      bool any = false;
+#pragma unroll
+      for (int t = 0; t < NPW; ++t) {
+        // all in the rotation type C: FP64 arithmetic costs ~56x FP32 on this GPU
+        rot[t] = act[t] && a[t] > C(0) && b[t] > C(0) && g[t] * g[t] > ctol2 * a[t] * b[t];
+        cs[t] = C(1);
+        sn[t] = C(0);
+        if (rot[t]) {
+          const C zeta = (b[t] - a[t]) / (C(2) * g[t]);
+          const C tt = (zeta >= C(0) ? C(1) : C(-1)) / (fabs(zeta) + sqrt(C(1) + zeta * zeta));
+          cs[t] = C(1) / sqrt(C(1) + tt * tt);
+          sn[t] = cs[t] * tt;
+          any = true;
+        }
+      }
+      if (any) {
+        for (int r = lane; r < q; r += 32) {
+#pragma unroll
+          for (int t = 0; t < NPW; ++t) {
+            if (!rot[t]) continue;
+            S* wi = W + (size_t)pi[t] * q;
+            S* wj = W + (size_t)pj[t] * q;
+            const C x = (C)wi[r], y = (C)wj[r];
+            wi[r] = (S)(cs[t] * x - sn[t] * y);
+            wj[r] = (S)(sn[t] * x + cs[t] * y);
+          }
+        }
         for (int r = lane; r < p; r += 32) {
-          C x = (C)vi[r], y = (C)vj[r];
-          vi[r] = (S)(cs * x - sn * y);
-          vj[r] = (S)(sn * x + cs * y);
+#pragma unroll
+          for (int t = 0; t < NPW; ++t) {
+            if (!rot[t]) continue;
+            S* vi = V + (size_t)pi[t] * p;
+            S* vj = V + (size_t)pj[t] * p;
+            const C x = (C)vi[r], y = (C)vj[r];
+            vi[r] = (S)(cs[t] * x - sn[t] * y);
+            vj[r] = (S)(sn[t] * x + cs[t] * y);
+          }
         }
         if (lane == 0) rotated = 1;
       }
@@ -194,18 +271,19 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int q, int p, S* __restric
     __syncthreads();
   }
   if (!done && threadIdx.x == 0 && errw) atomicOr(errw, ERRW_NOCONV);
+  if (threadIdx.x == 0 && errw) atomicMax((int*)errw + 1, sweep);  // diagnostics: Jacobi sweeps used
   // singular values = column norms, sorted descending, ties by index
   for (int c = warp; c < p; c += nw) {
     const S* wc = W + (size_t)c * q;
-    double s = 0;
-    for (int r = lane; r < q; r += 32) s += (double)wc[r] * (double)wc[r];
+    C s = 0;
+    for (int r = lane; r < q; r += 32) s += (C)wc[r] * (C)wc[r];
     s = warp_sum(s);
     if (lane == 0) nrm[c] = sqrt(s);
   }
   __syncthreads();
   for (int c = threadIdx.x; c < p; c += blockDim.x) {
     int rk = 0;
-    double v = nrm[c];
+    const C v = nrm[c];
     for (int d = 0; d < p; ++d) rk += (nrm[d] > v) || (nrm[d] == v && d < c);
     rank_[c] = rk;
     So[rk] = (S)v;
@@ -213,9 +291,9 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int q, int p, S* __restric
   __syncthreads();
   for (int c = warp; c < p; c += nw) {
     const int rk = rank_[c];
-    const double s = nrm[c];
-    const double inv = s > 0.0 ? 1.0 / s : 0.0;
-    for (int r = lane; r < q; r += 32) Uo[(size_t)rk * q + r] = (S)((double)W[(size_t)c * q + r] * inv);
+    const C s = nrm[c];
+    const C inv = s > C(0) ? C(1) / s : C(0);
+    for (int r = lane; r < q; r += 32) Uo[(size_t)rk * q + r] = (S)((C)W[(size_t)c * q + r] * inv);
     for (int r = lane; r < p; r += 32) Vo[(size_t)rk * p + r] = V[(size_t)c * p + r];
   }
 }
@@ -232,22 +310,25 @@ cudaError_t jacobi_svd(int q, int p, S* W, S* U, S* Sv, S* V, S* Vwork, int max_
   const double tol = 4.0 * eps * sqrt((double)q);
   const size_t need = ((size_t)q * p + (size_t)p * p) * sizeof(S);
   const size_t cap = 200 * 1024;
-  int in_smem = need <= cap ? 1 : 0;
-  if (in_smem) {
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(jacobi_kernel<C, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+  const int in_smem = need <= cap ? 1 : 0;
+  const int pairs = (p + (p & 1)) / 2;
+  auto launch = [&](auto kern) -> cudaError_t {
+    if (in_smem) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
       if (e != cudaSuccess) return e;
-      attr = true;
     }
-  }
-  jacobi_kernel<C, S><<<1, 1024, in_smem ? need : 0, st>>>(q, p, W, Vwork, max_sweeps, tol, errw, U, Sv, V, in_smem);
-  return cudaGetLastError();
+    kern<<<1, 1024, in_smem ? need : 0, st>>>(q, p, W, Vwork, max_sweeps, tol, errw, U, Sv, V, in_smem);
+    return cudaGetLastError();
+  };
+  if (pairs <= 32) return launch(jacobi_kernel<C, S, 1>);
+  if (pairs <= 64) return launch(jacobi_kernel<C, S, 2>);
+  if (pairs <= 96) return launch(jacobi_kernel<C, S, 3>);
+  if (pairs <= 128) return launch(jacobi_kernel<C, S, 4>);
+  if (pairs <= 256) return launch(jacobi_kernel<C, S, 8>);
+  return launch(jacobi_kernel<C, S, 16>);
 }
 template cudaError_t jacobi_svd<double, double>(int, int, double*, double*, double*, double*, double*, int,
                                                 uint32_t*, cudaStream_t);
-template cudaError_t jacobi_svd<float, double>(int, int, double*, double*, double*, double*, double*, int, uint32_t*,
-                                               cudaStream_t);
 template cudaError_t jacobi_svd<float, float>(int, int, float*, float*, float*, float*, float*, int, uint32_t*,
                                               cudaStream_t);
 
@@ -255,14 +336,14 @@ template cudaError_t jacobi_svd<float, float>(int, int, float*, float*, float*, 
 template <typename T>
 __global__ void __launch_bounds__(1024) frob_kernel(const T* __restrict__ x, long long n, double* out, uint32_t* errw) {
   __shared__ double red[32];
-  double s = 0;
+  T part = 0;  // per-thread partial in the value type (FP32 stays on the FP32 pipes)
   bool bad = false;
   for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-    double v = (double)x[i];
+    const T v = x[i];
     bad |= !isfinite(v);
-    s += v * v;
+    part += v * v;
   }
-  s = block_sum(s, red);
+  double s = block_sum((double)part, red);
   bad = __syncthreads_or(bad);
   if (threadIdx.x == 0) {
     *out = sqrt(s);
@@ -468,6 +549,42 @@ cudaError_t fix_signs(int m, int n, int p, F* U, int ld_u, F* V, int ld_v, cudaS
 }
 template cudaError_t fix_signs<double>(int, int, int, double*, int, double*, int, cudaStream_t);
 template cudaError_t fix_signs<float>(int, int, int, float*, int, float*, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Alg. 4 from FP64 isometries U (m x k), V (n x k) (column-major) and the
+// projected k x k block P = U^T Theta V: s = diag(P), Psi_l = U s (m x k
+// row-major), Psi_{l+1} = s V^T (k x n row-major), Y_l = 1 / s.
+template <typename T>
+__global__ void inverse_gauge_kernel(int m, int n, int k, const double* __restrict__ U, const double* __restrict__ V,
+                                     const T* __restrict__ P, double* Cl, double* Cr, double* Y) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (long long e = t0; e < (long long)m * k; e += stride) {
+    const int i = (int)(e / k), j = (int)(e % k);
+    Cl[e] = U[(size_t)j * m + i] * (double)P[(size_t)j * k + j];
+  }
+  for (long long e = t0; e < (long long)k * n; e += stride) {
+    const int j = (int)(e / n), c = (int)(e % n);
+    Cr[e] = (double)P[(size_t)j * k + j] * V[(size_t)j * n + c];
+  }
+  for (long long e = t0; e < k; e += stride) {
+    const double sj = (double)P[(size_t)e * k + e];
+    Y[e] = sj != 0.0 ? 1.0 / sj : 0.0;
+  }
+}
+
+template <typename T>
+cudaError_t inverse_gauge_update(int m, int n, int k, const double* U, const double* V, const T* P, double* Cl,
+                                 double* Cr, double* Y, cudaStream_t st) {
+  long long tot = (long long)(m > n ? m : n) * k;
+  int blocks = (int)std::min<long long>((tot + 255) / 256, 1024);
+  inverse_gauge_kernel<T><<<std::max(blocks, 1), 256, 0, st>>>(m, n, k, U, V, P, Cl, Cr, Y);
+  return cudaGetLastError();
+}
+template cudaError_t inverse_gauge_update<float>(int, int, int, const double*, const double*, const float*, double*,
+                                                 double*, double*, cudaStream_t);
+template cudaError_t inverse_gauge_update<double>(int, int, int, const double*, const double*, const double*, double*,
+                                                  double*, double*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 __global__ void scale_cols_kernel(int rows, int cols, const double* __restrict__ in, const double* __restrict__ y,

