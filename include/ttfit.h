@@ -105,6 +105,8 @@ typedef struct {
   void* stream;        /* cudaStream_t; NULL = legacy default stream                       */
   int prepare_inputs;  /* 1 (default): RQ + QR sweep of A and B (Alg. 5 left_orthogonalize) */
   uint32_t fault_inject; /* host-side fault injection for tests (TT_FAULT_*), default 0     */
+  int fast_factor;     /* FP64 precision only: 1 = FP32 factorisation + FP64 Newton-Schulz  */
+                       /* polish (fast; subspace to FP32 accuracy), 0 (default) = FP64 SVD  */
 } tt_fit_options;
 
 /* Host-side fault injection (tests only; nothing here touches the device). */
@@ -140,6 +142,15 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
  * Stops early once converged. rep may be NULL. Synchronises the handle's
  * stream before returning. */
 tt_status tt_fit_sweep(tt_fit* h, int n_sweeps, tt_sweep_report* rep);
+
+/* Change the contraction precision for the following sweeps (the paper's
+ * "cheap sweeps first, exact sweeps last", Sec. 5.3): the chain buffers are
+ * rebuilt in the new arithmetic and R_L..R_3 recomputed from the current C.
+ * Allowed only when the next sweep is a forward one (after create or after a
+ * backward sweep), i.e. while C is right-canonical; otherwise TT_ERR_STATE
+ * (the handle stays usable). fast_factor as in tt_fit_options. Resets the
+ * converged flag; delta keeps comparing consecutive sweeps. */
+tt_status tt_fit_set_precision(tt_fit* h, int precision, int fast_factor);
 
 /* Export C as a plain MPO. Two-step: with C->cores == NULL, fill
  * C->L, and the caller-provided arrays C->d_out, C->d_in (L ints) and C->bond

@@ -124,7 +124,9 @@ struct tt_fit {
   double flops = 0;
   long long launches = 0, tc_launches = 0;
   bool have_times = false;
-  bool use_f32 = false;
+  bool use_f32 = false;   // chain type: float (non-FP64 precisions) or double
+  bool fact_f32 = false;  // FP32 factorisation + FP64 polish (always for float chains; optional for FP64)
+  std::vector<void*> chain_bufs;  // buffers rebuilt when the chain precision changes
 };
 
 namespace {
@@ -574,10 +576,10 @@ int factorize(tt_fit* h, int m, int n, int sweep, int site1) {
 // small rotations of the kept subspace, the FP32 rounding of the subspace
 // enters ||C||^2 only at second order. Writes ||C_window||^2 to dn2[l].
 // ---------------------------------------------------------------------------
-template <typename T>
-void ns_orthonormalize(tt_fit* h, const T* X32, int rows, int k, double* X64) {
+template <typename F>
+void ns_orthonormalize(tt_fit* h, const F* X32, int rows, int k, double* X64) {
   double* G = h->pG;
-  copymap<T, double>(h, rows, k, X32, IdxMap::lin(1), IdxMap::lin(rows), h->pT, IdxMap::lin(1), IdxMap::lin(rows));
+  copymap<F, double>(h, rows, k, X32, IdxMap::lin(1), IdxMap::lin(rows), h->pT, IdxMap::lin(1), IdxMap::lin(rows));
   GemmArgs<double> g;  // G = X^T X (k x k)
   g.M = k; g.N = k; g.K = rows;
   g.A = h->pT; g.am = IdxMap::lin(rows); g.ak = IdxMap::lin(1);
@@ -595,7 +597,7 @@ void ns_orthonormalize(tt_fit* h, const T* X32, int rows, int k, double* X64) {
   gemm<double>(h, g2);
 }
 
-template <typename T>
+template <typename T, typename F>
 void polish_update(tt_fit* h, int mode, int m, int n, int k, int l) {
   const T* Th = (const T*)h->Th;
   T* Ut = (T*)h->Ut[l];
@@ -603,12 +605,12 @@ void polish_update(tt_fit* h, int mode, int m, int n, int k, int l) {
   T* P = (T*)h->pP;  // m x k (or k x n) projection, then the k x k block
   const int side = std::max(m, n);
   if (mode != 1) {  // left isometry U (m x k)
-    ns_orthonormalize<T>(h, (const T*)h->fUM, m, k, h->pU);
+    ns_orthonormalize<F>(h, (const F*)h->fUM, m, k, h->pU);
     // Ut (k x m row-major) = U^T : same memory order as U column-major
     copymap<double, T>(h, 1, m * k, h->pU, IdxMap::lin(0), IdxMap::lin(1), Ut, IdxMap::lin(0), IdxMap::lin(1));
   }
   if (mode != 0) {  // right isometry V (n x k)
-    ns_orthonormalize<T>(h, (const T*)h->fVM, n, k, h->pV);
+    ns_orthonormalize<F>(h, (const F*)h->fVM, n, k, h->pV);
     copymap<double, T>(h, 1, n * k, h->pV, IdxMap::lin(0), IdxMap::lin(1), Vt, IdxMap::lin(0), IdxMap::lin(1));
   }
   if (mode == 0) {  // site, forward: C_l = U, C_{l+1} = U^T Theta
@@ -688,9 +690,15 @@ struct Sweeper {
     int m, n;
     ch.join(l, m, n);
     CK(cudaEventRecord(h->ev[3], h->st));
-    int p = factorize<T, T>(h, m, n, sweep, l + 1);
-    const double cut = h->cutoff;
-    CK(truncate_rule<T>((const T*)h->fS, p, h->dnorm, h->tol / L, h->chi_max, cut, h->dk, h->ddinfo, h->st));
+    int p;
+    if (h->fact_f32) {
+      p = factorize<T, float>(h, m, n, sweep, l + 1);
+      CK(truncate_rule<float>((const float*)h->fS, p, h->dnorm, h->tol / L, h->chi_max, h->cutoff, h->dk, h->ddinfo,
+                              h->st));
+    } else {
+      p = factorize<T, T>(h, m, n, sweep, l + 1);
+      CK(truncate_rule<T>((const T*)h->fS, p, h->dnorm, h->tol / L, h->chi_max, h->cutoff, h->dk, h->ddinfo, h->st));
+    }
     h->launches += 1;
     CK(cudaEventRecord(h->ev[4], h->st));
     CK(cudaMemcpyAsync(h->hk, h->dk, sizeof(int), cudaMemcpyDeviceToHost, h->st));
@@ -721,19 +729,25 @@ struct Sweeper {
     // gauge update (Alg. 3 / Alg. 4)
     const int mode = (h->gauge == TT_GAUGE_INVERSE_CANONICAL) ? 2 : (fwd ? 0 : 1);
     CK(cudaEventRecord(h->ev[5], h->st));
-    if (h->precision == TT_PREC_FP64) {
+    if (!h->fact_f32) {
       CK(gauge_update<T, T>(mode, m, n, (const T*)h->fUM, m, (const T*)h->fS, (const T*)h->fVM, n, h->dk, h->C64[l],
                             h->C64[l + 1], h->Y[l + 1], (T*)h->Ut[l], (T*)h->Vt[l + 1], h->st));
       h->launches += 1;
     } else {
-      polish_update<T>(h, mode, m, n, k, l);
+      polish_update<T, float>(h, mode, m, n, k, l);
     }
     CK(cudaEventRecord(h->ev[6], h->st));
     h->gauge_pending = true;
     // host copy of the kept spectrum for tt_fit_result
-    std::vector<T> sv(k);
-    CK(cudaMemcpyAsync(sv.data(), h->fS, sizeof(T) * k, cudaMemcpyDeviceToHost, h->st));
-    h->lam[l + 1].assign(sv.begin(), sv.end());
+    if (h->fact_f32) {
+      std::vector<float> sv(k);
+      CK(cudaMemcpyAsync(sv.data(), h->fS, sizeof(float) * k, cudaMemcpyDeviceToHost, h->st));
+      h->lam[l + 1].assign(sv.begin(), sv.end());
+    } else {
+      std::vector<double> sv(k);
+      CK(cudaMemcpyAsync(sv.data(), h->fS, sizeof(double) * k, cudaMemcpyDeviceToHost, h->st));
+      h->lam[l + 1].assign(sv.begin(), sv.end());
+    }
   }
 
   void run(int n_sweeps) {
@@ -755,7 +769,7 @@ struct Sweeper {
       }
       CK(cudaStreamSynchronize(h->st));
       resolve_gauge();
-      if (h->precision != TT_PREC_FP64) {  // ||C||^2 from the FP64-orthonormal projection of the last window
+      if (h->fact_f32) {  // ||C||^2 from the FP64-orthonormal projection of the last window
         const int lw = h->forward ? L - 2 : 0;
         double nr = 0;
         CK(cudaMemcpy(&nr, h->dn2 + lw, sizeof(double), cudaMemcpyDeviceToHost));
@@ -813,6 +827,13 @@ void upload(tt_fit* h, const tt_mpo_desc* X, const std::vector<int>& dout, const
 }
 
 template <typename T>
+T* calloc_chain(tt_fit* h, size_t n) {
+  T* p = h->pool.alloc<T>(n);
+  h->chain_bufs.push_back(p);
+  return p;
+}
+
+template <typename T>
 void build_operands(tt_fit* h) {
   Dims& D = h->D;
   const int L = D.L;
@@ -823,10 +844,10 @@ void build_operands(tt_fit* h) {
   for (int j = 0; j < L; ++j) {
     const int a0 = D.a[j], a1 = D.a[j + 1], b0 = D.b[j], b1 = D.b[j + 1];
     const int ds = D.ds[j], du = D.du[j], dt = D.dt[j];
-    T* aop = h->pool.alloc<T>((size_t)a0 * ds * du * a1);
-    T* anat = h->pool.alloc<T>((size_t)a0 * ds * du * a1);
-    T* bl = h->pool.alloc<T>((size_t)b0 * du * dt * b1);
-    T* br = h->pool.alloc<T>((size_t)b0 * du * dt * b1);
+    T* aop = calloc_chain<T>(h, (size_t)a0 * ds * du * a1);
+    T* anat = calloc_chain<T>(h, (size_t)a0 * ds * du * a1);
+    T* bl = calloc_chain<T>(h, (size_t)b0 * du * dt * b1);
+    T* br = calloc_chain<T>(h, (size_t)b0 * du * dt * b1);
     // A natural (a0, s, u, a1) -> row i = a0, col = (s u a1)
     copymap<double, T>(h, a0, ds * du * a1, h->A64[j], IdxMap::lin((long long)ds * du * a1), IdxMap::lin(1), anat,
                        IdxMap::lin((long long)ds * du * a1), IdxMap::lin(1));
@@ -863,61 +884,85 @@ void allocate_chain(tt_fit* h) {
   long long mmax = 1, nmax = 1;
   for (int j = 0; j <= L; ++j) {
     const long long e = prodll({D.a[j], D.b[j], D.cb[j]});
-    h->Lenv[j] = h->pool.alloc<T>(e);
-    h->Renv[j] = h->pool.alloc<T>(e);
+    h->Lenv[j] = calloc_chain<T>(h, e);
+    h->Renv[j] = calloc_chain<T>(h, e);
   }
   for (int j = 0; j < L; ++j) {
     const int ds = D.ds[j], du = D.du[j], dt = D.dt[j];
-    h->H1[j] = h->pool.alloc<T>(prodll({D.cb[j], ds, dt, D.a[j + 1], D.b[j + 1]}));
-    h->H2[j] = h->pool.alloc<T>(prodll({D.a[j], D.b[j], ds, dt, D.cb[j + 1]}));
-    h->H1t[j] = h->pool.alloc<T>(prodll({D.cb[j], ds, dt, D.a[j + 1], D.b[j + 1]}));
-    h->H2t[j] = h->pool.alloc<T>(prodll({D.a[j], D.b[j], ds, dt, D.cb[j + 1]}));
-    h->Ut[j] = h->pool.alloc<T>(prodll({D.cb[j + 1], D.cb[j], ds, dt}));
-    h->Vt[j] = h->pool.alloc<T>(prodll({D.cb[j], ds, dt, D.cb[j + 1]}));
+    h->H1[j] = calloc_chain<T>(h, prodll({D.cb[j], ds, dt, D.a[j + 1], D.b[j + 1]}));
+    h->H2[j] = calloc_chain<T>(h, prodll({D.a[j], D.b[j], ds, dt, D.cb[j + 1]}));
+    h->H1t[j] = calloc_chain<T>(h, prodll({D.cb[j], ds, dt, D.a[j + 1], D.b[j + 1]}));
+    h->H2t[j] = calloc_chain<T>(h, prodll({D.a[j], D.b[j], ds, dt, D.cb[j + 1]}));
+    h->Ut[j] = calloc_chain<T>(h, prodll({D.cb[j + 1], D.cb[j], ds, dt}));
+    h->Vt[j] = calloc_chain<T>(h, prodll({D.cb[j], ds, dt, D.cb[j + 1]}));
     x1 = std::max<size_t>(x1, prodll({D.cb[j], D.b[j], ds, du, D.a[j + 1]}));
     zs = std::max<size_t>(zs, prodll({D.a[j], ds, du, D.cb[j + 1], D.b[j + 1]}));
     mmax = std::max<long long>(mmax, (long long)D.cb[j] * ds * dt);
     nmax = std::max<long long>(nmax, (long long)ds * dt * D.cb[j + 1]);
   }
-  h->X1 = h->pool.alloc<T>(x1);
-  h->Zs = h->pool.alloc<T>(zs);
-  h->Th = h->pool.alloc<T>((size_t)mmax * nmax);
+  h->X1 = calloc_chain<T>(h, x1);
+  h->Zs = calloc_chain<T>(h, zs);
+  h->Th = calloc_chain<T>(h, (size_t)mmax * nmax);
   // split-K workspace: up to 64 partial M x N tiles of the largest GEMM output we split
   h->gws_elems = (size_t)std::max<long long>(mmax * nmax, 1) * 16 + (1 << 20);
-  h->gws = h->pool.alloc<double>(h->gws_elems);
+  h->gws = calloc_chain<double>(h, h->gws_elems);
   const long long big = std::max(mmax, nmax);
   const long long ks = h->chi_max + h->oversample;
   const long long side = std::max(big, ks);
   h->fsz = (size_t)side * side;
-  h->fX = h->pool.alloc<double>(h->fsz);
-  h->fQ = h->pool.alloc<double>(h->fsz);
-  h->fR = h->pool.alloc<double>(h->fsz);
-  h->fU = h->pool.alloc<double>(h->fsz);
-  h->fV = h->pool.alloc<double>(h->fsz);
-  h->fVw = h->pool.alloc<double>(h->fsz);
-  h->fS = h->pool.alloc<double>(side);
-  h->fUM = h->pool.alloc<double>(h->fsz);
-  h->fVM = h->pool.alloc<double>(h->fsz);
-  h->fOm = h->pool.alloc<double>(h->fsz);
-  h->fY = h->pool.alloc<double>(h->fsz);
-  h->fBt = h->pool.alloc<double>(h->fsz);
-  h->fQ2 = h->pool.alloc<double>(h->fsz);
-  h->fR2 = h->pool.alloc<double>(h->fsz);
-  h->pU = h->pool.alloc<double>(h->fsz);
-  h->pV = h->pool.alloc<double>(h->fsz);
-  h->pG = h->pool.alloc<double>(h->fsz);
-  h->pT = h->pool.alloc<double>(h->fsz);
-  h->pP = h->pool.alloc<double>((size_t)side * ks + (size_t)ks * ks + 64);
-  h->dn2 = h->pool.alloc<double>(L + 1);
+  h->fX = calloc_chain<double>(h, h->fsz);
+  h->fQ = calloc_chain<double>(h, h->fsz);
+  h->fR = calloc_chain<double>(h, h->fsz);
+  h->fU = calloc_chain<double>(h, h->fsz);
+  h->fV = calloc_chain<double>(h, h->fsz);
+  h->fVw = calloc_chain<double>(h, h->fsz);
+  h->fS = calloc_chain<double>(h, side);
+  h->fUM = calloc_chain<double>(h, h->fsz);
+  h->fVM = calloc_chain<double>(h, h->fsz);
+  h->fOm = calloc_chain<double>(h, h->fsz);
+  h->fY = calloc_chain<double>(h, h->fsz);
+  h->fBt = calloc_chain<double>(h, h->fsz);
+  h->fQ2 = calloc_chain<double>(h, h->fsz);
+  h->fR2 = calloc_chain<double>(h, h->fsz);
+  h->pU = calloc_chain<double>(h, h->fsz);
+  h->pV = calloc_chain<double>(h, h->fsz);
+  h->pG = calloc_chain<double>(h, h->fsz);
+  h->pT = calloc_chain<double>(h, h->fsz);
+  h->pP = calloc_chain<double>(h, (size_t)side * ks + (size_t)ks * ks + 64);
+  h->dn2 = calloc_chain<double>(h, L + 1);
 }
 
+// (Re)build the contraction chain in type T from the current C, which must be
+// right-canonical (after create, or after a backward sweep): operands, buffers,
+// the right-environment operands Vt_j (site gauge C_j, inverse gauge
+// Y_{j-1} Psi_j), trivial end environments and R_L..R_3 with their halves.
 template <typename T>
+void rebuild_chain(tt_fit* h) {
+  Dims& D = h->D;
+  const int L = D.L;
+  CK(cudaStreamSynchronize(h->st));
+  for (void* p : h->chain_bufs) h->pool.release(p);
+  h->chain_bufs.clear();
+  build_operands<T>(h);
+  allocate_chain<T>(h);
+  for (int j = 0; j < L; ++j) {
+    const int rows = D.c[j], cols = D.ds[j] * D.dt[j] * D.c[j + 1];
+    const bool inv = h->gauge == TT_GAUGE_INVERSE_CANONICAL && j > 0;
+    CK(scale_rows<T>(rows, cols, h->C64[j], inv ? h->Y[j] : nullptr, (T*)h->Vt[j], h->st));
+    h->launches += 1;
+  }
+  T one = T(1);
+  CK(cudaMemcpyAsync(h->Lenv[0], &one, sizeof(T), cudaMemcpyHostToDevice, h->st));
+  CK(cudaMemcpyAsync(h->Renv[L], &one, sizeof(T), cudaMemcpyHostToDevice, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  Sweeper<T> sw(h);
+  sw.precompute_right();
+}
+
 void setup(tt_fit* h, const std::vector<double*>& C0) {
   Dims& D = h->D;
   const int L = D.L;
-  build_operands<T>(h);
-  allocate_chain<T>(h);
-  // C state: FP64 cores at capacity size, Y per bond = 1, env operands from C0
+  // C state: FP64 cores at capacity size, Y per bond = 1
   h->C64.assign(L, nullptr);
   h->Y.assign(L + 1, nullptr);
   h->lam.assign(L + 1, {});
@@ -926,9 +971,6 @@ void setup(tt_fit* h, const std::vector<double*>& C0) {
     h->C64[j] = h->pool.alloc<double>(cap);
     const long long n = prodll({D.c[j], D.ds[j], D.dt[j], D.c[j + 1]});
     CK(cudaMemcpyAsync(h->C64[j], C0[j], sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
-    // Vt_j = C0_j as (c_j-1) x (s t c_j) row-major
-    copymap<double, T>(h, 1, (int)n, C0[j], IdxMap::lin(0), IdxMap::lin(1), (T*)h->Vt[j], IdxMap::lin(0),
-                       IdxMap::lin(1));
   }
   std::vector<double> ones(1024, 1.0);
   for (int j = 0; j <= L; ++j) {
@@ -938,13 +980,8 @@ void setup(tt_fit* h, const std::vector<double*>& C0) {
       CK(cudaMemcpyAsync(h->Y[j] + off, ones.data(), sizeof(double) * std::min(1024, n - off), cudaMemcpyHostToDevice,
                          h->st));
   }
-  // trivial environments L_0 = R_{L+1} = [1]  (Sec. 2.3.3)
-  T one = T(1);
-  CK(cudaMemcpyAsync(h->Lenv[0], &one, sizeof(T), cudaMemcpyHostToDevice, h->st));
-  CK(cudaMemcpyAsync(h->Renv[L], &one, sizeof(T), cudaMemcpyHostToDevice, h->st));
-  CK(cudaStreamSynchronize(h->st));
-  Sweeper<T> sw(h);
-  sw.precompute_right();
+  if (h->use_f32) rebuild_chain<float>(h);
+  else rebuild_chain<double>(h);
 }
 
 thread_local std::string g_create_error;
@@ -1028,6 +1065,7 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
     h->init = o.init;
     h->seed = o.seed;
     h->use_f32 = (o.precision != TT_PREC_FP64);
+    h->fact_f32 = h->use_f32 || o.fast_factor;
     h->cutoff = o.sv_cutoff >= 0 ? o.sv_cutoff : (o.precision == TT_PREC_FP64 ? 1e-13 : 1e-6);
     h->conv_tol = o.conv_tol >= 0 ? o.conv_tol : tol;
     h->st = (cudaStream_t)o.stream;
@@ -1148,8 +1186,7 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
       cbond = bz;
     }
     D.c = cbond;
-    if (h->use_f32) setup<float>(h, C0);
-    else setup<double>(h, C0);
+    setup(h, C0);
     for (int j = 0; j < L; ++j) h->pool.release(C0[j]);
     CK(cudaStreamSynchronize(h->st));
     *out = h;
@@ -1253,6 +1290,28 @@ tt_status tt_fit_result(const tt_fit* hc, tt_mpo_desc* C, double* lambdas) {
       CK(cudaStreamSynchronize(h->st));
       h->pool.release(tmp);
     }
+  } catch (const TTError& e) {
+    poison(h, e);
+    return e.code;
+  }
+  return TT_OK;
+}
+
+tt_status tt_fit_set_precision(tt_fit* h, int precision, int fast_factor) {
+  if (!h || precision < 0 || precision > 4 || precision == TT_PREC_BF16_SPLIT) return TT_ERR_INVALID_ARGUMENT;
+  if (h->poisoned) return TT_ERR_STATE;
+  if (!h->forward) {
+    h->last_error = "tt_fit_set_precision: the next sweep must be a forward sweep (C right-canonical)";
+    return TT_ERR_STATE;
+  }
+  try {
+    const bool f32 = precision != TT_PREC_FP64;
+    h->precision = precision;
+    h->use_f32 = f32;
+    h->fact_f32 = f32 || fast_factor;
+    h->converged = false;
+    if (f32) rebuild_chain<float>(h);
+    else rebuild_chain<double>(h);
   } catch (const TTError& e) {
     poison(h, e);
     return e.code;

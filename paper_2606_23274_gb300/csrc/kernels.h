@@ -90,6 +90,10 @@ template <typename T>
 cudaError_t inverse_gauge_update(int m, int n, int k, const double* U, const double* V, const T* P, double* Cl,
                                  double* Cr, double* Y, cudaStream_t st);
 
+// out (rows x cols, row-major, type T) = diag(y) * in (y == nullptr: plain cast copy)
+template <typename T>
+cudaError_t scale_rows(int rows, int cols, const double* in, const double* y, T* out, cudaStream_t st);
+
 // out (rows x cols, row-major) = in * diag(y) (y == nullptr: plain copy)
 cudaError_t scale_cols(int rows, int cols, const double* in, const double* y, double* out, cudaStream_t st);
 

@@ -594,6 +594,25 @@ __global__ void scale_cols_kernel(int rows, int cols, const double* __restrict__
     out[e] = y ? in[e] * y[e % cols] : in[e];
 }
 
+template <typename T>
+__global__ void scale_rows_kernel(int rows, int cols, const double* __restrict__ in, const double* __restrict__ y,
+                                  T* __restrict__ out) {
+  const long long tot = (long long)rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x)
+    out[e] = (T)(y ? in[e] * y[e / cols] : in[e]);
+}
+
+template <typename T>
+cudaError_t scale_rows(int rows, int cols, const double* in, const double* y, T* out, cudaStream_t st) {
+  long long tot = (long long)rows * cols;
+  if (tot <= 0) return cudaSuccess;
+  int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
+  scale_rows_kernel<T><<<blocks, 256, 0, st>>>(rows, cols, in, y, out);
+  return cudaGetLastError();
+}
+template cudaError_t scale_rows<float>(int, int, const double*, const double*, float*, cudaStream_t);
+template cudaError_t scale_rows<double>(int, int, const double*, const double*, double*, cudaStream_t);
+
 cudaError_t scale_cols(int rows, int cols, const double* in, const double* y, double* out, cudaStream_t st) {
   long long tot = (long long)rows * cols;
   if (tot <= 0) return cudaSuccess;

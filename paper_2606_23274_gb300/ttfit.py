@@ -36,7 +36,8 @@ class tt_fit_options(ct.Structure):
     _fields_ = [("struct_size", ct.c_size_t), ("update", ct.c_int), ("oversample", ct.c_int),
                 ("seed", ct.c_uint64), ("precision", ct.c_int), ("init", ct.c_int),
                 ("init_C", ct.POINTER(tt_mpo_desc)), ("sv_cutoff", ct.c_double), ("conv_tol", ct.c_double),
-                ("stream", ct.c_void_p), ("prepare_inputs", ct.c_int), ("fault_inject", ct.c_uint32)]
+                ("stream", ct.c_void_p), ("prepare_inputs", ct.c_int), ("fault_inject", ct.c_uint32),
+                ("fast_factor", ct.c_int)]
 
 
 class tt_sweep_report(ct.Structure):
@@ -73,6 +74,8 @@ def load():
         lib.tt_status_string.restype = ct.c_char_p
         lib.tt_fit_last_error.argtypes = [ct.c_void_p]
         lib.tt_fit_last_error.restype = ct.c_char_p
+        lib.tt_fit_set_precision.argtypes = [ct.c_void_p, ct.c_int, ct.c_int]
+        lib.tt_fit_set_precision.restype = ct.c_int
         lib.tt_fit_stage_times.argtypes = [ct.c_void_p, ct.POINTER(ct.c_double)]
         lib.tt_fit_stage_times.restype = ct.c_int
         _lib = lib
@@ -125,7 +128,8 @@ def _check(code, h=None, what=""):
 
 def tt_fit_create(A: Sequence, B: Sequence, chi_max: int, tol: float, gauge="site", *, update="svd",
                   oversample=10, seed=0, precision="fp64", init="random", init_C=None, sv_cutoff=-1.0,
-                  conv_tol=-1.0, stream=None, prepare_inputs=True, fault_inject=0, device="cuda"):
+                  conv_tol=-1.0, stream=None, prepare_inputs=True, fault_inject=0, fast_factor=False,
+                  device="cuda"):
     """Create a fit handle (see tt_fit_create in include/ttfit.h). A, B: lists of
     (chi_l, d, d', chi_r) tensors (torch CUDA tensors, or host arrays that are copied)."""
     import torch
@@ -150,6 +154,7 @@ def tt_fit_create(A: Sequence, B: Sequence, chi_max: int, tol: float, gauge="sit
     o.stream = ct.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     o.prepare_inputs = 1 if prepare_inputs else 0
     o.fault_inject = int(fault_inject)
+    o.fast_factor = 1 if fast_factor else 0
     h = ct.c_void_p()
     g = GAUGE[gauge] if isinstance(gauge, str) else int(gauge)
     code = lib.tt_fit_create(ct.byref(dA.desc), ct.byref(dB.desc), int(chi_max), float(tol), g, ct.byref(o),
@@ -223,6 +228,11 @@ class Fit:
             out.append(np.array(buf[off:off + b]))
             off += b
         return out
+
+    def set_precision(self, precision, fast_factor=False):
+        """Switch the contraction precision for the following sweeps (see include/ttfit.h)."""
+        prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        _check(load().tt_fit_set_precision(self.h, prec, 1 if fast_factor else 0), self.h, "tt_fit_set_precision")
 
     def stage_times(self) -> dict:
         v = (ct.c_double * 7)()
