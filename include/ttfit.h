@@ -178,6 +178,21 @@ const char* tt_fit_last_error(const tt_fit* h);
  * sweep ran. */
 tt_status tt_fit_stage_times(const tt_fit* h, double out[7]);
 
+/* Truncated SVD of one device matrix, the factorisation of the local update
+ * (Sec. 2.3.4): M is m x n, row-major, FP64 (device). Computes the thin SVD
+ * M = U diag(S) Vt in FP64 (one-sided Jacobi; singular values descending;
+ * each pair signed so that the largest-magnitude entry of u_j is positive)
+ * into caller device buffers U (m x r row-major), S (r), Vt (r x n
+ * row-major), r = min(m, n) <= 1024, and returns in *k_out (host) the rank
+ * the truncation rule keeps: k = min(chi_max, min{k : sqrt(sum_{j>k} s_j^2)
+ * <= tau_rel ||M||_F}), values <= 1e-13 s_1 dropped, k >= 1. Allocates its
+ * scratch with cudaMalloc, runs on `stream` (cudaStream_t, NULL = default)
+ * and synchronises it. Errors: TT_ERR_INVALID_ARGUMENT (NULL pointer,
+ * non-positive size, r > 1024), TT_ERR_OUT_OF_MEMORY, TT_ERR_CUDA,
+ * TT_ERR_NUMERICAL (non-finite input, no convergence). */
+tt_status tt_svd_truncated(const double* M, int m, int n, int chi_max, double tau_rel, double* U, double* S,
+                           double* Vt, int* k_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,6 +74,9 @@ def load():
         lib.tt_status_string.restype = ct.c_char_p
         lib.tt_fit_last_error.argtypes = [ct.c_void_p]
         lib.tt_fit_last_error.restype = ct.c_char_p
+        lib.tt_svd_truncated.argtypes = [ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.c_double, ct.c_void_p,
+                                         ct.c_void_p, ct.c_void_p, ct.POINTER(ct.c_int), ct.c_void_p]
+        lib.tt_svd_truncated.restype = ct.c_int
         lib.tt_fit_set_precision.argtypes = [ct.c_void_p, ct.c_int, ct.c_int]
         lib.tt_fit_set_precision.restype = ct.c_int
         lib.tt_fit_stage_times.argtypes = [ct.c_void_p, ct.POINTER(ct.c_double)]
@@ -161,6 +164,26 @@ def tt_fit_create(A: Sequence, B: Sequence, chi_max: int, tol: float, gauge="sit
                              ct.byref(h))
     _check(code, None, "tt_fit_create")
     return Fit(h, device, len(A))
+
+
+def tt_svd_truncated(M, chi_max: int, tau_rel: float = 0.0, stream=None):
+    """Truncated SVD of a device (or host) FP64 matrix through the C ABI:
+    returns (U, S, Vt, k) with the thin factors as device tensors."""
+    import torch
+    lib = load()
+    M = torch.as_tensor(M, dtype=torch.float64).cuda().contiguous()
+    m, n = M.shape
+    r = min(m, n)
+    U = torch.empty((m, r), dtype=torch.float64, device=M.device)
+    S = torch.empty((r,), dtype=torch.float64, device=M.device)
+    Vt = torch.empty((r, n), dtype=torch.float64, device=M.device)
+    k = ct.c_int(0)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    code = lib.tt_svd_truncated(M.data_ptr(), m, n, int(chi_max), float(tau_rel), U.data_ptr(), S.data_ptr(),
+                                Vt.data_ptr(), ct.byref(k), ct.c_void_p(stream.cuda_stream))
+    _check(code, None, "tt_svd_truncated")
+    return U, S, Vt, k.value
 
 
 def tt_fit_sweep(fit: "Fit", n_sweeps: int):

