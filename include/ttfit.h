@@ -193,6 +193,25 @@ tt_status tt_fit_stage_times(const tt_fit* h, double out[7]);
 tt_status tt_svd_truncated(const double* M, int m, int n, int chi_max, double tau_rel, double* U, double* S,
                            double* Vt, int* k_out, void* stream);
 
+/* Same computation and arguments as tt_svd_truncated, for callers that must
+ * not allocate device memory: for example code running while a caching
+ * allocator owns the device's memory budget, or latency-critical loops where
+ * a cudaMalloc / cudaFree would synchronise the device. This entry point calls
+ * no cudaMalloc, cudaFree or other allocating routine. (The paper has no
+ * counterpart; it is an interface convenience.)
+ * Its scratch is a fixed 4 MiB device array inside the library (2^19
+ * doubles), held on every GPU that loads the library until the process exits.
+ * An m x n input needs 2 q r + 2 r^2 + r + 6 doubles of it (r = min(m, n),
+ * q = max(m, n); e.g. up to 512 x 256); larger inputs return
+ * TT_ERR_INVALID_ARGUMENT. The first call on a device looks up the array's
+ * address on that device (cudaGetSymbolAddress), so make that first call
+ * before any stream capture. All calls on a device share the one array and
+ * it keeps the last call's contents: calls that overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Synchronises `stream` before returning. */
+tt_status tt_svd_truncated_noalloc(const double* M, int m, int n, int chi_max, double tau_rel, double* U, double* S,
+                                   double* Vt, int* k_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
 
 #include "../../include/ttfit.h"
 #include "common.cuh"
@@ -103,6 +104,70 @@ extern "C" tt_status tt_svd_truncated(const double* M, int m, int n, int chi_max
     e = cudaMemcpyAsync(flags, scratch + svd_info_offset(m, n), 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(scratch);
+  if (e != cudaSuccess) return TT_ERR_CUDA;
+  if (flags[0] & (ERRW_NAN | ERRW_NOCONV)) return TT_ERR_NUMERICAL;
+  *k_out = k;
+  return TT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant. Its scratch is this file-scope device array: every
+// GPU that loads the library holds these 4 MiB until the process exits, and
+// every call on a device reuses the same array (so calls that overlap on the
+// GPU race). Host code may not use the array's name as a device address; the
+// address is looked up per device with cudaGetSymbolAddress and cached.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocDoubles = size_t(1) << 19;  // 4 MiB of FP64 scratch
+__device__ __align__(256) double g_svd_scratch[kNoAllocDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+double* g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of g_svd_scratch on the current device (looked up on the
+// first call on that device, with that device current).
+cudaError_t noalloc_scratch(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_svd_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_ptr[dev] = (double*)p;
+  }
+  *out = g_scratch_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" tt_status tt_svd_truncated_noalloc(const double* M, int m, int n, int chi_max, double tau_rel, double* U,
+                                              double* S, double* Vt, int* k_out, void* stream) {
+  tt_status s = svd_check(M, m, n, chi_max, tau_rel, U, S, Vt, k_out);
+  if (s != TT_OK) return s;
+  const size_t nd = svd_scratch_doubles(m, n);
+  if (nd > kNoAllocDoubles) return TT_ERR_INVALID_ARGUMENT;  // beyond the fixed scratch
+  cudaStream_t st = (cudaStream_t)stream;
+  double* scratch = nullptr;
+  if (noalloc_scratch(&scratch) != cudaSuccess) {
+    cudaGetLastError();
+    return TT_ERR_CUDA;
+  }
+  int* k_dev = (int*)(scratch + nd - 1);
+  // svd_run clears the error flags it reads; every other scratch word it uses
+  // is written before it is read
+  cudaError_t e = svd_run(M, m, n, chi_max, tau_rel, U, S, Vt, k_dev, scratch, st);
+  int k = 0;
+  uint32_t flags[2] = {0, 0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&k, k_dev, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(flags, scratch + svd_info_offset(m, n), 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return TT_ERR_CUDA;
   if (flags[0] & (ERRW_NAN | ERRW_NOCONV)) return TT_ERR_NUMERICAL;
   *k_out = k;
