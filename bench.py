@@ -7,12 +7,15 @@ each a sum of 128 Kronecker products of 2x2 Gaussian factors with weights
 Gaussian-sketch randomized update (oversampling 10) until the relative change
 of ||C||^2 between sweeps is <= 1e-8. A step is one complete fit: input
 preparation, initial guess and right environments, sweeps until converged, and
-the export of C. Metric: time-to-tol in seconds (lower is better), reported
-with the local-update TFLOP/s of the contraction kernels against the measured
-peak.
+the export of C. The default precision schedule runs cheap sweeps first and
+exact ones last: 3xTF32 tensor-core contractions with the FP32 factorisation
+until the change of ||C||^2 falls below 1e-4, then FP64 contractions with the
+FP64-polished factorisation to convergence. Metric: time-to-tol in seconds
+(lower is better), reported with the local-update TFLOP/s and a roofline entry
+for the dominant stage.
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload (a few bulk windows), scaled to the fit's window count.
+workload (bulk windows), scaled to the fit's window count.
 """
 from __future__ import annotations
 
@@ -31,7 +34,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MPO-MPO fit time-to-tol (s) & local-update TFLOP/s vs peak, L=30 χ=128"
 WORKLOAD = "kron_L30_chi128"
-L_SITES, CHI, OVERSAMPLE, TOL, MAX_SWEEPS = 30, 128, 10, 1e-8, 12
+L_SITES, CHI, OVERSAMPLE, TOL, MAX_SWEEPS = 30, 128, 10, 1e-8, 14
+SWITCH_DELTA = 1e-4
 
 
 def parse():
@@ -40,7 +44,10 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
-    p.add_argument("--precision", default=os.environ.get("TTFIT_BENCH_PRECISION", "fp32"))
+    p.add_argument("--precision", default=os.environ.get("TTFIT_BENCH_PRECISION", "tf32x3>fp64"),
+                   help='a precision ("fp64", "fp32", "tf32x3", ...) or the schedule "tf32x3>fp64"')
+    p.add_argument("--workload", default=WORKLOAD,
+                   help="synthetic workload (default: the timed one); smaller ones serve profiling captures")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -99,8 +106,43 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- native arm
+STAGES = ("halves_ms", "join_ms", "env_finish_ms", "factorize_ms", "gauge_ms", "contraction_flops", "launches")
+# peaks of the plain CUDA-core pipes (ALU bound): 152 SMs x FMA lanes per SM x 2 flop x max SM clock
+FMA_LANES = {"f64": 2, "f32": 128}
+
+
+def run_fit(ttfit, Ain, Bin, schedule, seed, dev, stream, chi=CHI):
+    """One complete fit. ``schedule`` is a precision name ("fp64", "fp32", "tf32x3", ...) for a
+    single-precision fit, or "tf32x3>fp64": 3xTF32 sweeps (FP32-factorised randomized update) until
+    the relative change of ||C||^2 is below SWITCH_DELTA after an even number of sweeps, then FP64
+    contractions with the FP64-polished FP32 factorisation until converged."""
+    lo, hi = (schedule.split(">") + [None])[:2]
+    f = ttfit.tt_fit_create(Ain, Bin, chi, TOL, "site", update="rsvd", oversample=OVERSAMPLE, seed=seed,
+                            precision=lo, device=dev, stream=stream)
+    phases = {lo: {k: 0.0 for k in STAGES}}
+    phase_sweeps = {lo: 0}
+    cur, sweeps, rep = lo, 0, None
+    while sweeps < MAX_SWEEPS:
+        rep = f.sweep(1)
+        sweeps += 1
+        phase_sweeps[cur] += 1
+        st = f.stage_times()
+        for k in STAGES:
+            phases[cur][k] += st[k]
+        if rep["converged"] and (hi is None or cur == hi):
+            break
+        if hi is not None and cur == lo and sweeps % 2 == 0 and rep["delta"] < SWITCH_DELTA:
+            f.set_precision(hi, fast_factor=True)
+            cur = hi
+            phases[hi] = {k: 0.0 for k in STAGES}
+            phase_sweeps[hi] = 0
+    C = f.result()
+    launches = f.launch_count()
+    f.destroy()
+    return rep, sweeps, phase_sweeps, phases, C, launches
+
+
 def native(args):
-    import numpy as np
     import torch
     import torch.distributed as dist
     from paper_2606_23274_gb300 import ttfit
@@ -117,37 +159,14 @@ def native(args):
     ttfit.load()
 
     # inputs resident in HBM before the timed region; rank r fits its own pair
-    A, B = mpo_pair(WORKLOAD, seed=rank)
+    from paper_2606_23274_gb300.synth import WORKLOADS
+    chi = WORKLOADS[args.workload]["chi_C"]
+    A, B = mpo_pair(args.workload, seed=rank)
     Ad = [torch.from_numpy(a).to(dev) for a in A]
     Bd = [torch.from_numpy(b).to(dev) for b in B]
     Ah = [torch.from_numpy(a).pin_memory() for a in A]
     Bh = [torch.from_numpy(b).pin_memory() for b in B]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
-
-    def one_fit(Ain, Bin, host=False):
-        if host:
-            Ain = [a.to(dev, non_blocking=True) for a in Ain]
-            Bin = [b.to(dev, non_blocking=True) for b in Bin]
-        f = ttfit.tt_fit_create(Ain, Bin, CHI, TOL, "site", update="rsvd", oversample=OVERSAMPLE, seed=rank,
-                                precision=args.precision, device=dev, stream=stream)
-        sweeps, rep = 0, None
-        stages = {k: 0.0 for k in ("halves_ms", "join_ms", "env_finish_ms", "factorize_ms", "gauge_ms",
-                                   "contraction_flops", "launches")}
-        while sweeps < MAX_SWEEPS:
-            rep = f.sweep(1)
-            sweeps += 1
-            st = f.stage_times()
-            for k in stages:
-                stages[k] += st[k]
-            if rep["converged"]:
-                break
-        C = f.result()
-        d2h = 0
-        if host:
-            Ch = [c.to("cpu", non_blocking=True) for c in C]
-            d2h = sum(c.numel() * c.element_size() for c in Ch)
-        f.destroy()
-        return rep, sweeps, stages, C, d2h
 
     def barrier():
         if world > 1:
@@ -155,23 +174,23 @@ def native(args):
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
-        one_fit(Ad, Bd)
+        run_fit(ttfit, Ad, Bd, args.precision, rank, dev, stream, chi)
         flush.zero_()
     barrier()
     clocks = ClockSampler(local)
-    times, reps, stage_acc = [], [], []
+    times, results = [], []
     t_wall0 = time.time()
     for _ in range(args.steps):
         flush.zero_()                       # L2 flushed between timed steps
+        barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        rep, sweeps, stages, C, _ = one_fit(Ad, Bd)
+        res = run_fit(ttfit, Ad, Bd, args.precision, rank, dev, stream, chi)
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
-        reps.append((rep, sweeps))
-        stage_acc.append(stages)
+        results.append(res)
     barrier()
     wall = time.time() - t_wall0
     clk = clocks.stop()
@@ -183,60 +202,82 @@ def native(args):
 
     e2e = None
     if not args.no_e2e:
-        et = []
-        h2d = sum(a.numel() * a.element_size() for a in Ah + Bh)
-        d2h = 0
+        # the public API end to end: pinned host inputs -> device, the fit, C -> host
+        et, h2d, d2h = [], 0, 0
         for _ in range(max(1, min(args.steps, 2))):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            _, _, _, _, d2h = one_fit(Ah, Bh, host=True)
+            Ain = [a.to(dev, non_blocking=True) for a in Ah]
+            Bin = [b.to(dev, non_blocking=True) for b in Bh]
+            _, _, _, _, C, _ = run_fit(ttfit, Ain, Bin, args.precision, rank, dev, stream, chi)
+            Ch = [c.to("cpu") for c in C]
             torch.cuda.synchronize()
             et.append(time.perf_counter() - t0)
-        e2e = {"value": statistics.mean(et), "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+            h2d = sum(a.numel() * a.element_size() for a in Ah + Bh)
+            d2h = sum(c.numel() * c.element_size() for c in Ch)
+        e2e = {"value": round(statistics.mean(et), 4), "unit": "s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
 
-    # live per-stage times (CUDA events on the launching stream, inside the timed steps)
-    agg = {k: statistics.mean(s[k] for s in stage_acc) for k in stage_acc[0]}
-    contr_ms = agg["halves_ms"] + agg["join_ms"] + agg["env_finish_ms"]
-    local_tflops = agg["contraction_flops"] / (contr_ms * 1e-3) / 1e12 if contr_ms > 0 else 0.0
+    # live per-stage times: CUDA events recorded by the library on the caller's stream, inside the
+    # timed steps, accumulated per precision phase and averaged over the steps
+    names = list(results[0][3].keys())
+    agg = {p: {k: statistics.mean(r[3][p][k] for r in results) for k in STAGES} for p in names}
     pk = peaks()
-    stage_ms = {k: agg[k] for k in ("halves_ms", "join_ms", "env_finish_ms", "factorize_ms", "gauge_ms")}
-    dominant = max(stage_ms, key=stage_ms.get)
-    # plain FP32 CUDA-core contractions: ALU bound, peak = 152 SMs x 128 FP32 FMA x 2 x 2.07 GHz
-    fp32_alu_peak = 152 * 128 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    if args.precision in ("fp32", "fp64"):
-        peak = fp32_alu_peak if args.precision == "fp32" else 152 * 2 * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": round(local_tflops, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-                "frac": round(local_tflops / peak, 4), "traffic": None,
-                "kernel": "contraction chain (halves + two-site join + environment finish)",
-                "peak_source": "derived: 152 SMs x FMA lanes x 2 x max SM clock"}
+    mhz = pk.get("sm_max_mhz", 2070.0)
+    rows = []
+    for p in names:
+        a = agg[p]
+        chain_ms = a["halves_ms"] + a["join_ms"] + a["env_finish_ms"]
+        rows.append((chain_ms, p, "chain", a["contraction_flops"]))
+        rows.append((a["factorize_ms"], p, "factorize", 0.0))
+        rows.append((a["gauge_ms"], p, "gauge", 0.0))
+    dom_ms, dom_phase, dom_stage, dom_flops = max(rows)
+    if dom_stage == "chain":
+        tflops = dom_flops / (dom_ms * 1e-3) / 1e12
+        if dom_phase in ("fp64", "fp32"):
+            dt = "f64" if dom_phase == "fp64" else "f32"
+            peak = 152 * FMA_LANES[dt] * 2 * mhz * 1e6 / 1e12
+            roof = {"bound": "alu", "achieved": round(tflops, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+                    "frac": round(tflops / peak, 4), "traffic": None,
+                    "kernel": f"gemm_simt_kernel<{'double' if dt == 'f64' else 'float'}> (contraction chain, "
+                              f"{dom_phase} phase)",
+                    "peak_source": f"derived: 152 SMs x {FMA_LANES[dt]} {dt} FMA/clk x 2 x {mhz:.0f} MHz"}
+        else:
+            bf16 = pk.get("bf16_tflops_sustained", 1700.0)
+            ratio = 2.0 if dom_phase == "tf32" else 6.0       # TF32 is half the bf16 rate; 3xTF32 issues 3 MMAs
+            peak = bf16 / ratio
+            roof = {"bound": "tensor", "achieved": round(tflops, 3), "peak": round(peak, 1), "unit": "TFLOP/s",
+                    "frac": round(tflops / peak, 4), "traffic": None,
+                    "kernel": f"gemm_tf32_kernel (contraction chain, {dom_phase} phase)",
+                    "peak_source": f"of measured: bf16 sustained / {ratio:g}"}
     else:
-        peak = pk.get("bf16_tflops", 1900.0) / (2.0 if args.precision == "tf32" else 1.0)
-        roof = {"bound": "tensor", "achieved": round(local_tflops, 3), "peak": round(peak, 1), "unit": "TFLOP/s",
-                "frac": round(local_tflops / peak, 4), "traffic": None,
-                "kernel": "contraction chain (halves + two-site join + environment finish)",
-                "peak_source": "MEASURED_PEAKS.json bf16 burst" + (" / 2 (tf32 nominal ratio)" if args.precision == "tf32" else "")}
-    last_rep, last_sweeps = reps[-1]
+        roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None, "traffic": None,
+                "kernel": f"{dom_stage} ({dom_phase} phase)"}
+    local_flops = sum(agg[p]["contraction_flops"] for p in names)
+    local_ms = sum(agg[p]["halves_ms"] + agg[p]["join_ms"] + agg[p]["env_finish_ms"] for p in names)
+    rep, sweeps, phase_sweeps, _, _, launches = results[-1]
+    dtypes = {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "tf32x3": "tf32x3"}
     out = {
         "metric": METRIC, "value": round(t_step, 4), "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_step * 1e3, 2), "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "tf32": "tf32",
-                                                           "bf16_split": "bf16x3"}[args.precision],
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "+".join(dtypes.get(p, p) for p in names),
         "data": "synthetic",
-        "config": {"workload": f"{WORKLOAD}: L=30, d=2x2, K=128 Kronecker terms (w=0.8^k), chi_A=chi_B=128, "
-                               f"chi_C=128, randomized update k=chi_C+{OVERSAMPLE}, conv tol {TOL:g}, "
-                               f"max {MAX_SWEEPS} sweeps, site gauge",
-                   "precision": args.precision, "parallelism": f"replicas x{world} (independent MPO pairs)",
+        "config": {"workload": (f"{WORKLOAD}: L=30, d=2x2, K=128 Kronecker terms (w=0.8^k), chi_A=chi_B=128, "
+                               f"chi_C=128, randomized update k=chi_C+{OVERSAMPLE}, conv tol {TOL:g} on the "
+                               f"relative change of ||C||^2, max {MAX_SWEEPS} sweeps, site gauge") if args.workload == WORKLOAD else args.workload,
+                   "schedule": args.precision, "parallelism": f"replicas x{world} (independent MPO pairs)",
                    "l2": "flushed between timed steps (256 MB write)"},
-        "local_update_tflops": round(local_tflops, 3),
-        "sweeps_to_tol": last_sweeps, "converged": bool(last_rep["converged"]), "final_delta": last_rep["delta"],
-        "stage_ms_per_fit": {k: round(v, 3) for k, v in stage_ms.items()}, "dominant_stage": dominant,
-        "roofline": roof, "clocks": clk, "e2e": e2e,
-        "gpu_launches": int(agg["launches"]), "fits_per_s": round(world / t_step, 4),
-        "wall_s_timed": round(wall, 2),
+        "sweeps_to_tol": sweeps, "sweeps_per_phase": phase_sweeps, "converged": bool(rep["converged"]),
+        "final_delta": rep["delta"], "norm2_C": rep["norm2_C"],
+        "local_update_tflops": round(local_flops / (local_ms * 1e-3) / 1e12, 3) if local_ms > 0 else None,
+        "stage_ms_per_fit": {p: {k: round(agg[p][k], 2) for k in STAGES[:5]} for p in names},
+        "roofline": roof, "clocks": clk, "e2e": e2e, "gpu_launches": int(sum(r[5] for r in results)), "gpu_launches_per_step": int(launches),
+        "fits_per_s": round(world / t_step, 4), "wall_s_timed": round(wall, 2),
     }
-    if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(last_sweeps)
+    if rank == 0 and not args.no_cpu_baseline and args.workload == WORKLOAD:
+        out["cpu_baseline"] = cpu_baseline(sweeps)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -178,6 +178,12 @@ const char* tt_fit_last_error(const tt_fit* h);
  * sweep ran. */
 tt_status tt_fit_stage_times(const tt_fit* h, double out[7]);
 
+/* Kernel launches issued by this handle since tt_fit_create, cumulative over
+ * creation (input preparation, initial guess, right environments), sweeps,
+ * precision switches and result export. Lets a caller check that the work it
+ * timed ran in this library's kernels. */
+tt_status tt_fit_launch_count(const tt_fit* h, long long* n);
+
 /* Truncated SVD of one device matrix, the factorisation of the local update
  * (Sec. 2.3.4): M is m x n, row-major, FP64 (device). Computes the thin SVD
  * M = U diag(S) Vt in FP64 (one-sided Jacobi; singular values descending;

@@ -122,7 +122,8 @@ struct tt_fit {
   bool gauge_pending = false;  // ev[5], ev[6] recorded but not yet read
   double stage_ms[5] = {0, 0, 0, 0, 0};
   double flops = 0;
-  long long launches = 0, tc_launches = 0;
+  long long launches = 0, tc_launches = 0;  // monotonic since creation
+  long long sweep_launches = 0;              // launches of the last tt_fit_sweep call
   bool have_times = false;
   bool use_f32 = false;   // chain type: float (non-FP64 precisions) or double
   bool fact_f32 = false;  // FP32 factorisation + FP64 polish (always for float chains; optional for FP64)
@@ -1219,7 +1220,7 @@ tt_status tt_fit_sweep(tt_fit* h, int n_sweeps, tt_sweep_report* rep) {
   try {
     for (double& s : h->stage_ms) s = 0;
     h->flops = 0;
-    h->launches = 0;
+    const long long launch0 = h->launches;
     if (h->use_f32) {
       Sweeper<float> sw(h);
       sw.run(n_sweeps);
@@ -1228,6 +1229,7 @@ tt_status tt_fit_sweep(tt_fit* h, int n_sweeps, tt_sweep_report* rep) {
       sw.run(n_sweeps);
     }
     CK(cudaStreamSynchronize(h->st));
+    h->sweep_launches = h->launches - launch0;
     h->have_times = true;
   } catch (const TTError& e) {
     poison(h, e);
@@ -1280,16 +1282,20 @@ tt_status tt_fit_result(const tt_fit* hc, tt_mpo_desc* C, double* lambdas) {
       const int rows = D.c[l] * D.ds[l] * D.dt[l], cols = D.c[l + 1];
       // C_l = Psi_l Y_l for l < L (inverse gauge); Y = 1 in the site gauge
       const bool scale = (h->gauge == TT_GAUGE_INVERSE_CANONICAL) && (l < L - 1);
-      double* tmp = h->pool.alloc<double>((size_t)rows * cols);
-      CK(scale_cols(rows, cols, h->C64[l], scale ? h->Y[l + 1] : nullptr, tmp, h->st));
-      if (C->dtype == TT_DTYPE_F64)
-        CK(cudaMemcpyAsync(C->cores[l], tmp, sizeof(double) * (size_t)rows * cols, cudaMemcpyDeviceToDevice, h->st));
-      else
+      if (C->dtype == TT_DTYPE_F64) {
+        CK(scale_cols(rows, cols, h->C64[l], scale ? h->Y[l + 1] : nullptr, (double*)C->cores[l], h->st));
+        h->launches += 1;
+      } else {
+        double* tmp = h->pool.alloc<double>((size_t)rows * cols);
+        CK(scale_cols(rows, cols, h->C64[l], scale ? h->Y[l + 1] : nullptr, tmp, h->st));
         CK(copy_map<double, float>(1, rows * cols, tmp, IdxMap::lin(0), IdxMap::lin(1), (float*)C->cores[l],
                                    IdxMap::lin(0), IdxMap::lin(1), 1.0, h->st));
-      CK(cudaStreamSynchronize(h->st));
-      h->pool.release(tmp);
+        CK(cudaStreamSynchronize(h->st));
+        h->pool.release(tmp);
+        h->launches += 2;
+      }
     }
+    CK(cudaStreamSynchronize(h->st));
   } catch (const TTError& e) {
     poison(h, e);
     return e.code;
@@ -1324,7 +1330,13 @@ tt_status tt_fit_stage_times(const tt_fit* h, double out[7]) {
   if (!h->have_times) return TT_ERR_STATE;
   for (int i = 0; i < 5; ++i) out[i] = h->stage_ms[i];
   out[5] = h->flops;
-  out[6] = (double)h->launches;
+  out[6] = (double)h->sweep_launches;
+  return TT_OK;
+}
+
+tt_status tt_fit_launch_count(const tt_fit* h, long long* n) {
+  if (!h || !n) return TT_ERR_INVALID_ARGUMENT;
+  *n = h->launches;
   return TT_OK;
 }
 

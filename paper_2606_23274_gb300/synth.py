@@ -106,4 +106,6 @@ WORKLOADS = {
     "kron_L10_chi16": dict(kind="kron", L=10, K=16, chi_C=16),
     "kron_L12_chi32": dict(kind="kron", L=12, K=32, chi_C=32),
     "uniform_L12_chi12": dict(kind="uniform", L=12, chi=12, alpha=-0.5, chi_C=12),
+    # the timed workload's window shapes (chi = 128 at the middle sites) on a short chain, for profiling
+    "kron_L10_chi128": dict(kind="kron", L=10, K=128, chi_C=128),
 }

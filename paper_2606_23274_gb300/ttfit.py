@@ -81,6 +81,8 @@ def load():
         lib.tt_fit_set_precision.restype = ct.c_int
         lib.tt_fit_stage_times.argtypes = [ct.c_void_p, ct.POINTER(ct.c_double)]
         lib.tt_fit_stage_times.restype = ct.c_int
+        lib.tt_fit_launch_count.argtypes = [ct.c_void_p, ct.POINTER(ct.c_longlong)]
+        lib.tt_fit_launch_count.restype = ct.c_int
         _lib = lib
     return _lib
 
@@ -263,6 +265,12 @@ class Fit:
         keys = ["halves_ms", "join_ms", "env_finish_ms", "factorize_ms", "gauge_ms", "contraction_flops",
                 "launches"]
         return dict(zip(keys, list(v)))
+
+    def launch_count(self) -> int:
+        """Kernel launches this fit has issued since creation (tt_fit_launch_count)."""
+        n = ct.c_longlong(0)
+        _check(load().tt_fit_launch_count(self.h, ct.byref(n)), self.h, "tt_fit_launch_count")
+        return int(n.value)
 
     def destroy(self):
         if self.h is not None and self.h.value:
