@@ -107,6 +107,12 @@ typedef struct {
   uint32_t fault_inject; /* host-side fault injection for tests (TT_FAULT_*), default 0     */
   int fast_factor;     /* FP64 precision only: 1 = FP32 factorisation + FP64 Newton-Schulz  */
                        /* polish (fast; subspace to FP32 accuracy), 0 (default) = FP64 SVD  */
+  int n_segments;      /* segment-parallel fit (Sec. 4, Alg. 6): number of contiguous       */
+                       /* segments N_p, each >= 2 sites; <= 1 (default) = serial Alg. 5.    */
+                       /* N_p > 1 needs the inverse canonical gauge (the site gauge needs a  */
+                       /* merge, not built); see tt_fit_sweep for what a sweep is then.     */
+  int edge_extra;      /* sites moved from the inner segments to each edge segment (load   */
+                       /* balance of Sec. 4.1: edge segments have one neighbour), default 0 */
 } tt_fit_options;
 
 /* Host-side fault injection (tests only; nothing here touches the device). */
@@ -140,7 +146,19 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
 /* Run up to n_sweeps directional sweeps of Alg. 5 (forward l = 1..L-1, then
  * backward l = L-1..1, alternating; the direction continues across calls).
  * Stops early once converged. rep may be NULL. Synchronises the handle's
- * stream before returning. */
+ * stream before returning.
+ *
+ * Segment-parallel handle (n_segments > 1, Sec. 4, Alg. 6): a sweep is one
+ * phase, i.e. half of a full set of local sweeps. Phase 0: odd segments
+ * (numbered from 1) sweep forward and even ones backward, all concurrently;
+ * then the windows straddling the odd|even boundaries are updated by their
+ * left segment. Phase 1: the directions swap and the even|odd boundaries
+ * follow. Each segment runs on its own stream and host thread, with its own
+ * scratch; the handle's stream waits for all of them. ||C||^2 of a set is
+ * that of its last update (every Psi is an orthogonality centre in the
+ * inverse gauge), and delta compares consecutive full sets, so convergence
+ * is tested after every second phase. The sketch of a window in phase p of
+ * set s uses sweep index 2 s + p. */
 tt_status tt_fit_sweep(tt_fit* h, int n_sweeps, tt_sweep_report* rep);
 
 /* Change the contraction precision for the following sweeps (the paper's
@@ -183,6 +201,32 @@ tt_status tt_fit_stage_times(const tt_fit* h, double out[7]);
  * precision switches and result export. Lets a caller check that the work it
  * timed ran in this library's kernels. */
 tt_status tt_fit_launch_count(const tt_fit* h, long long* n);
+
+/* The segments a fit with these options uses (Sec. 4.1): n_segments
+ * contiguous ranges of >= 2 sites, first[i]..last[i] (0-based, inclusive,
+ * arrays of n_segments). Sites are shared out evenly, the first L mod
+ * n_segments segments taking one more; then up to edge_extra sites move to
+ * each of the two edge segments, taken one at a time from the inner segments
+ * in turn while each keeps >= 2 sites. Host-only; needs no GPU.
+ * TT_ERR_INVALID_ARGUMENT if L < 2 n_segments or an argument is out of range. */
+tt_status tt_partition(int L, int n_segments, int edge_extra, int* first, int* last);
+
+/* Batched fits of independent pairs (A[i], B[i]) with their own chi_max[i]
+ * (uneven sizes allowed), all with the same tol, gauge, n_segments and
+ * options (opt->n_segments is overridden by n_segments; TT_INIT_GIVEN is
+ * rejected). Each handle gets a stream of its own, ordered after opt->stream,
+ * and is created on its own host thread; out[0..n-1] receive the handles,
+ * each destroyed with tt_fit_destroy. On any error every handle created so far
+ * is destroyed, out[] is set to NULL and the first failing status (by index)
+ * is returned. */
+tt_status tt_fit_create_batched(int n, const tt_mpo_desc* A, const tt_mpo_desc* B, const int* chi_max, double tol,
+                                int gauge, int n_segments, const tt_fit_options* opt, tt_fit** out);
+
+/* tt_fit_sweep on n handles concurrently (one host thread each, their own
+ * streams). rep, if not NULL, has n entries. Returns the first non-OK status
+ * by index; handles that failed are poisoned as by tt_fit_sweep, the others
+ * completed their sweeps. */
+tt_status tt_fit_sweep_batched(int n, tt_fit* const* h, int n_sweeps, tt_sweep_report* rep);
 
 /* Truncated SVD of one device matrix, the factorisation of the local update
  * (Sec. 2.3.4): M is m x n, row-major, FP64 (device). Computes the thin SVD

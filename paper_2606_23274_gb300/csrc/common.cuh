@@ -6,6 +6,11 @@
 
 namespace ttfit {
 
+// Kernel launches issued by the calling host thread; every launch site
+// increments it, and the API entry points attribute the difference to their
+// handle.
+inline thread_local long long tl_launches = 0;
+
 // Linear index -> memory offset through a mixed radix of up to three levels,
 // i = (i0 * n1 + i1) * n2 + i2, offset = i0*s0 + i1*s1 + i2*s2. Every tensor
 // permutation used by the contraction chain is a sum of two such maps (rows,

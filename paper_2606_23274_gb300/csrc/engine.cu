@@ -14,7 +14,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <exception>
 #include <memory>
+#include <mutex>
+#include <thread>
 #include <new>
 #include <stdexcept>
 #include <string>
@@ -80,14 +83,42 @@ struct Dims {
 
 }  // namespace
 
+// Working state of one sweep lane: the stream it runs on, its events and
+// timers, the scratch of the chain and of the factorisation, and the pinned
+// host mirrors of its device flags. The handle owns one; a segment-parallel
+// fit owns one more per segment, so that segments run concurrently.
+struct Work {
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  cudaEvent_t ev[10] = {};     // window stages (0..4), gauge update (5, 6), lane join (7), connection finish (8, 9)
+  bool gauge_pending = false;  // ev[5], ev[6] recorded but not yet read
+  bool connect_pending = false;  // ev[8], ev[9] recorded but not yet read
+  double stage_ms[5] = {0, 0, 0, 0, 0};
+  double flops = 0;
+  void *X1 = nullptr, *Zs = nullptr, *Th = nullptr, *gws = nullptr;
+  size_t gws_elems = 0;
+  // factorisation workspace (FP64-sized)
+  double *fX = nullptr, *fQ = nullptr, *fR = nullptr, *fU = nullptr, *fV = nullptr, *fVw = nullptr, *fS = nullptr;
+  double *fUM = nullptr, *fVM = nullptr, *fOm = nullptr, *fY = nullptr, *fBt = nullptr, *fQ2 = nullptr, *fR2 = nullptr;
+  double *pU = nullptr, *pV = nullptr, *pG = nullptr, *pT = nullptr, *pP = nullptr;  // FP64 polish
+  size_t fsz = 0;
+  double* dnorm = nullptr;
+  int* dk = nullptr;
+  double* ddinfo = nullptr;
+  uint32_t* errw = nullptr;
+  int* hk = nullptr;  // pinned host mirrors
+  double* hdinfo = nullptr;
+  uint32_t* herrw = nullptr;
+};
+
 struct tt_fit {
   // configuration
   int L = 0, chi_max = 0, gauge = 0, update = 0, oversample = 10, precision = 0, init = 0;
   double tol = 0, cutoff = 1e-13, conv_tol = 0;
   uint64_t seed = 0;
   uint32_t fault = 0;
-  cudaStream_t st = nullptr;
   int sm_count = 0;
+  int device = 0;
   Dims D;
   DevPool pool;
   // prepared inputs, FP64 natural layout
@@ -97,31 +128,19 @@ struct tt_fit {
   std::vector<std::vector<double>> lam;  // singular values of the last update per bond
   // contraction tensors in the working type (float or double)
   std::vector<void*> Aop, Anat, Bl, Br, Lenv, Renv, H1, H2, H1t, H2t, Ut, Vt;
-  void *X1 = nullptr, *Zs = nullptr, *Th = nullptr, *gws = nullptr;
-  size_t gws_elems = 0;
-  // factorisation workspace (FP64)
-  double *fX, *fQ, *fR, *fU, *fV, *fVw, *fS, *fUM, *fVM, *fOm, *fY, *fBt, *fQ2, *fR2;
-  double *pU = nullptr, *pV = nullptr, *pG = nullptr, *pT = nullptr, *pP = nullptr, *dn2 = nullptr;  // FP64 polish
-  size_t fsz = 0;
-  double* dnorm = nullptr;
-  int* dk = nullptr;
-  double* ddinfo = nullptr;
-  uint32_t* errw = nullptr;
-  // host mirrors (pinned)
-  int* hk = nullptr;
-  double* hdinfo = nullptr;
-  uint32_t* herrw = nullptr;
+  double* dn2 = nullptr;  // per window: ||C||^2 of the last polished update (FP64)
+  Work w0;                                 // the handle's own lane (its stream is the caller's)
+  std::vector<std::unique_ptr<Work>> wseg;  // one lane per segment (segment-parallel fit)
+  // segment-parallel fit (Alg. 6): 0-based inclusive site ranges
+  std::vector<std::pair<int, int>> segs;
+  int phases_done = 0;
   // state
   int sweeps_done = 0;
   bool forward = true, converged = false, poisoned = false;
   double last_n2 = -1.0, delta = INFINITY, max_disc = 0.0;
+  double cur_n2 = -1.0;  // ||C||^2 after the latest phase (segment-parallel fit)
   bool fault_nan_pending = false, fault_noconv_pending = false;
   std::string last_error;
-  // timing
-  cudaEvent_t ev[8] = {};      // stage boundaries of one window (0..4) and of its gauge update (5, 6)
-  bool gauge_pending = false;  // ev[5], ev[6] recorded but not yet read
-  double stage_ms[5] = {0, 0, 0, 0, 0};
-  double flops = 0;
   long long launches = 0, tc_launches = 0;  // monotonic since creation
   long long sweep_launches = 0;              // launches of the last tt_fit_sweep call
   bool have_times = false;
@@ -129,6 +148,20 @@ struct tt_fit {
   bool fact_f32 = false;  // FP32 factorisation + FP64 polish (always for float chains; optional for FP64)
   std::vector<void*> chain_bufs;  // buffers rebuilt when the chain precision changes
 };
+
+namespace {
+
+// The lane the calling host thread works in: a segment thread sets it to its
+// segment's lane; everywhere else it is the handle's own.
+thread_local Work* tl_work = nullptr;
+inline Work& W(tt_fit* h) { return tl_work ? *tl_work : h->w0; }
+inline std::vector<Work*> lanes(tt_fit* h) {
+  std::vector<Work*> v{&h->w0};
+  for (auto& w : h->wseg) v.push_back(w.get());
+  return v;
+}
+
+}  // namespace
 
 namespace {
 
@@ -146,37 +179,33 @@ inline long long prodll(std::initializer_list<long long> v) {
 // (FP64 / FP32 chains, and the 1- or 2-wide bonds at the ends of the chain).
 template <typename T>
 void gemm(tt_fit* h, const GemmArgs<T>& g, bool chain = false) {
-  const size_t wse = h->gws_elems * sizeof(double) / sizeof(T);
+  const size_t wse = W(h).gws_elems * sizeof(double) / sizeof(T);
   if constexpr (sizeof(T) == 4) {
     const bool tc = h->precision == TT_PREC_TF32 || h->precision == TT_PREC_TF32_SPLIT;
     if (chain && tc && (long long)g.M * g.N * g.K >= (1ll << 18)) {
-      cudaError_t e = gemm_tf32(g, (float*)h->gws, wse, h->sm_count, h->errw, h->st,
+      cudaError_t e = gemm_tf32(g, (float*)W(h).gws, wse, h->sm_count, W(h).errw, W(h).st,
                                 h->precision == TT_PREC_TF32_SPLIT);
       if (e == cudaSuccess) {
-        h->launches += 2;
         h->tc_launches += 1;
         return;
       }
       if (e != cudaErrorNotSupported) CK(e);
     }
   }
-  CK(gemm_simt<T>(g, (T*)h->gws, wse, h->sm_count, h->st));
-  h->launches += 2;
+  CK(gemm_simt<T>(g, (T*)W(h).gws, wse, h->sm_count, W(h).st));
 }
 
 template <typename Tin, typename Tout>
 void copymap(tt_fit* h, int rows, int cols, const Tin* in, IdxMap im, IdxMap in_, Tout* out, IdxMap om, IdxMap on,
              double scale = 1.0) {
-  CK(copy_map<Tin, Tout>(rows, cols, in, im, in_, out, om, on, scale, h->st));
-  h->launches += 1;
+  CK(copy_map<Tin, Tout>(rows, cols, in, im, in_, out, om, on, scale, W(h).st));
 }
 
 // QR on FP64 storage (input preparation and the guess): FP64 arithmetic; mixing
 // FP32 arithmetic with FP64 storage is slower on this GPU (conversions run on
 // the FP64 pipe).
 void qr(tt_fit* h, int q, int p, double* X, double* Q, double* R) {
-  CK(qr_householder<double, double>(q, p, X, Q, R, h->st));
-  h->launches += 1;
+  CK(qr_householder<double, double>(q, p, X, Q, R, W(h).st));
 }
 
 // Row-major (rows x cols) -> column-major copy (ld rows).
@@ -196,12 +225,10 @@ struct Prep {
 
 void prep_qr(tt_fit* h, Prep& P, int q, int p) {
   CK(qr_householder<double, double>(q, p, P.X, P.Q, P.R, P.st));
-  h->launches += 1;
 }
 
 void prep_gemm(tt_fit* h, Prep& P, const GemmArgs<double>& g) {
   CK(gemm_simt<double>(g, P.ws, P.ws_elems, h->sm_count, P.st));
-  h->launches += 2;
 }
 
 // Right-to-left RQ sweep: each core becomes the orthonormal-row factor of its
@@ -284,7 +311,6 @@ void qr_sweep(tt_fit* h, Prep& P, std::vector<double*>& X, std::vector<int>& bon
     X[j] = nc;
     X[j + 1] = nn;
     bond[j + 1] = r;
-    h->launches += 2;
   }
 }
 
@@ -311,11 +337,43 @@ void finish_prep(tt_fit* h, Prep& P) {
   P.st = nullptr;
 }
 
+// Events, pinned mirrors and device flags of a lane.
+void init_lane(tt_fit* h, Work& w, cudaStream_t st, bool own_stream) {
+  w.st = st;
+  w.own_stream = own_stream;
+  w.dnorm = h->pool.alloc<double>(1);
+  w.dk = h->pool.alloc<int>(4);
+  w.ddinfo = h->pool.alloc<double>(4);
+  w.errw = h->pool.alloc<uint32_t>(4);  // [0] error bits, [1] max Jacobi sweeps (diagnostic)
+  CK(cudaMemsetAsync(w.errw, 0, 4 * sizeof(uint32_t), w.st));
+  for (auto& e : w.ev) CK(cudaEventCreate(&e));
+  CK(cudaMallocHost(&w.hk, sizeof(int) * 4));
+  CK(cudaMallocHost(&w.hdinfo, sizeof(double) * 4));
+  CK(cudaMallocHost(&w.herrw, sizeof(uint32_t) * 4));
+  *w.herrw = 0;
+}
+
+void free_lane(Work& w) {
+  if (w.st) cudaStreamSynchronize(w.st);
+  for (auto& e : w.ev)
+    if (e) cudaEventDestroy(e), e = nullptr;
+  if (w.hk) cudaFreeHost(w.hk), w.hk = nullptr;
+  if (w.hdinfo) cudaFreeHost(w.hdinfo), w.hdinfo = nullptr;
+  if (w.herrw) cudaFreeHost(w.herrw), w.herrw = nullptr;
+  if (w.own_stream && w.st) cudaStreamDestroy(w.st);
+  w.st = nullptr;
+}
+
+void free_lanes(tt_fit* h) {
+  for (auto& w : h->wseg) free_lane(*w);
+  free_lane(h->w0);
+}
+
 void check_errw(tt_fit* h, const char* where) {
-  if (*h->herrw & ERRW_NAN) throw TTError(TT_ERR_NUMERICAL, std::string("non-finite two-site tensor at ") + where);
-  if (*h->herrw & ERRW_NOCONV) throw TTError(TT_ERR_NUMERICAL, std::string("Jacobi SVD did not converge at ") + where);
-  if (*h->herrw & ERRW_TIMEOUT) throw TTError(TT_ERR_TIMEOUT, std::string("bounded device wait expired at ") + where);
-  if (*h->herrw) throw TTError(TT_ERR_NUMERICAL, std::string("device error word set at ") + where);
+  if (*W(h).herrw & ERRW_NAN) throw TTError(TT_ERR_NUMERICAL, std::string("non-finite two-site tensor at ") + where);
+  if (*W(h).herrw & ERRW_NOCONV) throw TTError(TT_ERR_NUMERICAL, std::string("Jacobi SVD did not converge at ") + where);
+  if (*W(h).herrw & ERRW_TIMEOUT) throw TTError(TT_ERR_TIMEOUT, std::string("bounded device wait expired at ") + where);
+  if (*W(h).herrw) throw TTError(TT_ERR_NUMERICAL, std::string("device error word set at ") + where);
 }
 
 // ---------------------------------------------------------------------------
@@ -342,7 +400,7 @@ struct Chain {
     g.B = P(h->Aop[j]);
     g.bn = IdxMap::lin(a0);
     g.bk = IdxMap::lin(1);
-    g.C = P(h->X1);
+    g.C = P(W(h).X1);
     g.cm = IdxMap::two(b0, (long long)ds * a1 * b0 * du, du);
     g.cn = IdxMap::three(du, a1, (long long)a1 * b0 * du, 1, (long long)b0 * du);
     gemm<T>(h, g, true);
@@ -350,7 +408,7 @@ struct Chain {
     g2.M = c0 * ds * a1;
     g2.N = dt * b1;
     g2.K = b0 * du;
-    g2.A = P(h->X1);
+    g2.A = P(W(h).X1);
     g2.am = IdxMap::lin((long long)b0 * du);
     g2.ak = IdxMap::lin(1);
     g2.B = P(h->Bl[j]);
@@ -365,7 +423,7 @@ struct Chain {
     g2.cm2 = IdxMap::two(a1, dt, (long long)b1 * K1);
     g2.cn2 = IdxMap::two(b1, 1, K1);
     gemm<T>(h, g2, true);
-    h->flops += 2.0 * g.M * g.N * g.K + 2.0 * g2.M * g2.N * g2.K;
+    W(h).flops += 2.0 * g.M * g.N * g.K + 2.0 * g2.M * g2.N * g2.K;
   }
 
   // H2_j = A_j B_j R_{j+1}, stored [s][t][c1][a0][b0] (bond indices of site j)
@@ -383,7 +441,7 @@ struct Chain {
     g.B = P(h->Renv[j + 1]);
     g.bn = IdxMap::lin(a2);
     g.bk = IdxMap::lin(1);
-    g.C = P(h->Zs);
+    g.C = P(W(h).Zs);
     g.cm = IdxMap::two(du, (long long)c2 * du * b2, b2);
     g.cn = IdxMap::two(b2, (long long)du * b2, 1);
     gemm<T>(h, g, true);
@@ -391,7 +449,7 @@ struct Chain {
     g2.M = a1 * ds * c2;
     g2.N = b1 * dt;
     g2.K = du * b2;
-    g2.A = P(h->Zs);
+    g2.A = P(W(h).Zs);
     g2.am = IdxMap::lin((long long)du * b2);
     g2.ak = IdxMap::lin(1);
     g2.B = P(h->Br[j]);
@@ -406,7 +464,7 @@ struct Chain {
     g2.cm2 = IdxMap::three(ds, c2, (long long)b1 * K2, (long long)dt * c2, 1);
     g2.cn2 = IdxMap::two(dt, K2, c2);
     gemm<T>(h, g2, true);
-    h->flops += 2.0 * g.M * g.N * g.K + 2.0 * g2.M * g2.N * g2.K;
+    W(h).flops += 2.0 * g.M * g.N * g.K + 2.0 * g2.M * g2.N * g2.K;
   }
 
   // Theta(window l, l+1) = H1_l . H2_{l+1}, row-major (c0 s1 t1) x (s2 t2 c2)
@@ -425,11 +483,11 @@ struct Chain {
     g.B = P(h->H2[l + 1]);
     g.bn = IdxMap::lin((long long)a1 * b1);
     g.bk = IdxMap::lin(1);
-    g.C = P(h->Th);
+    g.C = P(W(h).Th);
     g.cm = IdxMap::lin(n);
     g.cn = IdxMap::lin(1);
     gemm<T>(h, g, true);
-    h->flops += 2.0 * g.M * g.N * g.K;
+    W(h).flops += 2.0 * g.M * g.N * g.K;
   }
 
   // L_j (bond j+1) = Ut_j . H1_j ; stored [c][b][a]
@@ -451,7 +509,7 @@ struct Chain {
     g.cm = IdxMap::lin((long long)a1 * b1);
     g.cn = IdxMap::two(b1, 1, a1);
     gemm<T>(h, g, true);
-    h->flops += 2.0 * g.M * g.N * g.K;
+    W(h).flops += 2.0 * g.M * g.N * g.K;
   }
 
   // R_j (bond j) = Vt_j . H2_j ; stored [c][b][a]
@@ -473,7 +531,7 @@ struct Chain {
     g.cm = IdxMap::lin((long long)a0 * b0);
     g.cn = IdxMap::two(b0, 1, a0);
     gemm<T>(h, g, true);
-    h->flops += 2.0 * g.M * g.N * g.K;
+    W(h).flops += 2.0 * g.M * g.N * g.K;
   }
 };
 
@@ -484,25 +542,21 @@ struct Chain {
 // ---------------------------------------------------------------------------
 template <typename T, typename F>
 int factorize(tt_fit* h, int m, int n, int sweep, int site1) {
-  F *fX = (F*)h->fX, *fQ = (F*)h->fQ, *fR = (F*)h->fR, *fU = (F*)h->fU, *fV = (F*)h->fV, *fVw = (F*)h->fVw;
-  F *fS = (F*)h->fS, *fUM = (F*)h->fUM, *fVM = (F*)h->fVM, *fOm = (F*)h->fOm, *MF = (F*)h->fY;
-  F *fBt = (F*)h->fBt, *fQ2 = (F*)h->fQ2, *fR2 = (F*)h->fR2;
+  F *fX = (F*)W(h).fX, *fQ = (F*)W(h).fQ, *fR = (F*)W(h).fR, *fU = (F*)W(h).fU, *fV = (F*)W(h).fV, *fVw = (F*)W(h).fVw;
+  F *fS = (F*)W(h).fS, *fUM = (F*)W(h).fUM, *fVM = (F*)W(h).fVM, *fOm = (F*)W(h).fOm, *MF = (F*)W(h).fY;
+  F *fBt = (F*)W(h).fBt, *fQ2 = (F*)W(h).fQ2, *fR2 = (F*)W(h).fR2;
   auto qrf = [&](int q, int p, F* X, F* Q, F* R) {
-    CK(qr_householder<F, F>(q, p, X, Q, R, h->st));
-    h->launches += 1;
+    CK(qr_householder<F, F>(q, p, X, Q, R, W(h).st));
   };
-  auto jac = [&](int q, int p, F* W, F* U, F* S, F* V) {
-    CK(jacobi_svd<F, F>(q, p, W, U, S, V, fVw, 60, h->errw, h->st));
-    h->launches += 1;
+  auto jac = [&](int q, int p, F* Wm, F* U, F* S, F* V) {
+    CK(jacobi_svd<F, F>(q, p, Wm, U, S, V, fVw, 60, W(h).errw, W(h).st));
   };
   // Theta (T, row-major) -> F copy; norm (flags NaN/Inf)
-  copymap<T, F>(h, m, n, (const T*)h->Th, IdxMap::lin(n), IdxMap::lin(1), MF, IdxMap::lin(n), IdxMap::lin(1));
-  CK(frob_norm<F>(MF, (long long)m * n, h->dnorm, h->errw, h->st));
-  h->launches += 1;
+  copymap<T, F>(h, m, n, (const T*)W(h).Th, IdxMap::lin(n), IdxMap::lin(1), MF, IdxMap::lin(n), IdxMap::lin(1));
+  CK(frob_norm<F>(MF, (long long)m * n, W(h).dnorm, W(h).errw, W(h).st));
   const int ks = h->chi_max + h->oversample;
   if (h->update == TT_UPDATE_2SITE_RSVD && ks < std::min(m, n)) {
-    CK(philox_fill<F>(fOm, (long long)n * ks, h->seed, omega_stream(sweep, site1), 1.0, h->st));
-    h->launches += 1;
+    CK(philox_fill<F>(fOm, (long long)n * ks, h->seed, omega_stream(sweep, site1), 1.0, W(h).st));
     GemmArgs<F> g;  // Ysk = M Omega (m x ks, col-major)
     g.M = m; g.N = ks; g.K = n;
     g.A = MF; g.am = IdxMap::lin(n); g.ak = IdxMap::lin(1);
@@ -530,14 +584,13 @@ int factorize(tt_fit* h, int m, int n, int sweep, int site1) {
     g4.B = fU; g4.bn = IdxMap::lin(ks); g4.bk = IdxMap::lin(1);
     g4.C = fVM; g4.cm = IdxMap::lin(1); g4.cn = IdxMap::lin(n);
     gemm<F>(h, g4);
-    CK(fix_signs<F>(m, n, ks, fUM, m, fVM, n, h->st));
-    h->launches += 1;
+    CK(fix_signs<F>(m, n, ks, fUM, m, fVM, n, W(h).st));
     return ks;
   }
   // exact: work on the tall orientation X (q x p col-major)
   const bool tr = m < n;
   const int q = tr ? n : m, p = tr ? m : n;
-  if (tr) CK(cudaMemcpyAsync(fX, MF, sizeof(F) * (size_t)m * n, cudaMemcpyDeviceToDevice, h->st));
+  if (tr) CK(cudaMemcpyAsync(fX, MF, sizeof(F) * (size_t)m * n, cudaMemcpyDeviceToDevice, W(h).st));
   else copymap<F, F>(h, m, n, MF, IdxMap::lin(n), IdxMap::lin(1), fX, IdxMap::lin(1), IdxMap::lin(m));
   F* Ufull;
   if (q > p) {
@@ -557,14 +610,13 @@ int factorize(tt_fit* h, int m, int n, int sweep, int site1) {
   // X = Ufull S Vr^T ; Theta = X (tr = false) or X^T (tr = true)
   const size_t qb = sizeof(F) * (size_t)q * p, pb = sizeof(F) * (size_t)p * p;
   if (!tr) {
-    CK(cudaMemcpyAsync(fUM, Ufull, qb, cudaMemcpyDeviceToDevice, h->st));
-    CK(cudaMemcpyAsync(fVM, fV, pb, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(fUM, Ufull, qb, cudaMemcpyDeviceToDevice, W(h).st));
+    CK(cudaMemcpyAsync(fVM, fV, pb, cudaMemcpyDeviceToDevice, W(h).st));
   } else {
-    CK(cudaMemcpyAsync(fUM, fV, pb, cudaMemcpyDeviceToDevice, h->st));
-    CK(cudaMemcpyAsync(fVM, Ufull, qb, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(fUM, fV, pb, cudaMemcpyDeviceToDevice, W(h).st));
+    CK(cudaMemcpyAsync(fVM, Ufull, qb, cudaMemcpyDeviceToDevice, W(h).st));
   }
-  CK(fix_signs<F>(m, n, p, fUM, m, fVM, n, h->st));
-  h->launches += 1;
+  CK(fix_signs<F>(m, n, p, fUM, m, fVM, n, W(h).st));
   return p;
 }
 
@@ -579,18 +631,18 @@ int factorize(tt_fit* h, int m, int n, int sweep, int site1) {
 // ---------------------------------------------------------------------------
 template <typename F>
 void ns_orthonormalize(tt_fit* h, const F* X32, int rows, int k, double* X64) {
-  double* G = h->pG;
-  copymap<F, double>(h, rows, k, X32, IdxMap::lin(1), IdxMap::lin(rows), h->pT, IdxMap::lin(1), IdxMap::lin(rows));
+  double* G = W(h).pG;
+  copymap<F, double>(h, rows, k, X32, IdxMap::lin(1), IdxMap::lin(rows), W(h).pT, IdxMap::lin(1), IdxMap::lin(rows));
   GemmArgs<double> g;  // G = X^T X (k x k)
   g.M = k; g.N = k; g.K = rows;
-  g.A = h->pT; g.am = IdxMap::lin(rows); g.ak = IdxMap::lin(1);
-  g.B = h->pT; g.bn = IdxMap::lin(rows); g.bk = IdxMap::lin(1);
+  g.A = W(h).pT; g.am = IdxMap::lin(rows); g.ak = IdxMap::lin(1);
+  g.B = W(h).pT; g.bn = IdxMap::lin(rows); g.bk = IdxMap::lin(1);
   g.C = G; g.cm = IdxMap::lin(k); g.cn = IdxMap::lin(1);
   gemm<double>(h, g);
-  CK(cudaMemcpyAsync(X64, h->pT, sizeof(double) * (size_t)rows * k, cudaMemcpyDeviceToDevice, h->st));
+  CK(cudaMemcpyAsync(X64, W(h).pT, sizeof(double) * (size_t)rows * k, cudaMemcpyDeviceToDevice, W(h).st));
   GemmArgs<double> g2;  // X64 = 1.5 X - 0.5 X G
   g2.M = rows; g2.N = k; g2.K = k;
-  g2.A = h->pT; g2.am = IdxMap::lin(1); g2.ak = IdxMap::lin(rows); g2.a_kfast = false;
+  g2.A = W(h).pT; g2.am = IdxMap::lin(1); g2.ak = IdxMap::lin(rows); g2.a_kfast = false;
   g2.B = G; g2.bn = IdxMap::lin(k); g2.bk = IdxMap::lin(1);
   g2.C = X64; g2.cm = IdxMap::lin(1); g2.cn = IdxMap::lin(rows);
   g2.alpha = -0.5;
@@ -600,22 +652,22 @@ void ns_orthonormalize(tt_fit* h, const F* X32, int rows, int k, double* X64) {
 
 template <typename T, typename F>
 void polish_update(tt_fit* h, int mode, int m, int n, int k, int l) {
-  const T* Th = (const T*)h->Th;
+  const T* Th = (const T*)W(h).Th;
   T* Ut = (T*)h->Ut[l];
   T* Vt = (T*)h->Vt[l + 1];
-  T* P = (T*)h->pP;  // m x k (or k x n) projection, then the k x k block
+  T* P = (T*)W(h).pP;  // m x k (or k x n) projection, then the k x k block
   const int side = std::max(m, n);
   if (mode != 1) {  // left isometry U (m x k)
-    ns_orthonormalize<F>(h, (const F*)h->fUM, m, k, h->pU);
+    ns_orthonormalize<F>(h, (const F*)W(h).fUM, m, k, W(h).pU);
     // Ut (k x m row-major) = U^T : same memory order as U column-major
-    copymap<double, T>(h, 1, m * k, h->pU, IdxMap::lin(0), IdxMap::lin(1), Ut, IdxMap::lin(0), IdxMap::lin(1));
+    copymap<double, T>(h, 1, m * k, W(h).pU, IdxMap::lin(0), IdxMap::lin(1), Ut, IdxMap::lin(0), IdxMap::lin(1));
   }
   if (mode != 0) {  // right isometry V (n x k)
-    ns_orthonormalize<F>(h, (const F*)h->fVM, n, k, h->pV);
-    copymap<double, T>(h, 1, n * k, h->pV, IdxMap::lin(0), IdxMap::lin(1), Vt, IdxMap::lin(0), IdxMap::lin(1));
+    ns_orthonormalize<F>(h, (const F*)W(h).fVM, n, k, W(h).pV);
+    copymap<double, T>(h, 1, n * k, W(h).pV, IdxMap::lin(0), IdxMap::lin(1), Vt, IdxMap::lin(0), IdxMap::lin(1));
   }
   if (mode == 0) {  // site, forward: C_l = U, C_{l+1} = U^T Theta
-    copymap<double, double>(h, m, k, h->pU, IdxMap::lin(1), IdxMap::lin(m), h->C64[l], IdxMap::lin(k), IdxMap::lin(1));
+    copymap<double, double>(h, m, k, W(h).pU, IdxMap::lin(1), IdxMap::lin(m), h->C64[l], IdxMap::lin(k), IdxMap::lin(1));
     GemmArgs<T> g;
     g.M = k; g.N = n; g.K = m;
     g.A = Ut; g.am = IdxMap::lin(m); g.ak = IdxMap::lin(1);
@@ -623,9 +675,9 @@ void polish_update(tt_fit* h, int mode, int m, int n, int k, int l) {
     g.C = P; g.cm = IdxMap::lin(n); g.cn = IdxMap::lin(1);
     gemm<T>(h, g);
     copymap<T, double>(h, 1, k * n, P, IdxMap::lin(0), IdxMap::lin(1), h->C64[l + 1], IdxMap::lin(0), IdxMap::lin(1));
-    CK(frob_norm<T>(P, (long long)k * n, h->dn2 + l, nullptr, h->st));
+    CK(frob_norm<T>(P, (long long)k * n, h->dn2 + l, nullptr, W(h).st));
   } else if (mode == 1) {  // site, backward: C_{l+1} = V^T, C_l = Theta V
-    copymap<double, double>(h, 1, n * k, h->pV, IdxMap::lin(0), IdxMap::lin(1), h->C64[l + 1], IdxMap::lin(0),
+    copymap<double, double>(h, 1, n * k, W(h).pV, IdxMap::lin(0), IdxMap::lin(1), h->C64[l + 1], IdxMap::lin(0),
                             IdxMap::lin(1));
     GemmArgs<T> g;
     g.M = m; g.N = k; g.K = n;
@@ -634,7 +686,7 @@ void polish_update(tt_fit* h, int mode, int m, int n, int k, int l) {
     g.C = P; g.cm = IdxMap::lin(k); g.cn = IdxMap::lin(1);
     gemm<T>(h, g);
     copymap<T, double>(h, 1, m * k, P, IdxMap::lin(0), IdxMap::lin(1), h->C64[l], IdxMap::lin(0), IdxMap::lin(1));
-    CK(frob_norm<T>(P, (long long)m * k, h->dn2 + l, nullptr, h->st));
+    CK(frob_norm<T>(P, (long long)m * k, h->dn2 + l, nullptr, W(h).st));
   } else {  // inverse: Psi_l = U s, Psi_{l+1} = s V^T, Y_l = 1/s with s = diag(U^T Theta V)
     GemmArgs<T> g;  // X = Theta V (m x k)
     g.M = m; g.N = k; g.K = n;
@@ -649,11 +701,9 @@ void polish_update(tt_fit* h, int mode, int m, int n, int k, int l) {
     g2.B = P; g2.bn = IdxMap::lin(1); g2.bk = IdxMap::lin(k); g2.b_kfast = false;
     g2.C = Pk; g2.cm = IdxMap::lin(k); g2.cn = IdxMap::lin(1);
     gemm<T>(h, g2);
-    CK(inverse_gauge_update<T>(m, n, k, h->pU, h->pV, Pk, h->C64[l], h->C64[l + 1], h->Y[l + 1], h->st));
-    CK(frob_norm<T>(Pk, (long long)k * k, h->dn2 + l, nullptr, h->st));
-    h->launches += 2;
+    CK(inverse_gauge_update<T>(m, n, k, W(h).pU, W(h).pV, Pk, h->C64[l], h->C64[l + 1], h->Y[l + 1], W(h).st));
+    CK(frob_norm<T>(Pk, (long long)k * k, h->dn2 + l, nullptr, W(h).st));
   }
-  h->launches += 1;
 }
 
 template <typename T>
@@ -664,48 +714,62 @@ struct Sweeper {
 
   void add(int stage, int e0, int e1) {
     float ms = 0;
-    CK(cudaEventElapsedTime(&ms, h->ev[e0], h->ev[e1]));
-    h->stage_ms[stage] += ms;
+    CK(cudaEventElapsedTime(&ms, W(h).ev[e0], W(h).ev[e1]));
+    W(h).stage_ms[stage] += ms;
   }
   // the previous window's gauge update has completed once the stream has been synchronised
   void resolve_gauge() {
-    if (h->gauge_pending) add(4, 5, 6);
-    h->gauge_pending = false;
+    if (W(h).gauge_pending) add(4, 5, 6);
+    W(h).gauge_pending = false;
+    if (W(h).connect_pending) add(2, 8, 9);
+    W(h).connect_pending = false;
   }
 
+  // Environment handling of a window (0-based window l = sites l, l+1):
+  //   ENV_SERIAL  Alg. 5: forward finishes L_l from the cached half of site l-1, backward R_{l+2};
+  //   ENV_NONE    first window of a local sweep of Alg. 6: the stored boundary environment is used;
+  //   ENV_CONNECT connection update of Alg. 6: both environments are finished first, both halves are
+  //               fresh, and L_{l+1}, R_{l+1} across the new bond are finished afterwards.
+  enum { ENV_SERIAL = 0, ENV_NONE = 1, ENV_CONNECT = 2 };
+
   // one window update; returns kept sum of s^2 and the discarded fraction
-  void window(int l, bool fwd, int sweep, double& n2, double& disc) {
+  void window(int l, bool fwd, int sweep, double& n2, double& disc, int env = ENV_SERIAL) {
     Dims& D = h->D;
     const int L = D.L;
-    CK(cudaEventRecord(h->ev[0], h->st));
-    if (fwd) {
+    CK(cudaEventRecord(W(h).ev[0], W(h).st));
+    if (env == ENV_CONNECT) {
       if (l >= 1) ch.finish_left(l - 1);
-      CK(cudaEventRecord(h->ev[1], h->st));
+      if (l + 2 <= L - 1) ch.finish_right(l + 2);
+      CK(cudaEventRecord(W(h).ev[1], W(h).st));
+      ch.half_left(l);
+      ch.half_right(l + 1);
+    } else if (fwd) {
+      if (l >= 1 && env == ENV_SERIAL) ch.finish_left(l - 1);
+      CK(cudaEventRecord(W(h).ev[1], W(h).st));
       ch.half_left(l);
     } else {
-      if (l + 2 <= L - 1) ch.finish_right(l + 2);
-      CK(cudaEventRecord(h->ev[1], h->st));
+      if (l + 2 <= L - 1 && env == ENV_SERIAL) ch.finish_right(l + 2);
+      CK(cudaEventRecord(W(h).ev[1], W(h).st));
       ch.half_right(l + 1);
     }
-    CK(cudaEventRecord(h->ev[2], h->st));
+    CK(cudaEventRecord(W(h).ev[2], W(h).st));
     int m, n;
     ch.join(l, m, n);
-    CK(cudaEventRecord(h->ev[3], h->st));
+    CK(cudaEventRecord(W(h).ev[3], W(h).st));
     int p;
     if (h->fact_f32) {
       p = factorize<T, float>(h, m, n, sweep, l + 1);
-      CK(truncate_rule<float>((const float*)h->fS, p, h->dnorm, h->tol / L, h->chi_max, h->cutoff, h->dk, h->ddinfo,
-                              h->st));
+      CK(truncate_rule<float>((const float*)W(h).fS, p, W(h).dnorm, h->tol / L, h->chi_max, h->cutoff, W(h).dk, W(h).ddinfo,
+                              W(h).st));
     } else {
       p = factorize<T, T>(h, m, n, sweep, l + 1);
-      CK(truncate_rule<T>((const T*)h->fS, p, h->dnorm, h->tol / L, h->chi_max, h->cutoff, h->dk, h->ddinfo, h->st));
+      CK(truncate_rule<T>((const T*)W(h).fS, p, W(h).dnorm, h->tol / L, h->chi_max, h->cutoff, W(h).dk, W(h).ddinfo, W(h).st));
     }
-    h->launches += 1;
-    CK(cudaEventRecord(h->ev[4], h->st));
-    CK(cudaMemcpyAsync(h->hk, h->dk, sizeof(int), cudaMemcpyDeviceToHost, h->st));
-    CK(cudaMemcpyAsync(h->hdinfo, h->ddinfo, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st));
-    CK(cudaMemcpyAsync(h->herrw, h->errw, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->st));
-    CK(cudaStreamSynchronize(h->st));
+    CK(cudaEventRecord(W(h).ev[4], W(h).st));
+    CK(cudaMemcpyAsync(W(h).hk, W(h).dk, sizeof(int), cudaMemcpyDeviceToHost, W(h).st));
+    CK(cudaMemcpyAsync(W(h).hdinfo, W(h).ddinfo, 2 * sizeof(double), cudaMemcpyDeviceToHost, W(h).st));
+    CK(cudaMemcpyAsync(W(h).herrw, W(h).errw, sizeof(uint32_t), cudaMemcpyDeviceToHost, W(h).st));
+    CK(cudaStreamSynchronize(W(h).st));
     add(2, 0, 1);
     add(0, 1, 2);
     add(1, 2, 3);
@@ -713,40 +777,46 @@ struct Sweeper {
     resolve_gauge();
     if (h->fault_nan_pending) {
       h->fault_nan_pending = false;
-      *h->herrw |= ERRW_NAN;
+      *W(h).herrw |= ERRW_NAN;
     }
     if (h->fault_noconv_pending) {
       h->fault_noconv_pending = false;
-      *h->herrw |= ERRW_NOCONV;
+      *W(h).herrw |= ERRW_NOCONV;
     }
     char where[64];
     snprintf(where, sizeof where, "window %d", l + 1);
     check_errw(h, where);
-    const int k = *h->hk;
-    n2 = h->hdinfo[0];
-    disc = h->hdinfo[1];
+    const int k = *W(h).hk;
+    n2 = W(h).hdinfo[0];
+    disc = W(h).hdinfo[1];
     if (k < 1 || k > D.cb[l + 1]) throw TTError(TT_ERR_NUMERICAL, "kept rank outside the bond capacity");
     D.c[l + 1] = k;
     // gauge update (Alg. 3 / Alg. 4)
     const int mode = (h->gauge == TT_GAUGE_INVERSE_CANONICAL) ? 2 : (fwd ? 0 : 1);
-    CK(cudaEventRecord(h->ev[5], h->st));
+    CK(cudaEventRecord(W(h).ev[5], W(h).st));
     if (!h->fact_f32) {
-      CK(gauge_update<T, T>(mode, m, n, (const T*)h->fUM, m, (const T*)h->fS, (const T*)h->fVM, n, h->dk, h->C64[l],
-                            h->C64[l + 1], h->Y[l + 1], (T*)h->Ut[l], (T*)h->Vt[l + 1], h->st));
-      h->launches += 1;
+      CK(gauge_update<T, T>(mode, m, n, (const T*)W(h).fUM, m, (const T*)W(h).fS, (const T*)W(h).fVM, n, W(h).dk, h->C64[l],
+                            h->C64[l + 1], h->Y[l + 1], (T*)h->Ut[l], (T*)h->Vt[l + 1], W(h).st));
     } else {
       polish_update<T, float>(h, mode, m, n, k, l);
     }
-    CK(cudaEventRecord(h->ev[6], h->st));
-    h->gauge_pending = true;
+    CK(cudaEventRecord(W(h).ev[6], W(h).st));
+    W(h).gauge_pending = true;
+    if (env == ENV_CONNECT) {  // environments across the updated bond, for both neighbours
+      CK(cudaEventRecord(W(h).ev[8], W(h).st));
+      ch.finish_left(l);
+      ch.finish_right(l + 1);
+      CK(cudaEventRecord(W(h).ev[9], W(h).st));
+      W(h).connect_pending = true;
+    }
     // host copy of the kept spectrum for tt_fit_result
     if (h->fact_f32) {
       std::vector<float> sv(k);
-      CK(cudaMemcpyAsync(sv.data(), h->fS, sizeof(float) * k, cudaMemcpyDeviceToHost, h->st));
+      CK(cudaMemcpyAsync(sv.data(), W(h).fS, sizeof(float) * k, cudaMemcpyDeviceToHost, W(h).st));
       h->lam[l + 1].assign(sv.begin(), sv.end());
     } else {
       std::vector<double> sv(k);
-      CK(cudaMemcpyAsync(sv.data(), h->fS, sizeof(double) * k, cudaMemcpyDeviceToHost, h->st));
+      CK(cudaMemcpyAsync(sv.data(), W(h).fS, sizeof(double) * k, cudaMemcpyDeviceToHost, W(h).st));
       h->lam[l + 1].assign(sv.begin(), sv.end());
     }
   }
@@ -768,7 +838,7 @@ struct Sweeper {
           maxd = std::max(maxd, disc);
         }
       }
-      CK(cudaStreamSynchronize(h->st));
+      CK(cudaStreamSynchronize(W(h).st));
       resolve_gauge();
       if (h->fact_f32) {  // ||C||^2 from the FP64-orthonormal projection of the last window
         const int lw = h->forward ? L - 2 : 0;
@@ -792,7 +862,7 @@ struct Sweeper {
       ch.half_right(j);
       if (j >= 2) ch.finish_right(j);
     }
-    CK(cudaStreamSynchronize(h->st));
+    CK(cudaStreamSynchronize(W(h).st));
   }
 };
 
@@ -901,35 +971,24 @@ void allocate_chain(tt_fit* h) {
     mmax = std::max<long long>(mmax, (long long)D.cb[j] * ds * dt);
     nmax = std::max<long long>(nmax, (long long)ds * dt * D.cb[j + 1]);
   }
-  h->X1 = calloc_chain<T>(h, x1);
-  h->Zs = calloc_chain<T>(h, zs);
-  h->Th = calloc_chain<T>(h, (size_t)mmax * nmax);
-  // split-K workspace: up to 64 partial M x N tiles of the largest GEMM output we split
-  h->gws_elems = (size_t)std::max<long long>(mmax * nmax, 1) * 16 + (1 << 20);
-  h->gws = calloc_chain<double>(h, h->gws_elems);
-  const long long big = std::max(mmax, nmax);
   const long long ks = h->chi_max + h->oversample;
-  const long long side = std::max(big, ks);
-  h->fsz = (size_t)side * side;
-  h->fX = calloc_chain<double>(h, h->fsz);
-  h->fQ = calloc_chain<double>(h, h->fsz);
-  h->fR = calloc_chain<double>(h, h->fsz);
-  h->fU = calloc_chain<double>(h, h->fsz);
-  h->fV = calloc_chain<double>(h, h->fsz);
-  h->fVw = calloc_chain<double>(h, h->fsz);
-  h->fS = calloc_chain<double>(h, side);
-  h->fUM = calloc_chain<double>(h, h->fsz);
-  h->fVM = calloc_chain<double>(h, h->fsz);
-  h->fOm = calloc_chain<double>(h, h->fsz);
-  h->fY = calloc_chain<double>(h, h->fsz);
-  h->fBt = calloc_chain<double>(h, h->fsz);
-  h->fQ2 = calloc_chain<double>(h, h->fsz);
-  h->fR2 = calloc_chain<double>(h, h->fsz);
-  h->pU = calloc_chain<double>(h, h->fsz);
-  h->pV = calloc_chain<double>(h, h->fsz);
-  h->pG = calloc_chain<double>(h, h->fsz);
-  h->pT = calloc_chain<double>(h, h->fsz);
-  h->pP = calloc_chain<double>(h, (size_t)side * ks + (size_t)ks * ks + 64);
+  const long long side = std::max(std::max(mmax, nmax), ks);
+  auto scratch = [&](Work& w) {
+    w.X1 = calloc_chain<T>(h, x1);
+    w.Zs = calloc_chain<T>(h, zs);
+    w.Th = calloc_chain<T>(h, (size_t)mmax * nmax);
+    // split-K workspace: up to 16 partial M x N tiles of the largest GEMM output we split
+    w.gws_elems = (size_t)std::max<long long>(mmax * nmax, 1) * 16 + (1 << 20);
+    w.gws = calloc_chain<double>(h, w.gws_elems);
+    w.fsz = (size_t)side * side;
+    for (double** f : {&w.fX, &w.fQ, &w.fR, &w.fU, &w.fV, &w.fVw, &w.fUM, &w.fVM, &w.fOm, &w.fY, &w.fBt, &w.fQ2,
+                       &w.fR2, &w.pU, &w.pV, &w.pG, &w.pT})
+      *f = calloc_chain<double>(h, w.fsz);
+    w.fS = calloc_chain<double>(h, side);
+    w.pP = calloc_chain<double>(h, (size_t)side * ks + (size_t)ks * ks + 64);
+  };
+  scratch(h->w0);
+  for (auto& w : h->wseg) scratch(*w);
   h->dn2 = calloc_chain<double>(h, L + 1);
 }
 
@@ -941,7 +1000,7 @@ template <typename T>
 void rebuild_chain(tt_fit* h) {
   Dims& D = h->D;
   const int L = D.L;
-  CK(cudaStreamSynchronize(h->st));
+  CK(cudaStreamSynchronize(W(h).st));
   for (void* p : h->chain_bufs) h->pool.release(p);
   h->chain_bufs.clear();
   build_operands<T>(h);
@@ -949,15 +1008,222 @@ void rebuild_chain(tt_fit* h) {
   for (int j = 0; j < L; ++j) {
     const int rows = D.c[j], cols = D.ds[j] * D.dt[j] * D.c[j + 1];
     const bool inv = h->gauge == TT_GAUGE_INVERSE_CANONICAL && j > 0;
-    CK(scale_rows<T>(rows, cols, h->C64[j], inv ? h->Y[j] : nullptr, (T*)h->Vt[j], h->st));
-    h->launches += 1;
+    CK(scale_rows<T>(rows, cols, h->C64[j], inv ? h->Y[j] : nullptr, (T*)h->Vt[j], W(h).st));
   }
   T one = T(1);
-  CK(cudaMemcpyAsync(h->Lenv[0], &one, sizeof(T), cudaMemcpyHostToDevice, h->st));
-  CK(cudaMemcpyAsync(h->Renv[L], &one, sizeof(T), cudaMemcpyHostToDevice, h->st));
-  CK(cudaStreamSynchronize(h->st));
+  CK(cudaMemcpyAsync(h->Lenv[0], &one, sizeof(T), cudaMemcpyHostToDevice, W(h).st));
+  CK(cudaMemcpyAsync(h->Renv[L], &one, sizeof(T), cudaMemcpyHostToDevice, W(h).st));
+  CK(cudaStreamSynchronize(W(h).st));
   Sweeper<T> sw(h);
   sw.precompute_right();
+}
+
+// ---------------------------------------------------------------------------
+// Segment-parallel fit (Sec. 4, Alg. 6), inverse canonical gauge.
+// ---------------------------------------------------------------------------
+
+// Contiguous segments of >= 2 sites, 0-based inclusive ranges. The sites are
+// shared out as evenly as possible (the first L mod N_p segments get one
+// more); edge_extra sites then move to each edge segment, taken one at a time
+// from the inner segments in turn, as far as the inner segments keep 2 sites
+// (Sec. 4.1: an edge segment has one neighbour, so it can do more local work).
+std::vector<std::pair<int, int>> partition_sites(int L, int n_seg, int edge_extra) {
+  std::vector<int> size(n_seg, L / n_seg);
+  for (int i = 0; i < L % n_seg; ++i) size[i] += 1;
+  if (n_seg >= 3 && edge_extra > 0) {
+    int spare = 0;
+    for (int i = 1; i < n_seg - 1; ++i) spare += size[i] - 2;
+    const int take = std::max(0, std::min(edge_extra, spare / 2));
+    size[0] += take;
+    size[n_seg - 1] += take;
+    for (int need = 2 * take, i = 0; need > 0; --need, ++i) size[1 + i % (n_seg - 2)] -= 1;
+  }
+  std::vector<std::pair<int, int>> out;
+  for (int i = 0, s0 = 0; i < n_seg; ++i) {
+    out.emplace_back(s0, s0 + size[i] - 1);
+    s0 += size[i];
+  }
+  return out;
+}
+
+// Runs fn(0..n-1) on n host threads with the handle's device current; the
+// first exception is rethrown here. Kernel launches of the threads are added
+// to this thread's launch counter.
+template <typename Fn>
+void run_threads(tt_fit* h, int n, Fn fn) {
+  std::vector<std::thread> th;
+  std::vector<long long> launched(n, 0);
+  std::mutex mu;
+  std::exception_ptr first;
+  for (int i = 0; i < n; ++i)
+    th.emplace_back([&, i] {
+      const long long l0 = tl_launches;
+      try {
+        CK(cudaSetDevice(h->device));
+        fn(i);
+      } catch (...) {
+        std::lock_guard<std::mutex> g(mu);
+        if (!first) first = std::current_exception();
+      }
+      launched[i] = tl_launches - l0;
+      tl_work = nullptr;
+    });
+  for (auto& t : th) t.join();
+  for (long long v : launched) tl_launches += v;
+  if (first) std::rethrow_exception(first);
+}
+
+// Initial guess -> inverse canonical (Vidal) form by a left-to-right SVD sweep
+// of the right-canonical guess (Sec. 4.2): core j = U S s.t. it is split as
+// Psi_j = U S, Y_{j+1} = 1/S, and S V^T is carried into core j+1. Values
+// <= cutoff * s_1 are dropped. The SVD is that of the fit's factorisation in
+// the handle's factorisation precision.
+template <typename T, typename F>
+void vidal_init(tt_fit* h) {
+  Dims& D = h->D;
+  const int L = D.L;
+  long long big = 1;
+  for (int j = 0; j < L; ++j) big = std::max(big, prodll({D.cb[j], D.ds[j], D.dt[j], D.cb[j + 1]}));
+  double* SV = h->pool.alloc<double>(big);  // S V^T, k x n
+  double* Cn = h->pool.alloc<double>(big);  // new core j+1
+  const int upd = h->update;
+  h->update = TT_UPDATE_2SITE_SVD;
+  try {
+    for (int j = 0; j + 1 < L; ++j) {
+      const int m = D.c[j] * D.ds[j] * D.dt[j], n = D.c[j + 1];
+      copymap<double, T>(h, m, n, h->C64[j], IdxMap::lin(n), IdxMap::lin(1), (T*)W(h).Th, IdxMap::lin(n),
+                         IdxMap::lin(1));
+      const int p = factorize<T, F>(h, m, n, 0, j + 1);
+      CK(truncate_rule<F>((const F*)W(h).fS, p, W(h).dnorm, 0.0, p, h->cutoff, W(h).dk, W(h).ddinfo, W(h).st));
+      CK(cudaMemcpyAsync(W(h).hk, W(h).dk, sizeof(int), cudaMemcpyDeviceToHost, W(h).st));
+      CK(cudaMemcpyAsync(W(h).herrw, W(h).errw, sizeof(uint32_t), cudaMemcpyDeviceToHost, W(h).st));
+      CK(cudaStreamSynchronize(W(h).st));
+      check_errw(h, "the inverse-gauge initialisation");
+      const int k = *W(h).hk;
+      if (k < 1 || k > D.cb[j + 1]) throw TTError(TT_ERR_NUMERICAL, "initial rank outside the bond capacity");
+      // Psi_j = U S (m x k), Y_{j+1} = 1/S, SV = S V^T (k x n); Ut_j = U^T is the left operand Psi_j Y_{j+1}
+      CK(gauge_update<T, F>(2, m, n, (const F*)W(h).fUM, m, (const F*)W(h).fS, (const F*)W(h).fVM, n, W(h).dk,
+                            h->C64[j], SV, h->Y[j + 1], (T*)h->Ut[j], (T*)h->Vt[j + 1], W(h).st));
+      // core j+1 <- (S V^T) core j+1
+      const int rest = D.ds[j + 1] * D.dt[j + 1] * D.c[j + 2];
+      GemmArgs<double> g;
+      g.M = k; g.N = rest; g.K = n;
+      g.A = SV; g.am = IdxMap::lin(n); g.ak = IdxMap::lin(1);
+      g.B = h->C64[j + 1]; g.bn = IdxMap::lin(1); g.bk = IdxMap::lin(rest); g.b_kfast = false;
+      g.C = Cn; g.cm = IdxMap::lin(rest); g.cn = IdxMap::lin(1);
+      gemm<double>(h, g);
+      CK(cudaMemcpyAsync(h->C64[j + 1], Cn, sizeof(double) * (size_t)k * rest, cudaMemcpyDeviceToDevice, W(h).st));
+      std::vector<F> sv(k);
+      CK(cudaMemcpyAsync(sv.data(), W(h).fS, sizeof(F) * k, cudaMemcpyDeviceToHost, W(h).st));
+      CK(cudaStreamSynchronize(W(h).st));
+      h->lam[j + 1].assign(sv.begin(), sv.end());
+      D.c[j + 1] = k;
+    }
+  } catch (...) {
+    h->update = upd;
+    throw;
+  }
+  h->update = upd;
+  CK(cudaStreamSynchronize(W(h).st));
+  h->pool.release(SV);
+  h->pool.release(Cn);
+}
+
+// Every environment and every cached half from the current C (inverse gauge):
+// right operands Y_{j} Psi_j, L_1..L_{L-1} with H1_0..H1_{L-2}, and
+// R_{L-1}..R_1 with H2_{L-1}..H2_1.
+template <typename T>
+void all_envs(tt_fit* h) {
+  Dims& D = h->D;
+  const int L = D.L;
+  for (int j = 0; j < L; ++j) {
+    const int rows = D.c[j], cols = D.ds[j] * D.dt[j] * D.c[j + 1];
+    CK(scale_rows<T>(rows, cols, h->C64[j], j > 0 ? h->Y[j] : nullptr, (T*)h->Vt[j], W(h).st));
+    if (j + 1 < L)  // left operand (Psi_j Y_{j+1})^T
+      CK(scale_cols_t<T>(D.c[j] * D.ds[j] * D.dt[j], D.c[j + 1], h->C64[j], h->Y[j + 1], (T*)h->Ut[j], W(h).st));
+  }
+  Chain<T> ch(h);
+  for (int j = 0; j + 1 < L; ++j) {
+    ch.half_left(j);
+    ch.finish_left(j);
+  }
+  for (int j = L - 1; j >= 1; --j) {
+    ch.half_right(j);
+    ch.finish_right(j);
+  }
+  CK(cudaStreamSynchronize(W(h).st));
+}
+
+// One phase of Alg. 6 (see tt_fit_sweep in include/ttfit.h); returns ||C||^2
+// of its last update in the algorithm's order, and the largest discarded
+// fraction of its windows.
+template <typename T>
+double run_phase(tt_fit* h, int ph, int sweep_index, double& maxd) {
+  const int ns = (int)h->segs.size();
+  CK(cudaEventRecord(h->w0.ev[7], h->w0.st));  // the lanes start after the handle's queued work
+  for (auto& w : h->wseg) CK(cudaStreamWaitEvent(w->st, h->w0.ev[7], 0));
+  std::vector<double> n2s(ns, 0.0), dmax(ns, 0.0), cn2(ns, 0.0);
+  std::vector<int> lastw(ns, -1);
+  // (3)/(5): local half-sweeps, odd segments (1-based) forward in phase 0
+  run_threads(h, ns, [&](int i) {
+    tl_work = h->wseg[i].get();
+    Sweeper<T> sw(h);
+    const int s0 = h->segs[i].first, e0 = h->segs[i].second;
+    const bool fwd = ((i % 2) == 0) == (ph == 0);
+    double n2 = 0, disc = 0;
+    if (fwd) {
+      for (int l = s0; l <= e0 - 1; ++l) {
+        sw.window(l, true, sweep_index, n2, disc, l == s0 ? Sweeper<T>::ENV_NONE : Sweeper<T>::ENV_SERIAL);
+        dmax[i] = std::max(dmax[i], disc);
+        lastw[i] = l;
+      }
+    } else {
+      for (int l = e0 - 1; l >= s0; --l) {
+        sw.window(l, false, sweep_index, n2, disc, l == e0 - 1 ? Sweeper<T>::ENV_NONE : Sweeper<T>::ENV_SERIAL);
+        dmax[i] = std::max(dmax[i], disc);
+        lastw[i] = l;
+      }
+    }
+    CK(cudaStreamSynchronize(W(h).st));
+    sw.resolve_gauge();
+    n2s[i] = n2;
+  });
+  // (4)/(6): connection updates at the odd|even (phase 0) or even|odd (phase 1) boundaries,
+  // done by the left segment
+  std::vector<int> conns;
+  for (int i = 0; i + 1 < ns; ++i)
+    if (((i % 2) == 0) == (ph == 0)) conns.push_back(i);
+  run_threads(h, (int)conns.size(), [&](int c) {
+    const int i = conns[c];
+    tl_work = h->wseg[i].get();
+    Sweeper<T> sw(h);
+    double disc = 0;
+    sw.window(h->segs[i].second, true, sweep_index, cn2[i], disc, Sweeper<T>::ENV_CONNECT);
+    CK(cudaStreamSynchronize(W(h).st));
+    sw.resolve_gauge();
+    dmax[i] = std::max(dmax[i], disc);
+  });
+  for (auto& w : h->wseg) {  // the handle's stream waits for every lane
+    CK(cudaEventRecord(w->ev[7], w->st));
+    CK(cudaStreamWaitEvent(h->w0.st, w->ev[7], 0));
+  }
+  maxd = *std::max_element(dmax.begin(), dmax.end());
+  int lw;
+  double n2;
+  if (!conns.empty()) {
+    lw = h->segs[conns.back()].second;
+    n2 = cn2[conns.back()];
+  } else {
+    lw = lastw[ns - 1];
+    n2 = n2s[ns - 1];
+  }
+  if (h->fact_f32) {  // ||C||^2 from the FP64-orthonormal projection of that window
+    double nr = 0;
+    CK(cudaMemcpyAsync(&nr, h->dn2 + lw, sizeof(double), cudaMemcpyDeviceToHost, h->w0.st));
+    CK(cudaStreamSynchronize(h->w0.st));
+    n2 = nr * nr;
+  }
+  return n2;
 }
 
 void setup(tt_fit* h, const std::vector<double*>& C0) {
@@ -971,7 +1237,7 @@ void setup(tt_fit* h, const std::vector<double*>& C0) {
     const long long cap = prodll({D.cb[j], D.ds[j], D.dt[j], D.cb[j + 1]});
     h->C64[j] = h->pool.alloc<double>(cap);
     const long long n = prodll({D.c[j], D.ds[j], D.dt[j], D.c[j + 1]});
-    CK(cudaMemcpyAsync(h->C64[j], C0[j], sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+    CK(cudaMemcpyAsync(h->C64[j], C0[j], sizeof(double) * n, cudaMemcpyDeviceToDevice, W(h).st));
   }
   std::vector<double> ones(1024, 1.0);
   for (int j = 0; j <= L; ++j) {
@@ -979,10 +1245,30 @@ void setup(tt_fit* h, const std::vector<double*>& C0) {
     int n = D.c[j];
     for (int off = 0; off < n; off += 1024)
       CK(cudaMemcpyAsync(h->Y[j] + off, ones.data(), sizeof(double) * std::min(1024, n - off), cudaMemcpyHostToDevice,
-                         h->st));
+                         W(h).st));
   }
   if (h->use_f32) rebuild_chain<float>(h);
   else rebuild_chain<double>(h);
+}
+
+// Runs fn(i) for i < n on n host threads with device `dev` current; returns
+// the first non-OK status (by index).
+template <typename Fn>
+tt_status run_handles(int n, int dev, Fn fn) {
+  std::vector<tt_status> st(n, TT_OK);
+  std::vector<std::thread> th;
+  for (int i = 0; i < n; ++i)
+    th.emplace_back([&, i] {
+      if (cudaSetDevice(dev) != cudaSuccess) {
+        st[i] = TT_ERR_CUDA;
+        return;
+      }
+      st[i] = fn(i);
+    });
+  for (auto& t : th) t.join();
+  for (tt_status x : st)
+    if (x != TT_OK) return x;
+  return TT_OK;
 }
 
 thread_local std::string g_create_error;
@@ -1018,6 +1304,16 @@ const char* tt_fit_last_error(const tt_fit* h) {
   return g_create_error.empty() ? "NULL handle" : g_create_error.c_str();
 }
 
+// Adds the kernel launches issued on this thread while it lives to h->launches.
+struct LaunchTally {
+  tt_fit* h;
+  long long l0;
+  explicit LaunchTally(tt_fit* hh) : h(hh), l0(tl_launches) {}
+  ~LaunchTally() {
+    if (h) h->launches += tl_launches - l0;
+  }
+};
+
 tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max, double tol, int gauge,
                         const tt_fit_options* opt, tt_fit** out) {
   if (!out) return TT_ERR_INVALID_ARGUMENT;
@@ -1043,15 +1339,19 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
     if (o.precision < 0 || o.precision > 4 || o.oversample < 0) return TT_ERR_INVALID_ARGUMENT;
     if (o.init < 0 || o.init > 2 || (o.init == TT_INIT_GIVEN && !o.init_C)) return TT_ERR_INVALID_ARGUMENT;
     if (o.precision == TT_PREC_BF16_SPLIT) return TT_ERR_INVALID_ARGUMENT;  // not in this build
+    if (o.n_segments > 1 && gauge != TT_GAUGE_INVERSE_CANONICAL) return TT_ERR_INVALID_ARGUMENT;
+    if (o.edge_extra < 0) return TT_ERR_INVALID_ARGUMENT;
     int LA, LB;
     std::vector<int> doA, diA, bA, doB, diB, bB;
     read_desc(A, LA, doA, diA, bA);
     read_desc(B, LB, doB, diB, bB);
     if (LA != LB) return TT_ERR_SHAPE_MISMATCH;
     if (LA < 2) return TT_ERR_INVALID_ARGUMENT;
+    if (o.n_segments > 1 && LA < 2 * o.n_segments) return TT_ERR_INVALID_ARGUMENT;  // >= 2 sites per segment
     for (int l = 0; l < LA; ++l)
       if (diA[l] != doB[l]) return TT_ERR_SHAPE_MISMATCH;
     h = new tt_fit();
+    LaunchTally tally(h);
     h->fault = o.fault_inject;
     h->pool.fault = o.fault_inject & TT_FAULT_ALLOC_FAIL;
     h->fault_nan_pending = (o.fault_inject & TT_FAULT_NAN_INPUT) != 0;
@@ -1069,21 +1369,20 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
     h->fact_f32 = h->use_f32 || o.fast_factor;
     h->cutoff = o.sv_cutoff >= 0 ? o.sv_cutoff : (o.precision == TT_PREC_FP64 ? 1e-13 : 1e-6);
     h->conv_tol = o.conv_tol >= 0 ? o.conv_tol : tol;
-    h->st = (cudaStream_t)o.stream;
     int dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev));
-    CK(cudaMalloc(&h->dnorm, sizeof(double)));
-    h->pool.ptrs.push_back(h->dnorm);
-    h->dk = h->pool.alloc<int>(4);
-    h->ddinfo = h->pool.alloc<double>(4);
-    h->errw = h->pool.alloc<uint32_t>(4);  // [0] error bits, [1] max Jacobi sweeps (diagnostic)
-    CK(cudaMemsetAsync(h->errw, 0, 4 * sizeof(uint32_t), h->st));
-    for (auto& e : h->ev) CK(cudaEventCreate(&e));
-    CK(cudaMallocHost(&h->hk, sizeof(int) * 4));
-    CK(cudaMallocHost(&h->hdinfo, sizeof(double) * 4));
-    CK(cudaMallocHost(&h->herrw, sizeof(uint32_t) * 4));
-    *h->herrw = 0;
+    h->device = dev;
+    init_lane(h, h->w0, (cudaStream_t)o.stream, false);
+    if (o.n_segments > 1) {  // Alg. 6: one lane (stream, scratch, host thread) per segment
+      h->segs = partition_sites(LA, o.n_segments, o.edge_extra);
+      for (int i = 0; i < o.n_segments; ++i) {
+        h->wseg.emplace_back(new Work());
+        cudaStream_t sti = nullptr;
+        CK(cudaStreamCreateWithFlags(&sti, cudaStreamNonBlocking));
+        init_lane(h, *h->wseg.back(), sti, true);
+      }
+    }
     Dims& D = h->D;
     D.L = LA;
     D.ds = doA;
@@ -1093,7 +1392,7 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
     D.b = bB;
     upload(h, A, doA, diA, bA, h->A64);
     upload(h, B, doB, diB, bB, h->B64);
-    CK(cudaStreamSynchronize(h->st));
+    CK(cudaStreamSynchronize(W(h).st));
     long long mc = 1;  // largest core of A, B (and a given guess): scratch of the preparation sweeps
     for (int l = 0; l < LA; ++l) {
       mc = std::max(mc, prodll({bA[l], doA[l], diA[l], bA[l + 1]}));
@@ -1133,7 +1432,7 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
       cudaStream_t pool[NS];
       for (auto& x : pool) CK(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
       std::vector<void*> dead;
-      CK(cudaStreamSynchronize(h->st));
+      CK(cudaStreamSynchronize(W(h).st));
       for (int j = 0; j < L; ++j) {
         cudaStream_t sj = pool[j % NS];
         const long long n = prodll({cbond[j], D.ds[j], D.dt[j], cbond[j + 1]});
@@ -1144,7 +1443,6 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
           double* R = h->pool.alloc<double>((size_t)p * p);
           double* Q = h->pool.alloc<double>((size_t)q * p);
           CK(qr_householder<double, double>(q, p, C0[j], Q, R, sj));
-          h->launches += 2;
           dead.push_back(C0[j]);
           dead.push_back(R);
           C0[j] = Q;
@@ -1173,11 +1471,11 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
         for (int l = 0; l < L; ++l) {
           const long long n = prodll({bz[l], D.du[l], D.dt[l], bz[l + 1]});
           G[l] = h->pool.alloc<double>(n);
-          CK(cudaMemcpyAsync(G[l], h->B64[l], sizeof(double) * n, cudaMemcpyDeviceToDevice, h->st));
+          CK(cudaMemcpyAsync(G[l], h->B64[l], sizeof(double) * n, cudaMemcpyDeviceToDevice, W(h).st));
         }
         if (D.du != D.ds) throw TTError(TT_ERR_SHAPE_MISMATCH, "TT_INIT_COPY_B needs A.d_out == B.d_out");
       }
-      CK(cudaStreamSynchronize(h->st));
+      CK(cudaStreamSynchronize(W(h).st));
       Prep PC = make_prep(h, mc);
       qr_sweep(h, PC, G, bz, D.ds, D.dt);
       rq_sweep(h, PC, G, bz, D.ds, D.dt, 1, false);
@@ -1188,26 +1486,36 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
     }
     D.c = cbond;
     setup(h, C0);
+    if (h->segs.size() > 1) {  // inverse canonical form and every environment (Sec. 4.2)
+      if (h->use_f32) {
+        vidal_init<float, float>(h);
+        all_envs<float>(h);
+      } else if (h->fact_f32) {
+        vidal_init<double, float>(h);
+        all_envs<double>(h);
+      } else {
+        vidal_init<double, double>(h);
+        all_envs<double>(h);
+      }
+    }
     for (int j = 0; j < L; ++j) h->pool.release(C0[j]);
-    CK(cudaStreamSynchronize(h->st));
+    CK(cudaStreamSynchronize(W(h).st));
     *out = h;
     return TT_OK;
   } catch (const TTError& e) {
     g_create_error = std::string("tt_fit_create: ") + e.what();
     if (h) {
       cudaGetLastError();
-      if (h->hk) cudaFreeHost(h->hk);
-      if (h->hdinfo) cudaFreeHost(h->hdinfo);
-      if (h->herrw) cudaFreeHost(h->herrw);
-      for (auto e : h->ev)
-        if (e) cudaEventDestroy(e);
+      free_lanes(h);
       delete h;
     }
     return e.code;
   } catch (const std::bad_alloc&) {
+    if (h) free_lanes(h);
     delete h;
     return TT_ERR_OUT_OF_MEMORY;
   } catch (...) {
+    if (h) free_lanes(h);
     delete h;
     return TT_ERR_CUDA;
   }
@@ -1217,19 +1525,38 @@ tt_status tt_fit_sweep(tt_fit* h, int n_sweeps, tt_sweep_report* rep) {
   if (!h || n_sweeps < 0) return TT_ERR_INVALID_ARGUMENT;
   if (h->poisoned) return TT_ERR_STATE;
   auto t0 = std::chrono::steady_clock::now();
+  LaunchTally tally(h);
   try {
-    for (double& s : h->stage_ms) s = 0;
-    h->flops = 0;
-    const long long launch0 = h->launches;
-    if (h->use_f32) {
+    for (Work* w : lanes(h)) {
+      for (double& s : w->stage_ms) s = 0;
+      w->flops = 0;
+    }
+    const long long launch0 = tl_launches;
+    if (h->segs.size() > 1) {
+      for (int s = 0; s < n_sweeps && !h->converged; ++s) {
+        const int ph = h->phases_done % 2;
+        double maxd = 0;
+        const double n2 = h->use_f32 ? run_phase<float>(h, ph, h->phases_done, maxd)
+                                     : run_phase<double>(h, ph, h->phases_done, maxd);
+        h->phases_done++;
+        h->sweeps_done++;
+        h->cur_n2 = n2;
+        h->max_disc = maxd;
+        if (ph == 1) {  // a full set of local sweeps is complete
+          h->delta = (h->last_n2 >= 0 && n2 > 0) ? std::fabs(n2 - h->last_n2) / n2 : INFINITY;
+          h->last_n2 = n2;
+          if (h->delta <= h->conv_tol) h->converged = true;
+        }
+      }
+    } else if (h->use_f32) {
       Sweeper<float> sw(h);
       sw.run(n_sweeps);
     } else {
       Sweeper<double> sw(h);
       sw.run(n_sweeps);
     }
-    CK(cudaStreamSynchronize(h->st));
-    h->sweep_launches = h->launches - launch0;
+    CK(cudaStreamSynchronize(W(h).st));
+    h->sweep_launches = tl_launches - launch0;
     h->have_times = true;
   } catch (const TTError& e) {
     poison(h, e);
@@ -1243,7 +1570,7 @@ tt_status tt_fit_sweep(tt_fit* h, int n_sweeps, tt_sweep_report* rep) {
     rep->sweeps_done = h->sweeps_done;
     rep->converged = h->converged ? 1 : 0;
     rep->delta = h->delta;
-    rep->norm2_C = h->last_n2;
+    rep->norm2_C = h->segs.size() > 1 ? h->cur_n2 : h->last_n2;
     rep->max_discarded = h->max_disc;
     rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
@@ -1253,6 +1580,7 @@ tt_status tt_fit_sweep(tt_fit* h, int n_sweeps, tt_sweep_report* rep) {
 tt_status tt_fit_result(const tt_fit* hc, tt_mpo_desc* C, double* lambdas) {
   tt_fit* h = const_cast<tt_fit*>(hc);
   if (!h || !C) return TT_ERR_INVALID_ARGUMENT;
+  LaunchTally tally(h);
   if (h->poisoned) return TT_ERR_STATE;
   const Dims& D = h->D;
   const int L = D.L;
@@ -1283,19 +1611,17 @@ tt_status tt_fit_result(const tt_fit* hc, tt_mpo_desc* C, double* lambdas) {
       // C_l = Psi_l Y_l for l < L (inverse gauge); Y = 1 in the site gauge
       const bool scale = (h->gauge == TT_GAUGE_INVERSE_CANONICAL) && (l < L - 1);
       if (C->dtype == TT_DTYPE_F64) {
-        CK(scale_cols(rows, cols, h->C64[l], scale ? h->Y[l + 1] : nullptr, (double*)C->cores[l], h->st));
-        h->launches += 1;
+        CK(scale_cols(rows, cols, h->C64[l], scale ? h->Y[l + 1] : nullptr, (double*)C->cores[l], W(h).st));
       } else {
         double* tmp = h->pool.alloc<double>((size_t)rows * cols);
-        CK(scale_cols(rows, cols, h->C64[l], scale ? h->Y[l + 1] : nullptr, tmp, h->st));
+        CK(scale_cols(rows, cols, h->C64[l], scale ? h->Y[l + 1] : nullptr, tmp, W(h).st));
         CK(copy_map<double, float>(1, rows * cols, tmp, IdxMap::lin(0), IdxMap::lin(1), (float*)C->cores[l],
-                                   IdxMap::lin(0), IdxMap::lin(1), 1.0, h->st));
-        CK(cudaStreamSynchronize(h->st));
+                                   IdxMap::lin(0), IdxMap::lin(1), 1.0, W(h).st));
+        CK(cudaStreamSynchronize(W(h).st));
         h->pool.release(tmp);
-        h->launches += 2;
       }
     }
-    CK(cudaStreamSynchronize(h->st));
+    CK(cudaStreamSynchronize(W(h).st));
   } catch (const TTError& e) {
     poison(h, e);
     return e.code;
@@ -1306,10 +1632,13 @@ tt_status tt_fit_result(const tt_fit* hc, tt_mpo_desc* C, double* lambdas) {
 tt_status tt_fit_set_precision(tt_fit* h, int precision, int fast_factor) {
   if (!h || precision < 0 || precision > 4 || precision == TT_PREC_BF16_SPLIT) return TT_ERR_INVALID_ARGUMENT;
   if (h->poisoned) return TT_ERR_STATE;
-  if (!h->forward) {
-    h->last_error = "tt_fit_set_precision: the next sweep must be a forward sweep (C right-canonical)";
+  if (h->segs.size() > 1 ? (h->phases_done % 2 != 0) : !h->forward) {
+    h->last_error = h->segs.size() > 1
+                        ? "tt_fit_set_precision: a segment-parallel fit switches between full sets of local sweeps"
+                        : "tt_fit_set_precision: the next sweep must be a forward sweep (C right-canonical)";
     return TT_ERR_STATE;
   }
+  LaunchTally tally(h);
   try {
     const bool f32 = precision != TT_PREC_FP64;
     h->precision = precision;
@@ -1318,6 +1647,10 @@ tt_status tt_fit_set_precision(tt_fit* h, int precision, int fast_factor) {
     h->converged = false;
     if (f32) rebuild_chain<float>(h);
     else rebuild_chain<double>(h);
+    if (h->segs.size() > 1) {  // the parallel fit needs every environment and half
+      if (f32) all_envs<float>(h);
+      else all_envs<double>(h);
+    }
   } catch (const TTError& e) {
     poison(h, e);
     return e.code;
@@ -1328,10 +1661,88 @@ tt_status tt_fit_set_precision(tt_fit* h, int precision, int fast_factor) {
 tt_status tt_fit_stage_times(const tt_fit* h, double out[7]) {
   if (!h || !out) return TT_ERR_INVALID_ARGUMENT;
   if (!h->have_times) return TT_ERR_STATE;
-  for (int i = 0; i < 5; ++i) out[i] = h->stage_ms[i];
-  out[5] = h->flops;
+  for (int i = 0; i < 6; ++i) out[i] = 0;
+  for (Work* w : lanes(const_cast<tt_fit*>(h))) {  // summed over the lanes (concurrent in a parallel fit)
+    for (int i = 0; i < 5; ++i) out[i] += w->stage_ms[i];
+    out[5] += w->flops;
+  }
   out[6] = (double)h->sweep_launches;
   return TT_OK;
+}
+
+tt_status tt_partition(int L, int n_segments, int edge_extra, int* first, int* last) {
+  if (L < 2 || n_segments < 1 || L < 2 * n_segments || edge_extra < 0 || !first || !last)
+    return TT_ERR_INVALID_ARGUMENT;
+  const auto segs = partition_sites(L, n_segments, edge_extra);
+  for (int i = 0; i < n_segments; ++i) {
+    first[i] = segs[i].first;
+    last[i] = segs[i].second;
+  }
+  return TT_OK;
+}
+
+tt_status tt_fit_create_batched(int n, const tt_mpo_desc* A, const tt_mpo_desc* B, const int* chi_max, double tol,
+                                int gauge, int n_segments, const tt_fit_options* opt, tt_fit** out) {
+  if (n < 1 || !A || !B || !chi_max || !out) return TT_ERR_INVALID_ARGUMENT;
+  for (int i = 0; i < n; ++i) out[i] = nullptr;
+  tt_fit_options o{};
+  o.struct_size = sizeof(o);
+  o.update = TT_UPDATE_2SITE_SVD;
+  o.oversample = 10;
+  o.precision = TT_PREC_FP64;
+  o.init = TT_INIT_RANDOM;
+  o.sv_cutoff = -1;
+  o.conv_tol = -1;
+  o.prepare_inputs = 1;
+  if (opt) {
+    if (opt->struct_size != sizeof(tt_fit_options)) return TT_ERR_INVALID_ARGUMENT;
+    o = *opt;
+  }
+  if (o.init == TT_INIT_GIVEN) return TT_ERR_INVALID_ARGUMENT;  // one guess cannot serve n pairs
+  o.n_segments = n_segments;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TT_ERR_CUDA;
+  // every handle gets a stream of its own, ordered after the caller's stream (where A, B were written)
+  cudaStream_t caller = (cudaStream_t)o.stream;
+  cudaEvent_t ready = nullptr;
+  if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess) return TT_ERR_CUDA;
+  if (cudaEventRecord(ready, caller) != cudaSuccess) {
+    cudaEventDestroy(ready);
+    return TT_ERR_CUDA;
+  }
+  std::vector<cudaStream_t> sts(n, nullptr);
+  tt_status r = TT_OK;
+  for (int i = 0; i < n && r == TT_OK; ++i)
+    if (cudaStreamCreateWithFlags(&sts[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamWaitEvent(sts[i], ready, 0) != cudaSuccess)
+      r = TT_ERR_CUDA;
+  if (r == TT_OK)
+    r = run_handles(n, dev, [&](int i) {
+      tt_fit_options oi = o;
+      oi.stream = sts[i];
+      tt_status si = tt_fit_create(&A[i], &B[i], chi_max[i], tol, gauge, &oi, &out[i]);
+      if (si == TT_OK) {
+        out[i]->w0.own_stream = true;  // destroyed with the handle
+        sts[i] = nullptr;
+      }
+      return si;
+    });
+  cudaEventDestroy(ready);
+  for (cudaStream_t x : sts)
+    if (x) cudaStreamDestroy(x);
+  if (r != TT_OK)
+    for (int i = 0; i < n; ++i) {
+      tt_fit_destroy(out[i]);
+      out[i] = nullptr;
+    }
+  return r;
+}
+
+tt_status tt_fit_sweep_batched(int n, tt_fit* const* h, int n_sweeps, tt_sweep_report* rep) {
+  if (n < 1 || !h || n_sweeps < 0) return TT_ERR_INVALID_ARGUMENT;
+  for (int i = 0; i < n; ++i)
+    if (!h[i]) return TT_ERR_INVALID_ARGUMENT;
+  return run_handles(n, h[0]->device, [&](int i) { return tt_fit_sweep(h[i], n_sweeps, rep ? &rep[i] : nullptr); });
 }
 
 tt_status tt_fit_launch_count(const tt_fit* h, long long* n) {
@@ -1342,13 +1753,9 @@ tt_status tt_fit_launch_count(const tt_fit* h, long long* n) {
 
 void tt_fit_destroy(tt_fit* h) {
   if (!h) return;
-  if (h->st) cudaStreamSynchronize(h->st);
+  if (h->w0.st) cudaStreamSynchronize(h->w0.st);
   else cudaDeviceSynchronize();
-  for (auto e : h->ev)
-    if (e) cudaEventDestroy(e);
-  if (h->hk) cudaFreeHost(h->hk);
-  if (h->hdinfo) cudaFreeHost(h->hdinfo);
-  if (h->herrw) cudaFreeHost(h->herrw);
+  free_lanes(h);
   delete h;
 }
 

@@ -113,6 +113,7 @@ cudaError_t splitk_reduce(const GemmArgs<T>& g, const T* ws, int splits, int sm_
   int blocks = (int)((total + 255) / 256);
   if (blocks > 4 * sm_count) blocks = 4 * sm_count;
   if (blocks < 1) blocks = 1;
+  ++tl_launches;
   splitk_reduce_kernel<T><<<blocks, 256, 0, st>>>(g, ws, splits);
   return cudaGetLastError();
 }
@@ -125,6 +126,7 @@ cudaError_t gemm_simt(const GemmArgs<T>& g, T* ws, size_t ws_elems, int sm_count
   if (g.K <= 0) {  // empty contraction: C = beta * C
     GemmArgs<T> z = g;
     z.alpha = T(0);
+    ++tl_launches;
     splitk_reduce_kernel<T><<<256, 256, 0, st>>>(z, nullptr, 0);
     return cudaGetLastError();
   }
@@ -141,12 +143,15 @@ cudaError_t gemm_simt(const GemmArgs<T>& g, T* ws, size_t ws_elems, int sm_count
   splits = (g.K + kps - 1) / kps;
   dim3 grid(gn, gm, splits);
   if (splits == 1) {
+    ++tl_launches;
     gemm_simt_kernel<T><<<grid, NT, 0, st>>>(g, nullptr, kps);
   } else {
+    ++tl_launches;
     gemm_simt_kernel<T><<<grid, NT, 0, st>>>(g, ws, kps);
     long long total = (long long)g.M * g.N;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 4 * sm_count) blocks = 4 * sm_count;
+    ++tl_launches;
     splitk_reduce_kernel<T><<<blocks, 256, 0, st>>>(g, ws, splits);
   }
   return cudaGetLastError();

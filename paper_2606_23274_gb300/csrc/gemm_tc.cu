@@ -383,6 +383,7 @@ cudaError_t gemm_tf32(const GemmArgs<float>& g, float* ws, size_t ws_elems, int 
   splits = (g.K + kps - 1) / kps;
   dim3 grid(gn, gm, splits);
   float* wsp = splits > 1 ? ws : nullptr;
+  ++tl_launches;
   if (split)
     gemm_tf32_kernel<false, true><<<grid, 128, Cfg<true>::SMEM_BYTES, st>>>(
         ta, tb, g.M, g.N, g.K, kps, g.C, g.cm, g.cn, g.alpha, g.beta, g.C2, g.cm2, g.cn2, wsp, errw);

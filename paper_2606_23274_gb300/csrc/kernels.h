@@ -96,5 +96,8 @@ cudaError_t scale_rows(int rows, int cols, const double* in, const double* y, T*
 
 // out (rows x cols, row-major) = in * diag(y) (y == nullptr: plain copy)
 cudaError_t scale_cols(int rows, int cols, const double* in, const double* y, double* out, cudaStream_t st);
+// out (cols x rows) = (in diag(y))^T in type T
+template <typename T>
+cudaError_t scale_cols_t(int rows, int cols, const double* in, const double* y, T* out, cudaStream_t st);
 
 }  // namespace ttfit

@@ -130,7 +130,8 @@ __global__ void __launch_bounds__(1024) qr_house_kernel(int q, int p, S* __restr
 template <typename C, typename S>
 cudaError_t qr_householder(int q, int p, S* X, S* Q, S* R, cudaStream_t st) {
   if (q <= 0 || p <= 0) return cudaSuccess;
-  if (min(q, p) > 1024) return cudaErrorInvalidValue;
+  if (min(q, p) > 1024 || q > 1024) return cudaErrorInvalidValue;
+  ++tl_launches;
   if (q <= 128) qr_house_kernel<C, S, 4><<<1, 1024, 0, st>>>(q, p, X, Q, R);
   else if (q <= 256) qr_house_kernel<C, S, 8><<<1, 1024, 0, st>>>(q, p, X, Q, R);
   else if (q <= 512) qr_house_kernel<C, S, 16><<<1, 1024, 0, st>>>(q, p, X, Q, R);
@@ -317,6 +318,7 @@ cudaError_t jacobi_svd(int q, int p, S* W, S* U, S* Sv, S* V, S* Vwork, int max_
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
       if (e != cudaSuccess) return e;
     }
+    ++tl_launches;
     kern<<<1, 1024, in_smem ? need : 0, st>>>(q, p, W, Vwork, max_sweeps, tol, errw, U, Sv, V, in_smem);
     return cudaGetLastError();
   };
@@ -353,6 +355,7 @@ __global__ void __launch_bounds__(1024) frob_kernel(const T* __restrict__ x, lon
 
 template <typename T>
 cudaError_t frob_norm(const T* x, long long n, double* out, uint32_t* errw, cudaStream_t st) {
+  ++tl_launches;
   frob_kernel<T><<<1, 1024, 0, st>>>(x, n, out, errw);
   return cudaGetLastError();
 }
@@ -397,6 +400,7 @@ __global__ void truncate_kernel(const F* S, int p, const double* normM, double t
 template <typename F>
 cudaError_t truncate_rule(const F* S, int p, const double* normM, double tau_over_L, int chi_max, double cutoff,
                           int* info, double* dinfo, cudaStream_t st) {
+  ++tl_launches;
   truncate_kernel<F><<<1, 32, 0, st>>>(S, p, normM, tau_over_L, chi_max, cutoff, info, dinfo);
   return cudaGetLastError();
 }
@@ -436,6 +440,7 @@ cudaError_t gauge_update(int mode, int m, int n, const F* U, int ld_u, const F* 
   int blocks = (int)((tot + 255) / 256);
   if (blocks > 1024) blocks = 1024;
   if (blocks < 1) blocks = 1;
+  ++tl_launches;
   gauge_update_kernel<T, F><<<blocks, 256, 0, st>>>(mode, m, n, U, ld_u, S, V, ld_v, kdev, Cl, Cr, Y, Ut, Vt);
   return cudaGetLastError();
 }
@@ -443,6 +448,8 @@ template cudaError_t gauge_update<double, double>(int, int, int, const double*, 
                                                   const int*, double*, double*, double*, double*, double*, cudaStream_t);
 template cudaError_t gauge_update<float, float>(int, int, int, const float*, int, const float*, const float*, int,
                                                 const int*, double*, double*, double*, float*, float*, cudaStream_t);
+template cudaError_t gauge_update<double, float>(int, int, int, const float*, int, const float*, const float*, int,
+                                                 const int*, double*, double*, double*, double*, double*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 template <typename Tin, typename Tout>
@@ -462,6 +469,7 @@ cudaError_t copy_map(int rows, int cols, const Tin* in, IdxMap im, IdxMap in_, T
   if (tot <= 0) return cudaSuccess;
   int blocks = (int)((tot + 255) / 256);
   if (blocks > 4096) blocks = 4096;
+  ++tl_launches;
   copy_map_kernel<Tin, Tout><<<blocks, 256, 0, st>>>(rows, cols, in, im, in_, out, om, on, scale);
   return cudaGetLastError();
 }
@@ -486,6 +494,7 @@ cudaError_t philox_fill(F* out, long long count, uint64_t seed, uint64_t stream,
   if (count <= 0) return cudaSuccess;
   int blocks = (int)((count + 255) / 256);
   if (blocks > 2048) blocks = 2048;
+  ++tl_launches;
   philox_fill_kernel<F><<<blocks, 256, 0, st>>>(out, count, seed, stream, scale);
   return cudaGetLastError();
 }
@@ -544,6 +553,7 @@ __global__ void fix_signs_kernel(int m, int n, F* __restrict__ U, int ld_u, F* _
 template <typename F>
 cudaError_t fix_signs(int m, int n, int p, F* U, int ld_u, F* V, int ld_v, cudaStream_t st) {
   if (p <= 0 || m <= 0) return cudaSuccess;
+  ++tl_launches;
   fix_signs_kernel<F><<<p, 256, 0, st>>>(m, n, U, ld_u, V, ld_v);
   return cudaGetLastError();
 }
@@ -578,6 +588,7 @@ cudaError_t inverse_gauge_update(int m, int n, int k, const double* U, const dou
                                  double* Cr, double* Y, cudaStream_t st) {
   long long tot = (long long)(m > n ? m : n) * k;
   int blocks = (int)std::min<long long>((tot + 255) / 256, 1024);
+  ++tl_launches;
   inverse_gauge_kernel<T><<<std::max(blocks, 1), 256, 0, st>>>(m, n, k, U, V, P, Cl, Cr, Y);
   return cudaGetLastError();
 }
@@ -607,6 +618,7 @@ cudaError_t scale_rows(int rows, int cols, const double* in, const double* y, T*
   long long tot = (long long)rows * cols;
   if (tot <= 0) return cudaSuccess;
   int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
+  ++tl_launches;
   scale_rows_kernel<T><<<blocks, 256, 0, st>>>(rows, cols, in, y, out);
   return cudaGetLastError();
 }
@@ -617,8 +629,35 @@ cudaError_t scale_cols(int rows, int cols, const double* in, const double* y, do
   long long tot = (long long)rows * cols;
   if (tot <= 0) return cudaSuccess;
   int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
+  ++tl_launches;
   scale_cols_kernel<<<blocks, 256, 0, st>>>(rows, cols, in, y, out);
   return cudaGetLastError();
 }
 
+}  // namespace ttfit
+
+// out (cols x rows, row-major) = (in diag(y))^T, in rows x cols row-major FP64
+namespace ttfit {
+template <typename T>
+__global__ void scale_cols_t_kernel(int rows, int cols, const double* __restrict__ in, const double* __restrict__ y,
+                                    T* __restrict__ out) {
+  const long long tot = (long long)rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(e / rows), r = (int)(e % rows);  // e indexes out; the read is strided
+    out[e] = (T)(in[(size_t)r * cols + c] * y[c]);
+  }
+}
+
+template <typename T>
+cudaError_t scale_cols_t(int rows, int cols, const double* in, const double* y, T* out, cudaStream_t st) {
+  long long tot = (long long)rows * cols;
+  if (tot <= 0) return cudaSuccess;
+  int blocks = (int)std::min<long long>((tot + 255) / 256, 4096);
+  ++tl_launches;
+  scale_cols_t_kernel<T><<<blocks, 256, 0, st>>>(rows, cols, in, y, out);
+  return cudaGetLastError();
+}
+template cudaError_t scale_cols_t<float>(int, int, const double*, const double*, float*, cudaStream_t);
+template cudaError_t scale_cols_t<double>(int, int, const double*, const double*, double*, cudaStream_t);
 }  // namespace ttfit

@@ -70,6 +70,7 @@ cudaError_t svd_run(const double* M, int m, int n, int chi_max, double tau_rel, 
   if ((e = truncate_rule<double>(Sv, r, nrm, tau_rel, chi_max, 1e-13, k_dev, dinfo, st)) != cudaSuccess) return e;
   const long long tot = (long long)q * r;
   const int blocks = (int)std::max<long long>(1, std::min<long long>((tot + 255) / 256, 1024));
+  ++tl_launches;
   svd_outputs_kernel<<<blocks, 256, 0, st>>>(m, n, tr ? 1 : 0, Ux, Vx, Sv, U, S, Vt);
   return cudaGetLastError();
 }

@@ -37,7 +37,7 @@ class tt_fit_options(ct.Structure):
                 ("seed", ct.c_uint64), ("precision", ct.c_int), ("init", ct.c_int),
                 ("init_C", ct.POINTER(tt_mpo_desc)), ("sv_cutoff", ct.c_double), ("conv_tol", ct.c_double),
                 ("stream", ct.c_void_p), ("prepare_inputs", ct.c_int), ("fault_inject", ct.c_uint32),
-                ("fast_factor", ct.c_int)]
+                ("fast_factor", ct.c_int), ("n_segments", ct.c_int), ("edge_extra", ct.c_int)]
 
 
 class tt_sweep_report(ct.Structure):
@@ -83,6 +83,13 @@ def load():
         lib.tt_fit_stage_times.restype = ct.c_int
         lib.tt_fit_launch_count.argtypes = [ct.c_void_p, ct.POINTER(ct.c_longlong)]
         lib.tt_fit_launch_count.restype = ct.c_int
+        lib.tt_fit_create_batched.argtypes = [ct.c_int, ct.POINTER(tt_mpo_desc), ct.POINTER(tt_mpo_desc),
+                                              ct.POINTER(ct.c_int), ct.c_double, ct.c_int, ct.c_int,
+                                              ct.POINTER(tt_fit_options), ct.POINTER(ct.c_void_p)]
+        lib.tt_fit_create_batched.restype = ct.c_int
+        lib.tt_fit_sweep_batched.argtypes = [ct.c_int, ct.POINTER(ct.c_void_p), ct.c_int,
+                                             ct.POINTER(tt_sweep_report)]
+        lib.tt_fit_sweep_batched.restype = ct.c_int
         _lib = lib
     return _lib
 
@@ -131,16 +138,11 @@ def _check(code, h=None, what=""):
         raise TTError(code, f"{what}: {msg}")
 
 
-def tt_fit_create(A: Sequence, B: Sequence, chi_max: int, tol: float, gauge="site", *, update="svd",
-                  oversample=10, seed=0, precision="fp64", init="random", init_C=None, sv_cutoff=-1.0,
-                  conv_tol=-1.0, stream=None, prepare_inputs=True, fault_inject=0, fast_factor=False,
-                  device="cuda"):
-    """Create a fit handle (see tt_fit_create in include/ttfit.h). A, B: lists of
-    (chi_l, d, d', chi_r) tensors (torch CUDA tensors, or host arrays that are copied)."""
+def _options(update="svd", oversample=10, seed=0, precision="fp64", init="random", init_C=None, sv_cutoff=-1.0,
+             conv_tol=-1.0, stream=None, prepare_inputs=True, fault_inject=0, fast_factor=False, n_segments=1,
+             edge_extra=0, device="cuda"):
+    """tt_fit_options from keyword arguments; returns (options, keep-alive objects)."""
     import torch
-    lib = load()
-    dA = _Desc(_as_device(A, device))
-    dB = _Desc(_as_device(B, device))
     o = tt_fit_options()
     o.struct_size = ct.sizeof(tt_fit_options)
     o.update = UPDATE[update] if isinstance(update, str) else int(update)
@@ -160,12 +162,54 @@ def tt_fit_create(A: Sequence, B: Sequence, chi_max: int, tol: float, gauge="sit
     o.prepare_inputs = 1 if prepare_inputs else 0
     o.fault_inject = int(fault_inject)
     o.fast_factor = 1 if fast_factor else 0
+    o.n_segments = int(n_segments)
+    o.edge_extra = int(edge_extra)
+    return o, dC
+
+
+def tt_fit_create(A: Sequence, B: Sequence, chi_max: int, tol: float, gauge="site", *, device="cuda", **kw):
+    """Create a fit handle (see tt_fit_create in include/ttfit.h). A, B: lists of
+    (chi_l, d, d', chi_r) tensors (torch CUDA tensors, or host arrays that are copied).
+    Keywords: update, oversample, seed, precision, init, init_C, sv_cutoff, conv_tol,
+    stream, prepare_inputs, fault_inject, fast_factor, n_segments, edge_extra."""
+    lib = load()
+    dA = _Desc(_as_device(A, device))
+    dB = _Desc(_as_device(B, device))
+    o, _keep = _options(device=device, **kw)
     h = ct.c_void_p()
     g = GAUGE[gauge] if isinstance(gauge, str) else int(gauge)
     code = lib.tt_fit_create(ct.byref(dA.desc), ct.byref(dB.desc), int(chi_max), float(tol), g, ct.byref(o),
                              ct.byref(h))
     _check(code, None, "tt_fit_create")
     return Fit(h, device, len(A))
+
+
+def tt_fit_create_batched(pairs: Sequence, chi_max: Sequence[int], tol: float, gauge="inverse", *, n_segments=1,
+                          device="cuda", **kw):
+    """tt_fit_create_batched: one handle per (A, B) pair, each with its own stream."""
+    lib = load()
+    n = len(pairs)
+    dAs = [_Desc(_as_device(A, device)) for A, _ in pairs]
+    dBs = [_Desc(_as_device(B, device)) for _, B in pairs]
+    arrA = (tt_mpo_desc * n)(*[d.desc for d in dAs])
+    arrB = (tt_mpo_desc * n)(*[d.desc for d in dBs])
+    chis = (ct.c_int * n)(*[int(c) for c in chi_max])
+    o, _keep = _options(device=device, **kw)
+    outs = (ct.c_void_p * n)()
+    g = GAUGE[gauge] if isinstance(gauge, str) else int(gauge)
+    code = lib.tt_fit_create_batched(n, arrA, arrB, chis, float(tol), g, int(n_segments), ct.byref(o), outs)
+    _check(code, None, "tt_fit_create_batched")
+    return [Fit(ct.c_void_p(outs[i]), device, len(pairs[i][0])) for i in range(n)]
+
+
+def tt_fit_sweep_batched(fits: Sequence["Fit"], n_sweeps: int) -> list[dict]:
+    """tt_fit_sweep_batched over the handles; returns one report per handle."""
+    n = len(fits)
+    reps = (tt_sweep_report * n)()
+    hs = (ct.c_void_p * n)(*[f.h.value for f in fits])
+    code = load().tt_fit_sweep_batched(n, hs, int(n_sweeps), reps)
+    _check(code, None, "tt_fit_sweep_batched")
+    return [{k: getattr(r, k) for k, _ in tt_sweep_report._fields_} for r in reps]
 
 
 def tt_svd_truncated(M, chi_max: int, tau_rel: float = 0.0, stream=None):

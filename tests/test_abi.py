@@ -72,3 +72,22 @@ int main(void) {
     O = ttfit.tt_fit_options
     assert sizes[3:7] == [O.seed.offset, O.init_C.offset, O.stream.offset, O.fault_inject.offset]
     assert sizes[7] == ttfit.tt_mpo_desc.dtype.offset
+
+
+def test_partition_matches_oracle_without_gpu():
+    """tt_partition (host-only) lays out the same segments as the oracle's
+    Alg. 6 simulation, for many lengths, segment counts and edge extras."""
+    ttfit = _built_lib()
+    from oracle.parallel import partition
+    lib = ttfit.load()
+    lib.tt_partition.argtypes = [ct.c_int, ct.c_int, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]
+    lib.tt_partition.restype = ct.c_int
+    for L in range(4, 70, 3):
+        for n in range(1, L // 2 + 1, max(1, L // 12)):
+            for e in (0, 1, 3, 7):
+                first = (ct.c_int * n)()
+                last = (ct.c_int * n)()
+                assert lib.tt_partition(L, n, e, first, last) == ttfit.TT_OK
+                assert [(a + 1, b + 1) for a, b in zip(first, last)] == partition(L, n, e), (L, n, e)
+    one = (ct.c_int * 4)()
+    assert lib.tt_partition(7, 4, 0, one, one) == ttfit.TT_ERR_INVALID_ARGUMENT   # 7 sites < 2 x 4
