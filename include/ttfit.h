@@ -228,6 +228,36 @@ tt_status tt_fit_create_batched(int n, const tt_mpo_desc* A, const tt_mpo_desc* 
  * completed their sweeps. */
 tt_status tt_fit_sweep_batched(int n, tt_fit* const* h, int n_sweeps, tt_sweep_report* rep);
 
+/* Objectives of the adjoint (tt_mpo_grad). */
+typedef enum {
+  TT_GRAD_RESIDUAL = 0, /* f1(A, B) = ||X - A B||_F^2, X (= C) held fixed   */
+  TT_GRAD_INNER = 1     /* f2(A, B) = <X, A B> = tr(X^T A B), X (= W) fixed */
+} tt_grad_target;
+
+/* Adjoint of the fit's contraction chain (not in the paper, which does not
+ * differentiate with respect to A or B): the value of the target and its
+ * gradient with respect to every core of A and B, at fixed X (no
+ * differentiation through the fit's factorisations).
+ * <X, AB> is the three-layer network of the fit's environments (Sec. 2.3.3);
+ * its gradient with respect to a core is the network with that core cut out.
+ * ||AB||^2 uses four-layer environments (two copies of A, B); its gradient is
+ * twice the punched hole of one copy, so d f1 = 2 (G^{ABAB} - G^{XAB}).
+ * A, B, X: device MPOs (FP64 or FP32 cores, layouts as tt_mpo_desc),
+ * A.d_in == B.d_out, X.d_out == A.d_out, X.d_in == B.d_in, equal L.
+ * gA, gB: caller device buffers with the shapes (d_out, d_in, bond) of A and
+ * B, FP64 or FP32; receive dtarget/dA_l and dtarget/dB_l. *value (host, may be
+ * NULL) receives the target. precision: TT_PREC_FP64 or TT_PREC_FP32 (the
+ * contractions and environments in that type). checkpoint_every: left
+ * environments are stored every k sites and recomputed in between during the
+ * right-to-left gradient pass (1 = store all; 0 = about sqrt(L)), which bounds
+ * memory at (L/k + k) environments; the four-layer ones hold (chi_A chi_B)^2
+ * values. Runs on `stream` (cudaStream_t) and synchronises it. Errors:
+ * TT_ERR_INVALID_ARGUMENT, TT_ERR_SHAPE_MISMATCH, TT_ERR_OUT_OF_MEMORY,
+ * TT_ERR_CUDA. */
+tt_status tt_mpo_grad(const tt_mpo_desc* A, const tt_mpo_desc* B, const tt_mpo_desc* X, int target, int precision,
+                      int checkpoint_every, void* stream, const tt_mpo_desc* gA, const tt_mpo_desc* gB,
+                      double* value);
+
 /* Truncated SVD of one device matrix, the factorisation of the local update
  * (Sec. 2.3.4): M is m x n, row-major, FP64 (device). Computes the thin SVD
  * M = U diag(S) Vt in FP64 (one-sided Jacobi; singular values descending;

