@@ -9,8 +9,9 @@ of ||C||^2 between sweeps is <= 1e-8. A step is one complete fit: input
 preparation, initial guess and right environments, sweeps until converged, and
 the export of C. The default precision schedule runs cheap sweeps first and
 exact ones last: 3xTF32 tensor-core contractions with the FP32 factorisation
-until the change of ||C||^2 falls below 1e-4, then FP64 contractions with the
-FP64-polished factorisation to convergence. Metric: time-to-tol in seconds
+until the change of ||C||^2 falls below 1e-4, then FP64-class double-FP32
+contractions (on the FP32 pipes) with the FP64-polished factorisation to
+convergence. Metric: time-to-tol in seconds
 (lower is better), reported with the local-update TFLOP/s and a roofline entry
 for the dominant stage.
 
@@ -44,8 +45,8 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
-    p.add_argument("--precision", default=os.environ.get("TTFIT_BENCH_PRECISION", "tf32x3>fp64"),
-                   help='a precision ("fp64", "fp32", "tf32x3", ...) or the schedule "tf32x3>fp64"')
+    p.add_argument("--precision", default=os.environ.get("TTFIT_BENCH_PRECISION", "tf32x3>df32"),
+                   help='a precision ("fp64", "df32", "fp32", "tf32x3", ...) or a schedule "lo>hi"')
     p.add_argument("--workload", default=WORKLOAD,
                    help="synthetic workload (default: the timed one); smaller ones serve profiling captures")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -109,13 +110,15 @@ class ClockSampler:
 STAGES = ("halves_ms", "join_ms", "env_finish_ms", "factorize_ms", "gauge_ms", "contraction_flops", "launches")
 # peaks of the plain CUDA-core pipes (ALU bound): 152 SMs x FMA lanes per SM x 2 flop x max SM clock
 FMA_LANES = {"f64": 2, "f32": 128}
+DF32_INSTR = 15  # FP32 instructions of one double-FP32 multiply-add (csrc/common.cuh, madd)
 
 
 def run_fit(ttfit, Ain, Bin, schedule, seed, dev, stream, chi=CHI):
-    """One complete fit. ``schedule`` is a precision name ("fp64", "fp32", "tf32x3", ...) for a
-    single-precision fit, or "tf32x3>fp64": 3xTF32 sweeps (FP32-factorised randomized update) until
-    the relative change of ||C||^2 is below SWITCH_DELTA after an even number of sweeps, then FP64
-    contractions with the FP64-polished FP32 factorisation until converged."""
+    """One complete fit. ``schedule`` is a precision name ("fp64", "df32", "tf32x3", ...) for a
+    single-precision fit, or "lo>hi", e.g. "tf32x3>df32": sweeps in ``lo`` (FP32-factorised
+    randomized update) until the relative change of ||C||^2 is below SWITCH_DELTA after an even
+    number of sweeps, then FP64-class contractions in ``hi`` with the FP64-polished FP32
+    factorisation until converged."""
     lo, hi = (schedule.split(">") + [None])[:2]
     f = ttfit.tt_fit_create(Ain, Bin, chi, TOL, "site", update="rsvd", oversample=OVERSAMPLE, seed=seed,
                             precision=lo, device=dev, stream=stream)
@@ -243,6 +246,15 @@ def native(args):
                     "kernel": f"gemm_simt_kernel<{'double' if dt == 'f64' else 'float'}> (contraction chain, "
                               f"{dom_phase} phase)",
                     "peak_source": f"derived: 152 SMs x {FMA_LANES[dt]} {dt} FMA/clk x 2 x {mhz:.0f} MHz"}
+        elif dom_phase == "df32":
+            # a double-FP32 multiply-add issues DF32_INSTR FP32 instructions (exact product, cross terms,
+            # two-sum, renormalisation); the ceiling is the FP32 issue rate divided by that
+            peak = 152 * FMA_LANES["f32"] * 2 * mhz * 1e6 / DF32_INSTR / 1e12
+            roof = {"bound": "alu", "achieved": round(tflops, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+                    "frac": round(tflops / peak, 4), "traffic": None,
+                    "kernel": "gemm_simt_kernel<df32> (contraction chain, df32 phase)",
+                    "peak_source": f"derived: 152 SMs x 128 FP32 lanes x {mhz:.0f} MHz / {DF32_INSTR} instructions "
+                                   f"per multiply-add, x 2 flop"}
         else:
             bf16 = pk.get("bf16_tflops_sustained", 1700.0)
             ratio = 2.0 if dom_phase == "tf32" else 6.0       # TF32 is half the bf16 rate; 3xTF32 issues 3 MMAs
@@ -257,7 +269,7 @@ def native(args):
     local_flops = sum(agg[p]["contraction_flops"] for p in names)
     local_ms = sum(agg[p]["halves_ms"] + agg[p]["join_ms"] + agg[p]["env_finish_ms"] for p in names)
     rep, sweeps, phase_sweeps, _, _, launches = results[-1]
-    dtypes = {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "tf32x3": "tf32x3"}
+    dtypes = {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "tf32x3": "tf32x3", "df32": "f32x2"}
     out = {
         "metric": METRIC, "value": round(t_step, 4), "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(t_step * 1e3, 2), "higher_is_better": False,

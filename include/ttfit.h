@@ -58,7 +58,11 @@ typedef enum { TT_UPDATE_2SITE_SVD = 0, TT_UPDATE_2SITE_RSVD = 1 } tt_update;
  * operands, FP32 accumulation in tensor memory). TF32_SPLIT: the same with
  * each operand split into a TF32 high part and an FP32 remainder, three
  * products (hi*hi + hi*lo + lo*hi): about FP32 accuracy. BF16_SPLIT: reserved,
- * rejected with TT_ERR_INVALID_ARGUMENT. The non-FP64 paths factorise in
+ * rejected with TT_ERR_INVALID_ARGUMENT. DF32: every value of the chain is a
+ * pair of floats hi + lo (about 48 significant bits) and every multiply-add
+ * is an exact FP32 product plus a compensated sum, all on the FP32 pipes
+ * (FP64-class contractions at several times the FP64 rate of this GPU);
+ * factorisation as for FP64. The FP32, TF32 and TF32_SPLIT paths factorise in
  * FP32 and make the kept singular vectors an FP64 isometry (one
  * Newton-Schulz step) before the gauge update; C is returned in FP64. */
 typedef enum {
@@ -66,7 +70,8 @@ typedef enum {
   TT_PREC_FP32 = 1,
   TT_PREC_TF32 = 2,
   TT_PREC_BF16_SPLIT = 3,
-  TT_PREC_TF32_SPLIT = 4
+  TT_PREC_TF32_SPLIT = 4,
+  TT_PREC_DF32 = 5
 } tt_precision;
 
 /* Initial guess (Sec. 2.3.5). RANDOM: right-canonical MPO from a Philox4x32-10
@@ -100,12 +105,14 @@ typedef struct {
   int precision;       /* tt_precision, default TT_PREC_FP64                              */
   int init;            /* tt_init, default TT_INIT_RANDOM                                 */
   const tt_mpo_desc* init_C; /* for TT_INIT_GIVEN                                          */
-  double sv_cutoff;    /* drop s_j <= sv_cutoff * s_1; <0 = default (1e-13 FP64, 1e-6 else) */
+  double sv_cutoff;    /* drop s_j <= sv_cutoff * s_1; <0 = default: 1e-13 FP64, 1e-12 DF32 */
+                       /* (FP64 factorisation), 1e-6 with an FP32 factorisation; follows  */
+                       /* tt_fit_set_precision                                            */
   double conv_tol;     /* delta threshold; <0 = use tol                                    */
   void* stream;        /* cudaStream_t; NULL = legacy default stream                       */
   int prepare_inputs;  /* 1 (default): RQ + QR sweep of A and B (Alg. 5 left_orthogonalize) */
   uint32_t fault_inject; /* host-side fault injection for tests (TT_FAULT_*), default 0     */
-  int fast_factor;     /* FP64 precision only: 1 = FP32 factorisation + FP64 Newton-Schulz  */
+  int fast_factor;     /* FP64 / DF32 only: 1 = FP32 factorisation + FP64 Newton-Schulz     */
                        /* polish (fast; subspace to FP32 accuracy), 0 (default) = FP64 SVD  */
   int n_segments;      /* segment-parallel fit (Sec. 4, Alg. 6): number of contiguous       */
                        /* segments N_p, each >= 2 sites; <= 1 (default) = serial Alg. 5.    */

@@ -52,6 +52,62 @@ struct IdxMap {
   }
 };
 
+// Double-FP32 number: the unevaluated sum hi + lo of two floats with
+// |lo| <= ulp(hi) / 2, about 48 significant bits. Its arithmetic runs on the
+// FP32 pipes, which on this GPU issue ~60x the FP64 rate: a multiply-add is
+// an exact product (Dekker's TwoProduct through one FMA), the cross terms,
+// Knuth's TwoSum and a renormalisation, 15 FP32 instructions against one DFMA.
+// Conversions from and to double are explicit so that mixed expressions do
+// not silently switch pipes.
+struct __align__(8) df32 {
+  float hi, lo;
+  df32() = default;  // trivial, so that it can live in __shared__ arrays
+  __host__ __device__ __forceinline__ df32(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ __forceinline__ explicit df32(double x) : hi((float)x), lo((float)(x - (double)(float)x)) {}
+  __host__ __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+  __host__ __device__ __forceinline__ explicit operator float() const { return hi + lo; }
+};
+
+// The error-free transformations below use the _rn intrinsics, which the
+// compiler never contracts into FMAs (a contraction would change the rounded
+// sum that the error terms are computed against).
+// s + e = a + b exactly (Knuth)
+__device__ __forceinline__ df32 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return df32(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+// renormalise (s, t) with |t| small against s (Dekker's fast two-sum)
+__device__ __forceinline__ df32 renorm(float s, float t) {
+  const float h = __fadd_rn(s, t);
+  return df32(h, __fsub_rn(t, __fsub_rn(h, s)));
+}
+__device__ __forceinline__ df32 operator+(df32 a, df32 b) {
+  df32 s = two_sum(a.hi, b.hi);
+  return renorm(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df32 operator-(df32 a) { return df32(-a.hi, -a.lo); }
+__device__ __forceinline__ df32 operator-(df32 a, df32 b) { return a + (-b); }
+__device__ __forceinline__ df32& operator+=(df32& a, df32 b) { return a = a + b; }
+__device__ __forceinline__ df32 operator*(df32 a, df32 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);  // exact rounding error of the leading product
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  return renorm(p, e);
+}
+// a * b + c, the inner step of the GEMM, for every working type
+__host__ __device__ __forceinline__ float madd(float a, float b, float c) { return fmaf(a, b, c); }
+__host__ __device__ __forceinline__ double madd(double a, double b, double c) { return ::fma(a, b, c); }
+__device__ __forceinline__ df32 madd(df32 a, df32 b, df32 c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  const df32 s = two_sum(p, c.hi);
+  return renorm(s.hi, __fadd_rn(s.lo, __fadd_rn(e, c.lo)));
+}
+__host__ __device__ __forceinline__ bool operator!=(df32 a, df32 b) { return a.hi != b.hi || a.lo != b.lo; }
+__host__ __device__ __forceinline__ bool operator==(df32 a, df32 b) { return a.hi == b.hi && a.lo == b.lo; }
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

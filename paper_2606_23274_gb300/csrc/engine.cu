@@ -115,6 +115,7 @@ struct tt_fit {
   // configuration
   int L = 0, chi_max = 0, gauge = 0, update = 0, oversample = 10, precision = 0, init = 0;
   double tol = 0, cutoff = 1e-13, conv_tol = 0;
+  bool cutoff_user = false;  // sv_cutoff given by the caller (else it follows the precision)
   uint64_t seed = 0;
   uint32_t fault = 0;
   int sm_count = 0;
@@ -144,7 +145,8 @@ struct tt_fit {
   long long launches = 0, tc_launches = 0;  // monotonic since creation
   long long sweep_launches = 0;              // launches of the last tt_fit_sweep call
   bool have_times = false;
-  bool use_f32 = false;   // chain type: float (non-FP64 precisions) or double
+  bool use_f32 = false;   // chain type: float (FP32 / TF32 precisions), df32 (DF32) or double (FP64)
+  bool use_df = false;
   bool fact_f32 = false;  // FP32 factorisation + FP64 polish (always for float chains; optional for FP64)
   std::vector<void*> chain_bufs;  // buffers rebuilt when the chain precision changes
 };
@@ -177,6 +179,25 @@ inline long long prodll(std::initializer_list<long long> v) {
 // Contraction dispatch: the tensor-core kernel for TF32 chains whenever TMA can
 // address both operands (16-byte aligned rows), the CUDA-core kernel otherwise
 // (FP64 / FP32 chains, and the 1- or 2-wide bonds at the ends of the chain).
+// Relative singular-value cut-off when the caller gives none: a little above
+// the rounding level of the factorisation and of the contractions. An FP32
+// factorisation resolves values down to ~1e-7 s_1 only; keeping smaller ones
+// would feed its noise back into C.
+inline double default_cutoff(int precision, bool fact_f32) {
+  if (fact_f32) return 1e-6;
+  return precision == TT_PREC_FP64 ? 1e-13 : precision == TT_PREC_DF32 ? 1e-12 : 1e-6;
+}
+
+// type of the exact factorisation for a chain type: FP64 for the FP64-class chains
+template <typename T>
+struct FactT {
+  using type = T;
+};
+template <>
+struct FactT<df32> {
+  using type = double;
+};
+
 template <typename T>
 void gemm(tt_fit* h, const GemmArgs<T>& g, bool chain = false) {
   const size_t wse = W(h).gws_elems * sizeof(double) / sizeof(T);
@@ -762,8 +783,9 @@ struct Sweeper {
       CK(truncate_rule<float>((const float*)W(h).fS, p, W(h).dnorm, h->tol / L, h->chi_max, h->cutoff, W(h).dk, W(h).ddinfo,
                               W(h).st));
     } else {
-      p = factorize<T, T>(h, m, n, sweep, l + 1);
-      CK(truncate_rule<T>((const T*)W(h).fS, p, W(h).dnorm, h->tol / L, h->chi_max, h->cutoff, W(h).dk, W(h).ddinfo, W(h).st));
+      using FX = typename FactT<T>::type;
+      p = factorize<T, FX>(h, m, n, sweep, l + 1);
+      CK(truncate_rule<FX>((const FX*)W(h).fS, p, W(h).dnorm, h->tol / L, h->chi_max, h->cutoff, W(h).dk, W(h).ddinfo, W(h).st));
     }
     CK(cudaEventRecord(W(h).ev[4], W(h).st));
     CK(cudaMemcpyAsync(W(h).hk, W(h).dk, sizeof(int), cudaMemcpyDeviceToHost, W(h).st));
@@ -795,7 +817,8 @@ struct Sweeper {
     const int mode = (h->gauge == TT_GAUGE_INVERSE_CANONICAL) ? 2 : (fwd ? 0 : 1);
     CK(cudaEventRecord(W(h).ev[5], W(h).st));
     if (!h->fact_f32) {
-      CK(gauge_update<T, T>(mode, m, n, (const T*)W(h).fUM, m, (const T*)W(h).fS, (const T*)W(h).fVM, n, W(h).dk, h->C64[l],
+      using FX = typename FactT<T>::type;
+      CK(gauge_update<T, FX>(mode, m, n, (const FX*)W(h).fUM, m, (const FX*)W(h).fS, (const FX*)W(h).fVM, n, W(h).dk, h->C64[l],
                             h->C64[l + 1], h->Y[l + 1], (T*)h->Ut[l], (T*)h->Vt[l + 1], W(h).st));
     } else {
       polish_update<T, float>(h, mode, m, n, k, l);
@@ -1248,6 +1271,7 @@ void setup(tt_fit* h, const std::vector<double*>& C0) {
                          W(h).st));
   }
   if (h->use_f32) rebuild_chain<float>(h);
+  else if (h->use_df) rebuild_chain<df32>(h);
   else rebuild_chain<double>(h);
 }
 
@@ -1336,7 +1360,7 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
       o = *opt;
     }
     if (o.update != 0 && o.update != 1) return TT_ERR_INVALID_ARGUMENT;
-    if (o.precision < 0 || o.precision > 4 || o.oversample < 0) return TT_ERR_INVALID_ARGUMENT;
+    if (o.precision < 0 || o.precision > 5 || o.oversample < 0) return TT_ERR_INVALID_ARGUMENT;
     if (o.init < 0 || o.init > 2 || (o.init == TT_INIT_GIVEN && !o.init_C)) return TT_ERR_INVALID_ARGUMENT;
     if (o.precision == TT_PREC_BF16_SPLIT) return TT_ERR_INVALID_ARGUMENT;  // not in this build
     if (o.n_segments > 1 && gauge != TT_GAUGE_INVERSE_CANONICAL) return TT_ERR_INVALID_ARGUMENT;
@@ -1365,9 +1389,11 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
     h->precision = o.precision;
     h->init = o.init;
     h->seed = o.seed;
-    h->use_f32 = (o.precision != TT_PREC_FP64);
+    h->use_f32 = (o.precision != TT_PREC_FP64 && o.precision != TT_PREC_DF32);
+    h->use_df = (o.precision == TT_PREC_DF32);
     h->fact_f32 = h->use_f32 || o.fast_factor;
-    h->cutoff = o.sv_cutoff >= 0 ? o.sv_cutoff : (o.precision == TT_PREC_FP64 ? 1e-13 : 1e-6);
+    h->cutoff_user = o.sv_cutoff >= 0;
+    h->cutoff = h->cutoff_user ? o.sv_cutoff : default_cutoff(o.precision, h->fact_f32);
     h->conv_tol = o.conv_tol >= 0 ? o.conv_tol : tol;
     int dev = 0;
     CK(cudaGetDevice(&dev));
@@ -1490,6 +1516,10 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
       if (h->use_f32) {
         vidal_init<float, float>(h);
         all_envs<float>(h);
+      } else if (h->use_df) {
+        if (h->fact_f32) vidal_init<df32, float>(h);
+        else vidal_init<df32, double>(h);
+        all_envs<df32>(h);
       } else if (h->fact_f32) {
         vidal_init<double, float>(h);
         all_envs<double>(h);
@@ -1536,8 +1566,9 @@ tt_status tt_fit_sweep(tt_fit* h, int n_sweeps, tt_sweep_report* rep) {
       for (int s = 0; s < n_sweeps && !h->converged; ++s) {
         const int ph = h->phases_done % 2;
         double maxd = 0;
-        const double n2 = h->use_f32 ? run_phase<float>(h, ph, h->phases_done, maxd)
-                                     : run_phase<double>(h, ph, h->phases_done, maxd);
+        const double n2 = h->use_f32  ? run_phase<float>(h, ph, h->phases_done, maxd)
+                          : h->use_df ? run_phase<df32>(h, ph, h->phases_done, maxd)
+                                      : run_phase<double>(h, ph, h->phases_done, maxd);
         h->phases_done++;
         h->sweeps_done++;
         h->cur_n2 = n2;
@@ -1550,6 +1581,9 @@ tt_status tt_fit_sweep(tt_fit* h, int n_sweeps, tt_sweep_report* rep) {
       }
     } else if (h->use_f32) {
       Sweeper<float> sw(h);
+      sw.run(n_sweeps);
+    } else if (h->use_df) {
+      Sweeper<df32> sw(h);
       sw.run(n_sweeps);
     } else {
       Sweeper<double> sw(h);
@@ -1630,7 +1664,7 @@ tt_status tt_fit_result(const tt_fit* hc, tt_mpo_desc* C, double* lambdas) {
 }
 
 tt_status tt_fit_set_precision(tt_fit* h, int precision, int fast_factor) {
-  if (!h || precision < 0 || precision > 4 || precision == TT_PREC_BF16_SPLIT) return TT_ERR_INVALID_ARGUMENT;
+  if (!h || precision < 0 || precision > 5 || precision == TT_PREC_BF16_SPLIT) return TT_ERR_INVALID_ARGUMENT;
   if (h->poisoned) return TT_ERR_STATE;
   if (h->segs.size() > 1 ? (h->phases_done % 2 != 0) : !h->forward) {
     h->last_error = h->segs.size() > 1
@@ -1640,15 +1674,19 @@ tt_status tt_fit_set_precision(tt_fit* h, int precision, int fast_factor) {
   }
   LaunchTally tally(h);
   try {
-    const bool f32 = precision != TT_PREC_FP64;
+    const bool f32 = precision != TT_PREC_FP64 && precision != TT_PREC_DF32;
     h->precision = precision;
     h->use_f32 = f32;
+    h->use_df = precision == TT_PREC_DF32;
     h->fact_f32 = f32 || fast_factor;
+    if (!h->cutoff_user) h->cutoff = default_cutoff(precision, h->fact_f32);
     h->converged = false;
     if (f32) rebuild_chain<float>(h);
+    else if (h->use_df) rebuild_chain<df32>(h);
     else rebuild_chain<double>(h);
     if (h->segs.size() > 1) {  // the parallel fit needs every environment and half
       if (f32) all_envs<float>(h);
+      else if (h->use_df) all_envs<df32>(h);
       else all_envs<double>(h);
     }
   } catch (const TTError& e) {

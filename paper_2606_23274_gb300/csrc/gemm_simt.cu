@@ -2,8 +2,9 @@
 //   C[cm(m) + cn(n)] = alpha * sum_k A[am(m) + ak(k)] * B[bn(n) + bk(k)] + beta * C[...]
 // Every contraction of the fit (environment diagrams, halves, two-site tensor)
 // is one call with the index maps of its operands (Sec. 2.3.3 / 2.3.4 shapes).
-// This is the FP64 path and the plain-FP32 baseline; the tensor-core path
-// lives in gemm_tc.cu.
+// It serves the FP64 path, the double-FP32 (df32) path that reaches FP64-class
+// accuracy on the FP32 pipes, and the plain-FP32 baseline; the tensor-core
+// path lives in gemm_tc.cu.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -12,10 +13,11 @@ namespace ttfit {
 constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 
 template <typename T>
-__global__ void __launch_bounds__(NT) gemm_simt_kernel(GemmArgs<T> g, T* __restrict__ ws, int k_per_split) {
+__global__ void __launch_bounds__(NT, 3) gemm_simt_kernel(GemmArgs<T> g, T* __restrict__ ws, int k_per_split) {
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
   __shared__ long long arow[BM], brow[BN];
+  __shared__ long long akoff[BK], bkoff[BK];  // k offsets of the current tile (one index-map evaluation each)
   const int tid = threadIdx.x;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int kb = blockIdx.z * k_per_split;
@@ -31,17 +33,20 @@ __global__ void __launch_bounds__(NT) gemm_simt_kernel(GemmArgs<T> g, T* __restr
     for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
 
   for (int k0 = kb; k0 < ke; k0 += BK) {
+    if (tid < BK) akoff[tid] = (k0 + tid < ke) ? g.ak(k0 + tid) : 0;
+    else if (tid < 2 * BK) bkoff[tid - BK] = (k0 + tid - BK < ke) ? g.bk(k0 + tid - BK) : 0;
+    __syncthreads();
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       int e = tid + NT * i;
       int r, kk;
       if (g.a_kfast) { r = e >> 4; kk = e & 15; } else { r = e & 63; kk = e >> 6; }
       T v = T(0);
-      if (m0 + r < g.M && k0 + kk < ke) v = g.A[arow[r] + g.ak(k0 + kk)];
+      if (m0 + r < g.M && k0 + kk < ke) v = g.A[arow[r] + akoff[kk]];
       As[kk][r] = v;
       if (g.b_kfast) { r = e >> 4; kk = e & 15; } else { r = e & 63; kk = e >> 6; }
       T w = T(0);
-      if (n0 + r < g.N && k0 + kk < ke) w = g.B[brow[r] + g.bk(k0 + kk)];
+      if (n0 + r < g.N && k0 + kk < ke) w = g.B[brow[r] + bkoff[kk]];
       Bs[kk][r] = w;
     }
     __syncthreads();
@@ -55,7 +60,7 @@ __global__ void __launch_bounds__(NT) gemm_simt_kernel(GemmArgs<T> g, T* __restr
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < 4; ++j) acc[i][j] = madd(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
@@ -119,6 +124,7 @@ cudaError_t splitk_reduce(const GemmArgs<T>& g, const T* ws, int splits, int sm_
 }
 template cudaError_t splitk_reduce<double>(const GemmArgs<double>&, const double*, int, int, cudaStream_t);
 template cudaError_t splitk_reduce<float>(const GemmArgs<float>&, const float*, int, int, cudaStream_t);
+template cudaError_t splitk_reduce<df32>(const GemmArgs<df32>&, const df32*, int, int, cudaStream_t);
 
 template <typename T>
 cudaError_t gemm_simt(const GemmArgs<T>& g, T* ws, size_t ws_elems, int sm_count, cudaStream_t st) {
@@ -159,5 +165,6 @@ cudaError_t gemm_simt(const GemmArgs<T>& g, T* ws, size_t ws_elems, int sm_count
 
 template cudaError_t gemm_simt<double>(const GemmArgs<double>&, double*, size_t, int, cudaStream_t);
 template cudaError_t gemm_simt<float>(const GemmArgs<float>&, float*, size_t, int, cudaStream_t);
+template cudaError_t gemm_simt<df32>(const GemmArgs<df32>&, df32*, size_t, int, cudaStream_t);
 
 }  // namespace ttfit

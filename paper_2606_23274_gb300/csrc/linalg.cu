@@ -353,6 +353,26 @@ __global__ void __launch_bounds__(1024) frob_kernel(const T* __restrict__ x, lon
   }
 }
 
+// double-FP32 values: the norm is taken of hi + lo in FP64 (small arrays only)
+template <>
+__global__ void __launch_bounds__(1024) frob_kernel<df32>(const df32* __restrict__ x, long long n, double* out,
+                                                           uint32_t* errw) {
+  __shared__ double red[32];
+  double part = 0;
+  bool bad = false;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    const double v = (double)x[i];
+    bad |= !isfinite(v);
+    part += v * v;
+  }
+  double s = block_sum(part, red);
+  bad = __syncthreads_or(bad);
+  if (threadIdx.x == 0) {
+    *out = sqrt(s);
+    if (bad && errw) atomicOr(errw, ERRW_NAN);
+  }
+}
+
 template <typename T>
 cudaError_t frob_norm(const T* x, long long n, double* out, uint32_t* errw, cudaStream_t st) {
   ++tl_launches;
@@ -361,6 +381,7 @@ cudaError_t frob_norm(const T* x, long long n, double* out, uint32_t* errw, cuda
 }
 template cudaError_t frob_norm<double>(const double*, long long, double*, uint32_t*, cudaStream_t);
 template cudaError_t frob_norm<float>(const float*, long long, double*, uint32_t*, cudaStream_t);
+template cudaError_t frob_norm<df32>(const df32*, long long, double*, uint32_t*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 template <typename F>
@@ -450,6 +471,10 @@ template cudaError_t gauge_update<float, float>(int, int, int, const float*, int
                                                 const int*, double*, double*, double*, float*, float*, cudaStream_t);
 template cudaError_t gauge_update<double, float>(int, int, int, const float*, int, const float*, const float*, int,
                                                  const int*, double*, double*, double*, double*, double*, cudaStream_t);
+template cudaError_t gauge_update<df32, float>(int, int, int, const float*, int, const float*, const float*, int,
+                                               const int*, double*, double*, double*, df32*, df32*, cudaStream_t);
+template cudaError_t gauge_update<df32, double>(int, int, int, const double*, int, const double*, const double*, int,
+                                                const int*, double*, double*, double*, df32*, df32*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 template <typename Tin, typename Tout>
@@ -458,7 +483,8 @@ __global__ void copy_map_kernel(int rows, int cols, const Tin* __restrict__ in, 
   const long long tot = (long long)rows * cols;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(e / cols), j = (int)(e % cols);
-    out[om(i) + on(j)] = (Tout)(scale * (double)in[im(i) + in_(j)]);
+    const Tin x = in[im(i) + in_(j)];
+    out[om(i) + on(j)] = scale == 1.0 ? (Tout)x : (Tout)(scale * (double)x);  // plain copies stay off the FP64 pipe
   }
 }
 
@@ -481,6 +507,14 @@ template cudaError_t copy_map<float, double>(int, int, const float*, IdxMap, Idx
                                              cudaStream_t);
 template cudaError_t copy_map<float, float>(int, int, const float*, IdxMap, IdxMap, float*, IdxMap, IdxMap, double,
                                             cudaStream_t);
+template cudaError_t copy_map<double, df32>(int, int, const double*, IdxMap, IdxMap, df32*, IdxMap, IdxMap, double,
+                                            cudaStream_t);
+template cudaError_t copy_map<df32, double>(int, int, const df32*, IdxMap, IdxMap, double*, IdxMap, IdxMap, double,
+                                            cudaStream_t);
+template cudaError_t copy_map<df32, float>(int, int, const df32*, IdxMap, IdxMap, float*, IdxMap, IdxMap, double,
+                                           cudaStream_t);
+template cudaError_t copy_map<df32, df32>(int, int, const df32*, IdxMap, IdxMap, df32*, IdxMap, IdxMap, double,
+                                          cudaStream_t);
 
 // ---------------------------------------------------------------------------
 template <typename F>
@@ -596,6 +630,8 @@ template cudaError_t inverse_gauge_update<float>(int, int, int, const double*, c
                                                  double*, double*, cudaStream_t);
 template cudaError_t inverse_gauge_update<double>(int, int, int, const double*, const double*, const double*, double*,
                                                   double*, double*, cudaStream_t);
+template cudaError_t inverse_gauge_update<df32>(int, int, int, const double*, const double*, const df32*, double*,
+                                                double*, double*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 __global__ void scale_cols_kernel(int rows, int cols, const double* __restrict__ in, const double* __restrict__ y,
@@ -624,6 +660,7 @@ cudaError_t scale_rows(int rows, int cols, const double* in, const double* y, T*
 }
 template cudaError_t scale_rows<float>(int, int, const double*, const double*, float*, cudaStream_t);
 template cudaError_t scale_rows<double>(int, int, const double*, const double*, double*, cudaStream_t);
+template cudaError_t scale_rows<df32>(int, int, const double*, const double*, df32*, cudaStream_t);
 
 cudaError_t scale_cols(int rows, int cols, const double* in, const double* y, double* out, cudaStream_t st) {
   long long tot = (long long)rows * cols;
@@ -660,4 +697,5 @@ cudaError_t scale_cols_t(int rows, int cols, const double* in, const double* y, 
 }
 template cudaError_t scale_cols_t<float>(int, int, const double*, const double*, float*, cudaStream_t);
 template cudaError_t scale_cols_t<double>(int, int, const double*, const double*, double*, cudaStream_t);
+template cudaError_t scale_cols_t<df32>(int, int, const double*, const double*, df32*, cudaStream_t);
 }  // namespace ttfit

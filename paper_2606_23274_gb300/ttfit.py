@@ -21,7 +21,7 @@ TT_OK, TT_ERR_INVALID_ARGUMENT, TT_ERR_SHAPE_MISMATCH, TT_ERR_OUT_OF_MEMORY = 0,
 TT_ERR_CUDA, TT_ERR_NUMERICAL, TT_ERR_TIMEOUT, TT_ERR_STATE = 4, 5, 6, 7
 GAUGE = {"site": 0, "inverse": 1}
 UPDATE = {"svd": 0, "rsvd": 1}
-PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16_split": 3, "tf32x3": 4}
+PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16_split": 3, "tf32x3": 4, "df32": 5}
 INIT = {"random": 0, "copy_b": 1, "given": 2}
 TT_FAULT_ALLOC_FAIL, TT_FAULT_NAN_INPUT, TT_FAULT_SVD_NOCONV = 0x1, 0x2, 0x4
 DTYPE_F64, DTYPE_F32 = 0, 1

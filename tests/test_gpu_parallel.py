@@ -119,7 +119,9 @@ def test_parallel_precision_switch():
     p = ParallelFitOracle(A, B, 12, 0.0, 3)
     for _ in range(12):
         p.full_sweep_set()
-    assert _rel(_cpu(f.result()), p.result()) <= 1e-6
+    # ||C||^2 is stationary at the fixed point, so delta <= 1e-10 bounds the
+    # distance of the operators only to about sqrt(delta)
+    assert _rel(_cpu(f.result()), p.result()) <= 1e-5
     f.destroy()
 
 
@@ -164,3 +166,15 @@ def test_batched_segment_parallel_pairs():
         p.full_sweep_set()
         assert _rel(_cpu(f.result()), p.result()) <= 1e-9
         f.destroy()
+
+
+def test_parallel_df32_matches_oracle():
+    A, B = mpo_pair("kron_L12_chi32", 1)
+    p = ParallelFitOracle(A, B, 12, 0.0, 3, 1, update="rsvd", oversample=4, seed=5, sv_cutoff=1e-12)
+    par = [p.full_sweep_set() for _ in range(2)]
+    f = ttfit.tt_fit_create(A, B, 12, 0.0, "inverse", update="rsvd", oversample=4, seed=5, precision="df32",
+                            sv_cutoff=1e-12, conv_tol=0.0, n_segments=3, edge_extra=1)
+    reps = [f.sweep(1) for _ in range(4)]
+    assert abs(reps[3]["norm2_C"] - par[1][0]) <= 1e-10 * par[1][0]
+    assert _rel(_cpu(f.result()), p.result()) <= 1e-9
+    f.destroy()

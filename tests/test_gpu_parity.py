@@ -263,3 +263,59 @@ def test_fast_factor_fp64_converges():
     assert reps[-1]["delta"] <= 1e-10
     res = mpo_diff_norm(N, C) ** 2
     assert res <= res_o * (1 + 1e-6)
+
+
+@pytest.mark.parametrize("gauge", ["site", "inverse"])
+@pytest.mark.parametrize("update", ["svd", "rsvd"])
+def test_df32_fit_matches_fp64_oracle(gauge, update):
+    """Double-FP32 contractions (FP64-class on the FP32 pipes) with the FP64
+    factorisation: the same results as the FP64 oracle to 1e-9."""
+    A, B = mpo_pair("kron_L12_chi32", 1)
+    chi, sweeps = 12, 4
+    f = FitOracle(A, B, chi, 0.0, gauge=gauge, update=update, oversample=4, seed=3, sv_cutoff=1e-12)
+    f.sweep(sweeps, stop_on_converge=False)
+    C, reps, b, lam = _gpu_fit(A, B, chi, 0.0, sweeps, gauge=gauge, update=update, oversample=4, seed=3,
+                               precision="df32", sv_cutoff=1e-12, conv_tol=0.0)
+    assert b == f.bonds()
+    assert _rel(C, f.result()) <= 1e-9
+    for r, h in zip(reps, f.st.history):
+        assert abs(r["norm2_C"] - h.norm2) <= 1e-10 * h.norm2
+
+
+def test_df32_exact_product():
+    A, B = mpo_pair("gauss_L8_chi8", 0)
+    C, _, b, _ = _gpu_fit(A, B, 64, 0.0, 2, precision="df32")
+    D = to_dense(A) @ to_dense(B)
+    assert np.linalg.norm(to_dense(C) - D) <= 1e-11 * np.linalg.norm(D)
+
+
+def test_df32_fast_factor_converges():
+    """The bench's second phase: DF32 contractions with the FP32 factorisation
+    and FP64 polish reach delta <= 1e-10 and the FP64 oracle's operator."""
+    A, B = _fast_pair(3)
+    o = FitOracle(A, B, 12, 0.0)
+    o.sweep(12, stop_on_converge=False)
+    h = ttfit.tt_fit_create(A, B, 12, 0.0, "site", precision="df32", fast_factor=True, conv_tol=0.0)
+    reps = [h.sweep(1) for _ in range(12)]
+    assert reps[-1]["delta"] <= 1e-10
+    # the FP32 subspace enters ||C||^2 only at second order: delta <= 1e-10
+    # bounds the operator distance to about sqrt(delta)
+    assert _rel([c.cpu().numpy() for c in h.result()], o.result()) <= 1e-5
+    h.destroy()
+
+
+def test_switch_tf32x3_to_df32_and_cutoff_follows_precision():
+    """A 3xTF32 start (cut-off 1e-6) switched to DF32 keeps values down to the
+    DF32 cut-off (1e-12), like an FP64 fit with that cut-off."""
+    A, B = _fast_pair(2)
+    o = FitOracle(A, B, 12, 0.0, sv_cutoff=1e-12)
+    o.sweep(14, stop_on_converge=False)
+    h = ttfit.tt_fit_create(A, B, 12, 0.0, "site", precision="tf32x3", conv_tol=0.0)
+    h.sweep(2)
+    h.set_precision("df32")
+    for _ in range(12):
+        rep = h.sweep(1)
+    assert rep["delta"] <= 1e-10
+    assert h.bonds() == o.bonds()
+    assert _rel([c.cpu().numpy() for c in h.result()], o.result()) <= 1e-8
+    h.destroy()
