@@ -125,9 +125,11 @@ def run_fit(ttfit, Ain, Bin, schedule, seed, dev, stream, chi=CHI):
     phases = {lo: {k: 0.0 for k in STAGES}}
     phase_sweeps = {lo: 0}
     cur, sweeps, rep = lo, 0, None
+    history = []
     while sweeps < MAX_SWEEPS:
         rep = f.sweep(1)
         sweeps += 1
+        history.append(rep["delta"])
         phase_sweeps[cur] += 1
         st = f.stage_times()
         for k in STAGES:
@@ -142,6 +144,7 @@ def run_fit(ttfit, Ain, Bin, schedule, seed, dev, stream, chi=CHI):
     C = f.result()
     launches = f.launch_count()
     f.destroy()
+    rep["history"] = history
     return rep, sweeps, phase_sweeps, phases, C, launches
 
 
@@ -283,6 +286,7 @@ def native(args):
                    "l2": "flushed between timed steps (256 MB write)"},
         "sweeps_to_tol": sweeps, "sweeps_per_phase": phase_sweeps, "converged": bool(rep["converged"]),
         "final_delta": rep["delta"], "norm2_C": rep["norm2_C"],
+        "delta_history": [float(f"{d:.3e}") if d != float("inf") else None for d in rep["history"]],
         "local_update_tflops": round(local_flops / (local_ms * 1e-3) / 1e12, 3) if local_ms > 0 else None,
         "stage_ms_per_fit": {p: {k: round(agg[p][k], 2) for k in STAGES[:5]} for p in names},
         "roofline": roof, "clocks": clk, "e2e": e2e, "gpu_launches": int(sum(r[5] for r in results)), "gpu_launches_per_step": int(launches),

@@ -562,7 +562,7 @@ struct Chain {
 // S (p, sorted), V_M (n x p, ld n). Returns p (computed singular triplets).
 // ---------------------------------------------------------------------------
 template <typename T, typename F>
-int factorize(tt_fit* h, int m, int n, int sweep, int site1) {
+int factorize(tt_fit* h, int m, int n, int sweep, int site1, int need = 3) {
   F *fX = (F*)W(h).fX, *fQ = (F*)W(h).fQ, *fR = (F*)W(h).fR, *fU = (F*)W(h).fU, *fV = (F*)W(h).fV, *fVw = (F*)W(h).fVw;
   F *fS = (F*)W(h).fS, *fUM = (F*)W(h).fUM, *fVM = (F*)W(h).fVM, *fOm = (F*)W(h).fOm, *MF = (F*)W(h).fY;
   F *fBt = (F*)W(h).fBt, *fQ2 = (F*)W(h).fQ2, *fR2 = (F*)W(h).fR2;
@@ -592,6 +592,21 @@ int factorize(tt_fit* h, int m, int n, int sweep, int site1) {
     g2.C = fBt; g2.cm = IdxMap::lin(1); g2.cn = IdxMap::lin(n);
     gemm<F>(h, g2);
     qrf(n, ks, fBt, fQ2, fR2);                    // Bm^T = Q2 R2
+    if (need == 1) {
+      // only U_M = Q Vr is wanted: one-sided Jacobi on R2^T gives Vr as its
+      // normalised columns, with no rotations to accumulate (and it converges
+      // in fewer sweeps than on R2)
+      copymap<F, F>(h, ks, ks, fR2, IdxMap::lin(1), IdxMap::lin(ks), fX, IdxMap::lin(ks), IdxMap::lin(1));
+      CK(jacobi_svd<F, F>(ks, ks, fX, fV, fS, nullptr, fVw, 60, W(h).errw, W(h).st));
+      GemmArgs<F> g3;  // U_M = Q Vr (m x ks)
+      g3.M = m; g3.N = ks; g3.K = ks;
+      g3.A = fQ; g3.am = IdxMap::lin(1); g3.ak = IdxMap::lin(m); g3.a_kfast = false;
+      g3.B = fV; g3.bn = IdxMap::lin(ks); g3.bk = IdxMap::lin(1);
+      g3.C = fUM; g3.cm = IdxMap::lin(1); g3.cn = IdxMap::lin(m);
+      gemm<F>(h, g3);
+      CK(fix_signs<F>(m, n, ks, fUM, m, (F*)nullptr, n, W(h).st));
+      return ks;
+    }
     jac(ks, ks, fR2, fU, fS, fV);                 // R2 = Ur S Vr^T
     GemmArgs<F> g3;  // U_M = Q Vr (m x ks)
     g3.M = m; g3.N = ks; g3.K = ks;
@@ -779,7 +794,9 @@ struct Sweeper {
     CK(cudaEventRecord(W(h).ev[3], W(h).st));
     int p;
     if (h->fact_f32) {
-      p = factorize<T, float>(h, m, n, sweep, l + 1);
+      // a forward step of the site gauge keeps only U (C_l = U, C_{l+1} = U^T Theta)
+      const bool left_only = h->gauge != TT_GAUGE_INVERSE_CANONICAL && fwd;
+      p = factorize<T, float>(h, m, n, sweep, l + 1, left_only ? 1 : 3);
       CK(truncate_rule<float>((const float*)W(h).fS, p, W(h).dnorm, h->tol / L, h->chi_max, h->cutoff, W(h).dk, W(h).ddinfo,
                               W(h).st));
     } else {

@@ -2,8 +2,10 @@
 // Householder QR, one-sided Jacobi SVD, the truncation rule (Sec. 2.3.4), the
 // gauge update of Alg. 3 / Alg. 4, Philox Gaussian fill (Sec. 3.1's Omega),
 // layout copies and norms.
+#include <cooperative_groups.h>
 #include <algorithm>
 #include <cfloat>
+#include <type_traits>
 #include "common.cuh"
 #include "kernels.h"
 
@@ -158,11 +160,30 @@ __device__ __forceinline__ void rr_pair(int round, int k, int P, int& i, int& j)
   }
 }
 
+// Jacobi rotation (c, s) that zeroes the (i, j) entry of the 2x2 Gram block
+// [[a, g], [g, b]] (Rutishauser's formulas). In FP32 the fast reciprocal square
+// root and division serve: any rotation this close to the exact one still
+// drives the pair towards orthogonality, and convergence is decided on the
+// recomputed Gram entries, not on these values.
+__device__ __forceinline__ void rotation_params(float a, float b, float g, float& cs, float& sn) {
+  const float zeta = __fdividef(b - a, 2.f * g);
+  const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+  cs = rsqrtf(1.f + t * t);
+  sn = cs * t;
+}
+__device__ __forceinline__ void rotation_params(double a, double b, double g, double& cs, double& sn) {
+  const double zeta = (b - a) / (2.0 * g);
+  const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  cs = 1.0 / sqrt(1.0 + t * t);
+  sn = cs * t;
+}
+
 template <typename C, typename S, int NPW>
 __global__ void __launch_bounds__(1024) jacobi_kernel(int q, int p, S* __restrict__ Wg, S* __restrict__ Vg,
                                                       int max_sweeps, double tol, uint32_t* errw,
                                                       S* __restrict__ Uo, S* __restrict__ So,
                                                       S* __restrict__ Vo, int in_smem) {
+  const bool want_v = Vo != nullptr;  // the right rotations are accumulated only when asked for
   extern __shared__ __align__(16) unsigned char jsm[];
   __shared__ int rotated;
   __shared__ C nrm[1024];
@@ -175,10 +196,11 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int q, int p, S* __restric
     V = W + (size_t)q * p;
     for (long long e = threadIdx.x; e < (long long)q * p; e += blockDim.x) W[e] = Wg[e];
   }
-  for (long long e = threadIdx.x; e < (long long)p * p; e += blockDim.x) {
-    int i = (int)(e % p), c = (int)(e / p);
-    V[e] = (i == c) ? S(1) : S(0);
-  }
+  if (want_v)
+    for (long long e = threadIdx.x; e < (long long)p * p; e += blockDim.x) {
+      int i = (int)(e % p), c = (int)(e / p);
+      V[e] = (i == c) ? S(1) : S(0);
+    }
   const int P = p + (p & 1);
   const C ctol2 = (C)(tol * tol);
   int sweep = 0;
@@ -233,10 +255,7 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int q, int p, S* __restric
         cs[t] = C(1);
         sn[t] = C(0);
         if (rot[t]) {
-          const C zeta = (b[t] - a[t]) / (C(2) * g[t]);
-          const C tt = (zeta >= C(0) ? C(1) : C(-1)) / (fabs(zeta) + sqrt(C(1) + zeta * zeta));
-          cs[t] = C(1) / sqrt(C(1) + tt * tt);
-          sn[t] = cs[t] * tt;
+          rotation_params(a[t], b[t], g[t], cs[t], sn[t]);
           any = true;
         }
       }
@@ -252,7 +271,7 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int q, int p, S* __restric
             wj[r] = (S)(sn[t] * x + cs[t] * y);
           }
         }
-        for (int r = lane; r < p; r += 32) {
+        for (int r = lane; want_v && r < p; r += 32) {
 #pragma unroll
           for (int t = 0; t < NPW; ++t) {
             if (!rot[t]) continue;
@@ -295,8 +314,184 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int q, int p, S* __restric
     const C s = nrm[c];
     const C inv = s > C(0) ? C(1) / s : C(0);
     for (int r = lane; r < q; r += 32) Uo[(size_t)rk * q + r] = (S)((C)W[(size_t)c * q + r] * inv);
-    for (int r = lane; r < p; r += 32) Vo[(size_t)rk * p + r] = V[(size_t)c * p + r];
+    if (want_v)
+      for (int r = lane; r < p; r += 32) Vo[(size_t)rk * p + r] = V[(size_t)c * p + r];
   }
+}
+
+// ---------------------------------------------------------------------------
+// One-sided Jacobi on a thread-block cluster of JC CTAs (JC SMs). The p columns
+// (w part: q rows; v part: the accumulated rotations, p rows) are cut into
+// 2 JC blocks of b columns that live in the CTAs' shared memory, two blocks per
+// CTA. A sweep is a round-robin tournament of the blocks (circle method, 2 JC - 1
+// super-rounds): in each super-round a CTA orthogonalises every pair of columns
+// between its two blocks (b micro-rounds of b disjoint pairs, one warp per
+// pair); in the first super-round it also orthogonalises the columns inside each
+// of its blocks. Between super-rounds every CTA pulls its next two blocks from
+// the CTAs that hold them (distributed shared memory, double-buffered), behind
+// one cluster barrier. Every column meets every other once per sweep, as in the
+// cyclic method; the sweep count and the rotation test are those of
+// jacobi_kernel. All CTAs run the same number of barriers (the stop decision is
+// a cluster-wide OR read by all), so no barrier waits on a CTA that has left.
+// ---------------------------------------------------------------------------
+namespace cg = cooperative_groups;
+constexpr int JC = 8;  // CTAs per cluster (portable size)
+
+template <typename C>
+__device__ __forceinline__ bool jacobi_pair(C* __restrict__ xi, C* __restrict__ xj, int q, int rows, C tol2) {
+  const int lane = threadIdx.x & 31;
+  C a = 0, b = 0, g = 0;
+  for (int r = lane; r < q; r += 32) {
+    const C x = xi[r], y = xj[r];
+    a += x * x;
+    b += y * y;
+    g += x * y;
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  g = warp_sum(g);
+  if (!(a > C(0) && b > C(0) && g * g > tol2 * a * b)) return false;
+  C cs, sn;
+  rotation_params(a, b, g, cs, sn);
+  for (int r = lane; r < rows; r += 32) {
+    const C x = xi[r], y = xj[r];
+    xi[r] = cs * x - sn * y;
+    xj[r] = sn * x + cs * y;
+  }
+  return true;
+}
+
+template <typename C>
+__global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(1024)
+    jacobi_cluster_kernel(int q, int p, int b, const C* __restrict__ Win, int max_sweeps, double tol, uint32_t* errw,
+                          C* __restrict__ Uo, C* __restrict__ So, C* __restrict__ Vo) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int P = 2 * JC;
+  const bool want_v = Vo != nullptr;
+  const int rows = q + (want_v ? p : 0);  // a column: its w part, then its v part
+  extern __shared__ __align__(16) unsigned char jcs[];
+  C* buf = (C*)jcs;                                       // [2 buffers][2 slots][b][rows]
+  int* ids = (int*)(buf + (size_t)4 * b * rows);          // [2 buffers][2 slots][b] global column or -1
+  C* nrm = (C*)(ids + 4 * b + 4);                         // [2 slots][b] final column norms (16-byte aligned)
+  __shared__ int flag[2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  auto col = [&](int bi, int sl, int k) { return buf + ((size_t)(bi * 2 + sl) * b + k) * rows; };
+  auto cid = [&](int bi, int sl, int k) -> int& { return ids[(bi * 2 + sl) * b + k]; };
+  const C tol2 = (C)(tol * tol);
+
+  // blocks start at their own positions: CTA c holds positions c and P-1-c
+  for (int sl = 0; sl < 2; ++sl) {
+    const int blk = sl == 0 ? rank : P - 1 - rank;
+    for (int k = 0; k < b; ++k) {
+      const int gid = blk * b + k;
+      if (threadIdx.x == 0) cid(0, sl, k) = gid < p ? gid : -1;
+      C* x = col(0, sl, k);
+      for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        C v = C(0);
+        if (gid < p) v = r < q ? Win[(size_t)gid * q + r] : ((r - q) == gid ? C(1) : C(0));
+        x[r] = v;
+      }
+    }
+  }
+  if (threadIdx.x < 2) flag[threadIdx.x] = 0;
+  cl.sync();
+
+  int cur = 0, sweep = 0;
+  bool done = false;
+  while (!done && sweep < max_sweeps) {
+    bool rot = false;
+    for (int sr = 0; sr < P - 1; ++sr) {
+      if (sr == 0) {  // pairs inside each block (round robin over the b columns of both slots)
+        const int B = b + (b & 1), half = B / 2;
+        for (int mr = 0; mr < B - 1; ++mr) {
+          for (int w = warp; w < 2 * half; w += nw) {
+            const int sl = w / half, k = w % half;
+            int i, j;
+            rr_pair(mr, k, B, i, j);
+            if (i < b && j < b && cid(cur, sl, i) >= 0 && cid(cur, sl, j) >= 0)
+              rot |= jacobi_pair<C>(col(cur, sl, i), col(cur, sl, j), q, rows, tol2);
+          }
+          __syncthreads();
+        }
+      }
+      for (int mr = 0; mr < b; ++mr) {  // pairs between the two blocks
+        for (int w = warp; w < b; w += nw) {
+          const int j = (w + mr) % b;
+          if (cid(cur, 0, w) >= 0 && cid(cur, 1, j) >= 0)
+            rot |= jacobi_pair<C>(col(cur, 0, w), col(cur, 1, j), q, rows, tol2);
+        }
+        __syncthreads();
+      }
+      // rotate the positions 1..P-1 by one (position 0 stays): pull the next two blocks
+      cl.sync();
+      const int nb = cur ^ 1;
+      for (int sl = 0; sl < 2; ++sl) {
+        const int x = sl == 0 ? rank : P - 1 - rank;
+        const int src = x == 0 ? 0 : (x == 1 ? P - 1 : x - 1);
+        const int scta = src < JC ? src : P - 1 - src, ssl = src < JC ? 0 : 1;
+        const C* rsrc = cl.map_shared_rank(col(cur, ssl, 0), scta);
+        const int* rid = cl.map_shared_rank(&cid(cur, ssl, 0), scta);
+        C* dst = col(nb, sl, 0);
+        for (long long e = threadIdx.x; e < (long long)b * rows; e += blockDim.x) dst[e] = rsrc[e];
+        if (threadIdx.x < b) cid(nb, sl, threadIdx.x) = rid[threadIdx.x];
+      }
+      cur = nb;
+      __syncthreads();
+    }
+    // the cluster-wide "any rotation" of this sweep decides, identically in every CTA
+    const int any = __syncthreads_or(rot ? 1 : 0);
+    int* f0 = cl.map_shared_rank(&flag[sweep & 1], 0);
+    if (any && threadIdx.x == 0) atomicOr(f0, 1);
+    cl.sync();
+    done = (*f0 == 0);
+    if (rank == 0 && threadIdx.x == 0) flag[(sweep + 1) & 1] = 0;  // next sweep's flag (last read a sweep ago)
+    ++sweep;
+    cl.sync();
+  }
+  if (!done && rank == 0 && threadIdx.x == 0 && errw) atomicOr(errw, ERRW_NOCONV);
+  if (rank == 0 && threadIdx.x == 0 && errw) atomicMax((int*)errw + 1, sweep);
+  // column norms, then every column's rank among all p (descending, ties by column index)
+  for (int w = warp; w < 2 * b; w += nw) {
+    const int sl = w / b, k = w % b;
+    const C* x = col(cur, sl, k);
+    C ss = 0;
+    for (int r = lane; r < q; r += 32) ss += x[r] * x[r];
+    ss = warp_sum(ss);
+    if (lane == 0) nrm[w] = cid(cur, sl, k) >= 0 ? sqrt(ss) : C(-1);
+  }
+  cl.sync();
+  for (int w = warp; w < 2 * b; w += nw) {
+    const int sl = w / b, k = w % b;
+    const int me = cid(cur, sl, k);
+    if (me < 0) continue;
+    const C v = nrm[w];
+    int rk = 0;
+    for (int c = 0; c < JC; ++c) {
+      const C* rn = cl.map_shared_rank(nrm, c);
+      const int* ri = cl.map_shared_rank(&cid(cur, 0, 0), c);
+      for (int t = lane; t < 2 * b; t += 32) {
+        const int o = ri[t];  // ids of slot 0 then slot 1 are contiguous
+        const C u = rn[t];
+        rk += (o >= 0) && (u > v || (u == v && o < me));
+      }
+    }
+    rk = warp_sum(rk);
+    const C* x = col(cur, sl, k);
+    const C inv = v > C(0) ? C(1) / v : C(0);
+    for (int r = lane; r < q; r += 32) Uo[(size_t)rk * q + r] = x[r] * inv;
+    if (want_v)
+      for (int r = lane; r < p; r += 32) Vo[(size_t)rk * p + r] = x[q + r];
+    if (lane == 0) So[rk] = v;
+  }
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+template <typename C>
+size_t jacobi_cluster_smem(int q, int p, bool want_v) {
+  const int b = (p + 2 * JC - 1) / (2 * JC);
+  const size_t rows = (size_t)q + (want_v ? p : 0);
+  return 4 * (size_t)b * rows * sizeof(C) + (4 * (size_t)b + 4) * sizeof(int) + 2 * (size_t)b * sizeof(C) + 16;
 }
 
 template <typename C, typename S>
@@ -309,7 +504,22 @@ cudaError_t jacobi_svd(int q, int p, S* W, S* U, S* Sv, S* V, S* Vwork, int max_
   // would keep rotating on noise
   const double eps = (sizeof(C) == 8) ? DBL_EPSILON : (double)FLT_EPSILON;
   const double tol = 4.0 * eps * sqrt((double)q);
-  const size_t need = ((size_t)q * p + (size_t)p * p) * sizeof(S);
+  // the cluster kernel spreads the columns over JC SMs when there are enough of them
+  if constexpr (std::is_same<C, S>::value) {
+    const size_t csm = jacobi_cluster_smem<C>(q, p, V != nullptr);
+    const int bc = (p + 2 * JC - 1) / (2 * JC), B = bc + (bc & 1);
+    if (p >= 32 && csm <= 200 * 1024 && 32 * B <= 1024) {
+      if (csm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(jacobi_cluster_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)csm);
+        if (e != cudaSuccess) return e;
+      }
+      ++tl_launches;
+      jacobi_cluster_kernel<C><<<JC, 32 * B, csm, st>>>(q, p, bc, W, max_sweeps, tol, errw, U, Sv, V);
+      return cudaGetLastError();
+    }
+  }
+  const size_t need = ((size_t)q * p + (V ? (size_t)p * p : 0)) * sizeof(S);
   const size_t cap = 200 * 1024;
   const int in_smem = need <= cap ? 1 : 0;
   const int pairs = (p + (p & 1)) / 2;
@@ -579,8 +789,10 @@ __global__ void fix_signs_kernel(int m, int n, F* __restrict__ U, int ld_u, F* _
   __syncthreads();
   if (sgn < 0.0) {
     for (int i = threadIdx.x; i < m; i += blockDim.x) u[i] = -u[i];
-    F* v = V + (size_t)blockIdx.x * ld_v;
-    for (int c = threadIdx.x; c < n; c += blockDim.x) v[c] = -v[c];
+    if (V) {  // V may be absent when only the left factor is wanted
+      F* v = V + (size_t)blockIdx.x * ld_v;
+      for (int c = threadIdx.x; c < n; c += blockDim.x) v[c] = -v[c];
+    }
   }
 }
 
