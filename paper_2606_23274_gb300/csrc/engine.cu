@@ -562,7 +562,7 @@ struct Chain {
 // S (p, sorted), V_M (n x p, ld n). Returns p (computed singular triplets).
 // ---------------------------------------------------------------------------
 template <typename T, typename F>
-int factorize(tt_fit* h, int m, int n, int sweep, int site1, int need = 3) {
+int factorize_body(tt_fit* h, int m, int n, int sweep, int site1, int need) {
   F *fX = (F*)W(h).fX, *fQ = (F*)W(h).fQ, *fR = (F*)W(h).fR, *fU = (F*)W(h).fU, *fV = (F*)W(h).fV, *fVw = (F*)W(h).fVw;
   F *fS = (F*)W(h).fS, *fUM = (F*)W(h).fUM, *fVM = (F*)W(h).fVM, *fOm = (F*)W(h).fOm, *MF = (F*)W(h).fY;
   F *fBt = (F*)W(h).fBt, *fQ2 = (F*)W(h).fQ2, *fR2 = (F*)W(h).fR2;
@@ -572,8 +572,11 @@ int factorize(tt_fit* h, int m, int n, int sweep, int site1, int need = 3) {
   auto jac = [&](int q, int p, F* Wm, F* U, F* S, F* V) {
     CK(jacobi_svd<F, F>(q, p, Wm, U, S, V, fVw, 60, W(h).errw, W(h).st));
   };
-  // Theta (T, row-major) -> F copy; norm (flags NaN/Inf)
-  copymap<T, F>(h, m, n, (const T*)W(h).Th, IdxMap::lin(n), IdxMap::lin(1), MF, IdxMap::lin(n), IdxMap::lin(1));
+  // Theta (T, row-major) -> F copy scaled by 2^-e (e: exponent of max |Theta|, in dk[1]) so that its
+  // squares stay inside the range of F; norm (flags NaN/Inf)
+  int* ex = W(h).dk + 1;
+  CK(absmax_exponent<T>((const T*)W(h).Th, (long long)m * n, ex, W(h).st));
+  CK(copy_pow2<T, F>((long long)m * n, (const T*)W(h).Th, MF, ex, W(h).st));
   CK(frob_norm<F>(MF, (long long)m * n, W(h).dnorm, W(h).errw, W(h).st));
   const int ks = h->chi_max + h->oversample;
   if (h->update == TT_UPDATE_2SITE_RSVD && ks < std::min(m, n)) {
@@ -653,6 +656,15 @@ int factorize(tt_fit* h, int m, int n, int sweep, int site1, int need = 3) {
     CK(cudaMemcpyAsync(fVM, Ufull, qb, cudaMemcpyDeviceToDevice, W(h).st));
   }
   CK(fix_signs<F>(m, n, p, fUM, m, fVM, n, W(h).st));
+  return p;
+}
+
+// The factorisation of Theta: that of 2^-e Theta, with the singular values and
+// ||Theta|| scaled back (the singular vectors do not change).
+template <typename T, typename F>
+int factorize(tt_fit* h, int m, int n, int sweep, int site1, int need = 3) {
+  const int p = factorize_body<T, F>(h, m, n, sweep, site1, need);
+  CK(unscale_pow2<F>(p, (F*)W(h).fS, W(h).dnorm, W(h).dk + 1, W(h).st));
   return p;
 }
 

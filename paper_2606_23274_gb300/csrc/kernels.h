@@ -96,6 +96,13 @@ cudaError_t scale_rows(int rows, int cols, const double* in, const double* y, T*
 
 // out (rows x cols, row-major) = in * diag(y) (y == nullptr: plain copy)
 cudaError_t scale_cols(int rows, int cols, const double* in, const double* y, double* out, cudaStream_t st);
+// 2^-e scaling around a lower-precision factorisation (e = exponent of max |x|, device int)
+template <typename T>
+cudaError_t absmax_exponent(const T* x, long long n, int* e, cudaStream_t st);
+template <typename Tin, typename Tout>
+cudaError_t copy_pow2(long long n, const Tin* in, Tout* out, const int* e, cudaStream_t st);
+template <typename F>
+cudaError_t unscale_pow2(int p, F* s, double* nrm, const int* e, cudaStream_t st);
 // out (cols x rows) = (in diag(y))^T in type T
 template <typename T>
 cudaError_t scale_cols_t(int rows, int cols, const double* in, const double* y, T* out, cudaStream_t st);

@@ -9,6 +9,8 @@
 #include "common.cuh"
 #include "kernels.h"
 
+namespace cg = cooperative_groups;
+
 namespace ttfit {
 
 template <typename C>
@@ -129,10 +131,157 @@ __global__ void __launch_bounds__(1024) qr_house_kernel(int q, int p, S* __restr
   }
 }
 
+// ---------------------------------------------------------------------------
+// Householder QR on a thread-block cluster of JQ CTAs: CTA k holds rows
+// [k rb, (k+1) rb) of X and of Q in shared memory, so the matrix never leaves
+// the SMs. Step j: the CTAs exchange their partial |x_j|^2 and the pivot
+// (all-to-all through distributed shared memory, cluster barrier), each forms
+// the same reflector, exchanges its partial dot products v^T X (second
+// barrier) and updates its own rows. Q = H_0 ... H_{r-1} [I; 0] is then formed
+// backwards with one exchange per reflector (buffers alternate by step parity,
+// so a CTA that runs ahead never overwrites sums another one still reads).
+// Same contract and sign convention (diag R >= 0) as qr_house_kernel.
+// ---------------------------------------------------------------------------
+constexpr int JQ = 8;
+
+template <typename C>
+__global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
+    qr_cluster_kernel(int q, int p, const C* __restrict__ Xg, C* __restrict__ Qg, C* __restrict__ Rg) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int k = (int)cl.block_rank();
+  const int r = min(q, p);
+  const int rb = (q + JQ - 1) / JQ;
+  const int r0 = k * rb, nr = max(0, min(rb, q - r0));  // my rows: r0 .. r0 + nr - 1
+  extern __shared__ __align__(16) unsigned char qcs[];
+  C* X = (C*)qcs;                          // [p][rb] my rows of X, column-major
+  C* Qm = X + (size_t)p * rb;              // [r][rb] my rows of Q, column-major
+  C* xw = Qm + (size_t)r * rb;             // [2][JQ][p] exchanged partial dot products
+  C* xs = xw + 2 * (size_t)JQ * p;         // [JQ] partial squared norms
+  C* diag = xs + JQ;                       // [r] alpha of every reflector
+  C* x0s = diag + r;                       // [1] pivot of the current step
+  __shared__ C red[32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (long long e = threadIdx.x; e < (long long)p * rb; e += blockDim.x) {
+    const int i = (int)(e % rb), c = (int)(e / rb);
+    X[e] = i < nr ? Xg[(size_t)c * q + r0 + i] : C(0);
+  }
+  cl.sync();
+  for (int j = 0; j < r; ++j) {
+    C* xj = X + (size_t)j * rb;
+    // (a) partial |x_j[j:]|^2 and the pivot x_jj, to every CTA
+    C ss = 0;
+    for (int i = threadIdx.x; i < nr; i += blockDim.x)
+      if (r0 + i >= j) ss += xj[i] * xj[i];
+    ss = block_sum(ss, red);
+    if (threadIdx.x < JQ) {
+      C* dst = cl.map_shared_rank(xs, (unsigned)threadIdx.x);
+      dst[k] = ss;
+      if (j >= r0 && j < r0 + nr) *cl.map_shared_rank(x0s, (unsigned)threadIdx.x) = xj[j - r0];
+    }
+    cl.sync();
+    C tot = 0;
+    for (int t = 0; t < JQ; ++t) tot += xs[t];
+    const C x0 = *x0s;
+    const C nrm = sqrt(tot);
+    const C alpha = (x0 >= C(0)) ? -nrm : nrm;
+    const C v0 = x0 - alpha;
+    const C vn2 = tot - x0 * x0 + v0 * v0;
+    const bool zero = !(vn2 > C(0));
+    const C inv = zero ? C(0) : C(1) / sqrt(vn2);
+    if (threadIdx.x == 0) diag[j] = zero ? C(0) : alpha;
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+      const int gi = r0 + i;
+      if (gi >= j) xj[i] = (gi == j ? v0 : xj[i]) * inv;  // the reflector v (unit norm) below the diagonal
+    }
+    __syncthreads();
+    // (b) partial w_c = v^T x_c for c > j, to every CTA
+    C* wbuf = xw + (size_t)(j & 1) * JQ * p;
+    for (int c = j + 1 + warp; c < p; c += nw) {
+      const C* xc = X + (size_t)c * rb;
+      C d = 0;
+      for (int i = lane; i < nr; i += 32)
+        if (r0 + i >= j) d += xj[i] * xc[i];
+      d = warp_sum(d);
+      if (lane < JQ) cl.map_shared_rank(wbuf, (unsigned)lane)[k * p + c] = d;
+    }
+    cl.sync();
+    // (c) x_c -= 2 v w_c on my rows
+    if (!zero)
+      for (long long e = threadIdx.x; e < (long long)(p - j - 1) * nr; e += blockDim.x) {
+        const int i = (int)(e % nr), c = j + 1 + (int)(e / nr);
+        if (r0 + i < j) continue;
+        C w = 0;
+        for (int t = 0; t < JQ; ++t) w += wbuf[t * p + c];
+        X[(size_t)c * rb + i] -= C(2) * xj[i] * w;
+      }
+    __syncthreads();
+  }
+  // Q = H_0 ... H_{r-1} [I_r; 0], my rows
+  for (long long e = threadIdx.x; e < (long long)r * rb; e += blockDim.x) {
+    const int i = (int)(e % rb), c = (int)(e / rb);
+    Qm[e] = (r0 + i == c) ? C(1) : C(0);
+  }
+  cl.sync();  // every CTA has read the last step's sums before the buffers are reused below
+  for (int j = r - 1; j >= 0; --j) {
+    const C* vj = X + (size_t)j * rb;
+    C* tbuf = xw + (size_t)(j & 1) * JQ * p;
+    for (int c = j + warp; c < r; c += nw) {
+      const C* qc = Qm + (size_t)c * rb;
+      C d = 0;
+      for (int i = lane; i < nr; i += 32)
+        if (r0 + i >= j) d += vj[i] * qc[i];
+      d = warp_sum(d);
+      if (lane < JQ) cl.map_shared_rank(tbuf, (unsigned)lane)[k * p + c] = d;
+    }
+    cl.sync();
+    if (diag[j] != C(0))
+      for (long long e = threadIdx.x; e < (long long)(r - j) * nr; e += blockDim.x) {
+        const int i = (int)(e % nr), c = j + (int)(e / nr);
+        if (r0 + i < j) continue;
+        C t = 0;
+        for (int u = 0; u < JQ; ++u) t += tbuf[u * p + c];
+        Qm[(size_t)c * rb + i] -= C(2) * vj[i] * t;
+      }
+    __syncthreads();
+  }
+  // outputs with diag(R) >= 0: row i of R and column i of Q change sign where alpha_i < 0
+  for (long long e = threadIdx.x; e < (long long)r * nr; e += blockDim.x) {
+    const int i = (int)(e % nr), c = (int)(e / nr);
+    Qg[(size_t)c * q + r0 + i] = diag[c] < C(0) ? -Qm[(size_t)c * rb + i] : Qm[(size_t)c * rb + i];
+  }
+  for (long long e = threadIdx.x; e < (long long)p * nr; e += blockDim.x) {
+    const int i = (int)(e % nr), c = (int)(e / nr);
+    const int gi = r0 + i;
+    if (gi >= r) continue;
+    const C val = gi < c ? X[(size_t)c * rb + i] : (gi == c ? diag[gi] : C(0));
+    Rg[(size_t)c * r + gi] = diag[gi] < C(0) ? -val : val;
+  }
+  cl.sync();  // no CTA leaves while another may still write into its shared memory
+}
+
+template <typename C>
+size_t qr_cluster_smem(int q, int p) {
+  const size_t rb = (q + JQ - 1) / JQ, r = std::min(q, p);
+  return ((size_t)p * rb + r * rb + 2 * (size_t)JQ * p + JQ + r + 1) * sizeof(C) + 16;
+}
+
 template <typename C, typename S>
 cudaError_t qr_householder(int q, int p, S* X, S* Q, S* R, cudaStream_t st) {
   if (q <= 0 || p <= 0) return cudaSuccess;
   if (min(q, p) > 1024 || q > 1024) return cudaErrorInvalidValue;
+  if constexpr (std::is_same<C, S>::value) {  // rows spread over a cluster when the matrix is large enough
+    const size_t csm = qr_cluster_smem<C>(q, p);
+    if (q >= 128 && p >= 16 && csm <= 200 * 1024) {
+      if (csm > 48 * 1024) {
+        cudaError_t e =
+            cudaFuncSetAttribute(qr_cluster_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+        if (e != cudaSuccess) return e;
+      }
+      ++tl_launches;
+      qr_cluster_kernel<C><<<JQ, 256, csm, st>>>(q, p, X, Q, R);
+      return cudaGetLastError();
+    }
+  }
   ++tl_launches;
   if (q <= 128) qr_house_kernel<C, S, 4><<<1, 1024, 0, st>>>(q, p, X, Q, R);
   else if (q <= 256) qr_house_kernel<C, S, 8><<<1, 1024, 0, st>>>(q, p, X, Q, R);
@@ -334,7 +483,6 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int q, int p, S* __restric
 // jacobi_kernel. All CTAs run the same number of barriers (the stop decision is
 // a cluster-wide OR read by all), so no barrier waits on a CTA that has left.
 // ---------------------------------------------------------------------------
-namespace cg = cooperative_groups;
 constexpr int JC = 8;  // CTAs per cluster (portable size)
 
 template <typename C>
@@ -910,4 +1058,95 @@ cudaError_t scale_cols_t(int rows, int cols, const double* in, const double* y, 
 template cudaError_t scale_cols_t<float>(int, int, const double*, const double*, float*, cudaStream_t);
 template cudaError_t scale_cols_t<double>(int, int, const double*, const double*, double*, cudaStream_t);
 template cudaError_t scale_cols_t<df32>(int, int, const double*, const double*, df32*, cudaStream_t);
+}  // namespace ttfit
+
+// ---------------------------------------------------------------------------
+// Power-of-two scaling around a lower-precision factorisation. The two-site
+// tensor of an early window can be tiny (a random guess overlaps A B by ~1e-15
+// on a long chain); its squares underflow FP32 inside the Gram sums. Scaling by
+// 2^-e (e the exponent of max |x|) is exact, leaves the singular vectors and
+// every relative rule unchanged, and is undone on the singular values.
+namespace ttfit {
+template <typename T>
+__device__ __forceinline__ double abs_as_double(T x) {
+  return fabs((double)x);
+}
+template <typename T>
+__global__ void __launch_bounds__(1024) absmax_exponent_kernel(const T* __restrict__ x, long long n, int* e) {
+  __shared__ double red[32];
+  double m = 0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    const double a = abs_as_double(x[i]);
+    m = (a > m) ? a : m;  // NaN is caught by the norm check of the factorisation
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, red[w]);
+    int ex = 0;
+    if (t > 0 && isfinite(t)) frexp(t, &ex);  // t = f 2^ex, f in [0.5, 1)
+    *e = ex;
+  }
+}
+template <typename T>
+cudaError_t absmax_exponent(const T* x, long long n, int* e, cudaStream_t st) {
+  ++tl_launches;
+  absmax_exponent_kernel<T><<<1, 1024, 0, st>>>(x, n, e);
+  return cudaGetLastError();
+}
+template cudaError_t absmax_exponent<double>(const double*, long long, int*, cudaStream_t);
+template cudaError_t absmax_exponent<float>(const float*, long long, int*, cudaStream_t);
+template cudaError_t absmax_exponent<df32>(const df32*, long long, int*, cudaStream_t);
+
+template <typename Tout, typename Tin>
+__device__ __forceinline__ Tout scale_pow2(Tin x, int s);
+template <>
+__device__ __forceinline__ float scale_pow2<float, float>(float x, int s) { return scalbnf(x, s); }
+template <>
+__device__ __forceinline__ float scale_pow2<float, double>(double x, int s) { return (float)scalbn(x, s); }
+template <>
+__device__ __forceinline__ float scale_pow2<float, df32>(df32 x, int s) { return scalbnf(x.hi, s) + scalbnf(x.lo, s); }
+template <>
+__device__ __forceinline__ double scale_pow2<double, double>(double x, int s) { return scalbn(x, s); }
+template <>
+__device__ __forceinline__ double scale_pow2<double, df32>(df32 x, int s) { return scalbn((double)x, s); }
+
+template <typename Tin, typename Tout>
+__global__ void copy_pow2_kernel(long long n, const Tin* __restrict__ in, Tout* __restrict__ out, const int* e) {
+  const int s = -*e;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = scale_pow2<Tout, Tin>(in[i], s);
+}
+template <typename Tin, typename Tout>
+cudaError_t copy_pow2(long long n, const Tin* in, Tout* out, const int* e, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 4096);
+  ++tl_launches;
+  copy_pow2_kernel<Tin, Tout><<<blocks, 256, 0, st>>>(n, in, out, e);
+  return cudaGetLastError();
+}
+template cudaError_t copy_pow2<double, double>(long long, const double*, double*, const int*, cudaStream_t);
+template cudaError_t copy_pow2<double, float>(long long, const double*, float*, const int*, cudaStream_t);
+template cudaError_t copy_pow2<float, float>(long long, const float*, float*, const int*, cudaStream_t);
+template cudaError_t copy_pow2<df32, float>(long long, const df32*, float*, const int*, cudaStream_t);
+template cudaError_t copy_pow2<df32, double>(long long, const df32*, double*, const int*, cudaStream_t);
+
+// s_i <- s_i 2^e and ||M|| <- ||M|| 2^e: the factorisation of 2^-e M back to M
+template <typename F>
+__global__ void unscale_pow2_kernel(int p, F* s, double* nrm, const int* e) {
+  const int ex = *e;
+  for (int i = threadIdx.x; i < p; i += blockDim.x) s[i] = (F)scalbn((double)s[i], ex);
+  if (threadIdx.x == 0) *nrm = scalbn(*nrm, ex);
+}
+template <typename F>
+cudaError_t unscale_pow2(int p, F* s, double* nrm, const int* e, cudaStream_t st) {
+  ++tl_launches;
+  unscale_pow2_kernel<F><<<1, 256, 0, st>>>(p, s, nrm, e);
+  return cudaGetLastError();
+}
+template cudaError_t unscale_pow2<float>(int, float*, double*, const int*, cudaStream_t);
+template cudaError_t unscale_pow2<double>(int, double*, double*, const int*, cudaStream_t);
 }  // namespace ttfit

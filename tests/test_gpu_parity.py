@@ -319,3 +319,25 @@ def test_switch_tf32x3_to_df32_and_cutoff_follows_precision():
     assert h.bonds() == o.bonds()
     assert _rel([c.cpu().numpy() for c in h.result()], o.result()) <= 1e-8
     h.destroy()
+
+
+@pytest.mark.parametrize("precision,fast", [("fp64", True), ("df32", True), ("tf32x3", False), ("fp32", False)])
+def test_fp32_factorisation_of_a_tiny_first_window(precision, fast):
+    """From a random guess on a long chain the two-site tensors of the first
+    sweep are tiny (the guess overlaps A B by ~1e-15): their squares underflow
+    FP32 unless the factorisation works on 2^-e Theta. Every precision's first
+    sweep must give the FP64 path's ||C||^2 (to its own accuracy), and C must be
+    the fitted operator (its norm equals the reported one)."""
+    A = kron_sum_mpo(30, 16, 0, 0)
+    B = kron_sum_mpo(30, 16, 0, 1)
+    ref = ttfit.tt_fit_create(A, B, 16, 0.0, "site", precision="fp64", conv_tol=0.0, sv_cutoff=1e-13)
+    r0 = ref.sweep(1)
+    ref.destroy()
+    f = ttfit.tt_fit_create(A, B, 16, 0.0, "site", precision=precision, fast_factor=fast, conv_tol=0.0,
+                            sv_cutoff=1e-13)
+    r = f.sweep(1)
+    C = [c.cpu().numpy() for c in f.result()]
+    f.destroy()
+    tol = 1e-3 if precision in ("tf32x3", "fp32") else 1e-6
+    assert abs(r["norm2_C"] - r0["norm2_C"]) <= tol * r0["norm2_C"]
+    assert abs(mpo_norm(C) ** 2 - r["norm2_C"]) <= 10 * tol * r["norm2_C"]
