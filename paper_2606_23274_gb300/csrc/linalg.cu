@@ -5,6 +5,7 @@
 #include <cooperative_groups.h>
 #include <algorithm>
 #include <cfloat>
+#include <climits>
 #include <type_traits>
 #include "common.cuh"
 #include "kernels.h"
@@ -151,27 +152,28 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
   const int k = (int)cl.block_rank();
   const int r = min(q, p);
   const int rb = (q + JQ - 1) / JQ;
+  const int ld = rb | 1;  // odd column stride: threads reading one row of consecutive columns hit distinct banks
   const int r0 = k * rb, nr = max(0, min(rb, q - r0));  // my rows: r0 .. r0 + nr - 1
   extern __shared__ __align__(16) unsigned char qcs[];
-  C* X = (C*)qcs;                          // [p][rb] my rows of X, column-major
-  C* Qm = X + (size_t)p * rb;              // [r][rb] my rows of Q, column-major
-  C* xw = Qm + (size_t)r * rb;             // [2][JQ][p] exchanged partial dot products
-  C* xs = xw + 2 * (size_t)JQ * p;         // [JQ] partial squared norms
+  C* X = (C*)qcs;                          // [p][ld] my rows of X, column-major
+  C* Qm = X + (size_t)p * ld;              // [r][ld] my rows of Q, column-major
+  C* xw = Qm + (size_t)r * ld;             // [2][JQ][p] exchanged partial dot products
+  C* wsum = xw + 2 * (size_t)JQ * p;       // [p] summed dot products of the current step
+  C* xs = wsum + p;                        // [JQ] partial squared norms
   C* diag = xs + JQ;                       // [r] alpha of every reflector
   C* x0s = diag + r;                       // [1] pivot of the current step
   __shared__ C red[32];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (long long e = threadIdx.x; e < (long long)p * rb; e += blockDim.x) {
     const int i = (int)(e % rb), c = (int)(e / rb);
-    X[e] = i < nr ? Xg[(size_t)c * q + r0 + i] : C(0);
+    X[(size_t)c * ld + i] = i < nr ? Xg[(size_t)c * q + r0 + i] : C(0);
   }
   cl.sync();
   for (int j = 0; j < r; ++j) {
-    C* xj = X + (size_t)j * rb;
+    C* xj = X + (size_t)j * ld;
+    const int i0 = max(0, min(nr, j - r0));  // my first row at or below the diagonal
     // (a) partial |x_j[j:]|^2 and the pivot x_jj, to every CTA
     C ss = 0;
-    for (int i = threadIdx.x; i < nr; i += blockDim.x)
-      if (r0 + i >= j) ss += xj[i] * xj[i];
+    for (int i = i0 + (int)threadIdx.x; i < nr; i += blockDim.x) ss += xj[i] * xj[i];
     ss = block_sum(ss, red);
     if (threadIdx.x < JQ) {
       C* dst = cl.map_shared_rank(xs, (unsigned)threadIdx.x);
@@ -189,71 +191,74 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
     const bool zero = !(vn2 > C(0));
     const C inv = zero ? C(0) : C(1) / sqrt(vn2);
     if (threadIdx.x == 0) diag[j] = zero ? C(0) : alpha;
-    for (int i = threadIdx.x; i < nr; i += blockDim.x) {
-      const int gi = r0 + i;
-      if (gi >= j) xj[i] = (gi == j ? v0 : xj[i]) * inv;  // the reflector v (unit norm) below the diagonal
-    }
+    for (int i = i0 + (int)threadIdx.x; i < nr; i += blockDim.x)
+      xj[i] = (r0 + i == j ? v0 : xj[i]) * inv;  // the reflector v (unit norm) below the diagonal
     __syncthreads();
-    // (b) partial w_c = v^T x_c for c > j, to every CTA
+    // (b) partial w_c = v^T x_c for c > j (one thread per column), to every CTA
     C* wbuf = xw + (size_t)(j & 1) * JQ * p;
-    for (int c = j + 1 + warp; c < p; c += nw) {
-      const C* xc = X + (size_t)c * rb;
+    for (int c = j + 1 + (int)threadIdx.x; c < p; c += blockDim.x) {
+      const C* xc = X + (size_t)c * ld;
       C d = 0;
-      for (int i = lane; i < nr; i += 32)
-        if (r0 + i >= j) d += xj[i] * xc[i];
-      d = warp_sum(d);
-      if (lane < JQ) cl.map_shared_rank(wbuf, (unsigned)lane)[k * p + c] = d;
+      for (int i = i0; i < nr; ++i) d += xj[i] * xc[i];
+#pragma unroll
+      for (int t = 0; t < JQ; ++t) cl.map_shared_rank(wbuf, (unsigned)t)[k * p + c] = d;
     }
     cl.sync();
     // (c) x_c -= 2 v w_c on my rows
-    if (!zero)
-      for (long long e = threadIdx.x; e < (long long)(p - j - 1) * nr; e += blockDim.x) {
-        const int i = (int)(e % nr), c = j + 1 + (int)(e / nr);
-        if (r0 + i < j) continue;
-        C w = 0;
-        for (int t = 0; t < JQ; ++t) w += wbuf[t * p + c];
-        X[(size_t)c * rb + i] -= C(2) * xj[i] * w;
+    for (int c = j + 1 + (int)threadIdx.x; c < p; c += blockDim.x) {
+      C w = 0;
+      for (int t = 0; t < JQ; ++t) w += wbuf[t * p + c];
+      wsum[c] = C(2) * w;
+    }
+    __syncthreads();
+    if (!zero && nr > i0)
+      for (long long e = threadIdx.x; e < (long long)(p - j - 1) * (nr - i0); e += blockDim.x) {
+        const int i = i0 + (int)(e % (nr - i0)), c = j + 1 + (int)(e / (nr - i0));
+        X[(size_t)c * ld + i] -= xj[i] * wsum[c];
       }
     __syncthreads();
   }
   // Q = H_0 ... H_{r-1} [I_r; 0], my rows
   for (long long e = threadIdx.x; e < (long long)r * rb; e += blockDim.x) {
     const int i = (int)(e % rb), c = (int)(e / rb);
-    Qm[e] = (r0 + i == c) ? C(1) : C(0);
+    Qm[(size_t)c * ld + i] = (r0 + i == c) ? C(1) : C(0);
   }
   cl.sync();  // every CTA has read the last step's sums before the buffers are reused below
   for (int j = r - 1; j >= 0; --j) {
-    const C* vj = X + (size_t)j * rb;
+    const C* vj = X + (size_t)j * ld;
+    const int i0 = max(0, min(nr, j - r0));
     C* tbuf = xw + (size_t)(j & 1) * JQ * p;
-    for (int c = j + warp; c < r; c += nw) {
-      const C* qc = Qm + (size_t)c * rb;
+    for (int c = j + (int)threadIdx.x; c < r; c += blockDim.x) {
+      const C* qc = Qm + (size_t)c * ld;
       C d = 0;
-      for (int i = lane; i < nr; i += 32)
-        if (r0 + i >= j) d += vj[i] * qc[i];
-      d = warp_sum(d);
-      if (lane < JQ) cl.map_shared_rank(tbuf, (unsigned)lane)[k * p + c] = d;
+      for (int i = i0; i < nr; ++i) d += vj[i] * qc[i];
+#pragma unroll
+      for (int t = 0; t < JQ; ++t) cl.map_shared_rank(tbuf, (unsigned)t)[k * p + c] = d;
     }
     cl.sync();
-    if (diag[j] != C(0))
-      for (long long e = threadIdx.x; e < (long long)(r - j) * nr; e += blockDim.x) {
-        const int i = (int)(e % nr), c = j + (int)(e / nr);
-        if (r0 + i < j) continue;
-        C t = 0;
-        for (int u = 0; u < JQ; ++u) t += tbuf[u * p + c];
-        Qm[(size_t)c * rb + i] -= C(2) * vj[i] * t;
+    for (int c = j + (int)threadIdx.x; c < r; c += blockDim.x) {
+      C t = 0;
+      for (int u = 0; u < JQ; ++u) t += tbuf[u * p + c];
+      wsum[c] = C(2) * t;
+    }
+    __syncthreads();
+    if (diag[j] != C(0) && nr > i0)
+      for (long long e = threadIdx.x; e < (long long)(r - j) * (nr - i0); e += blockDim.x) {
+        const int i = i0 + (int)(e % (nr - i0)), c = j + (int)(e / (nr - i0));
+        Qm[(size_t)c * ld + i] -= vj[i] * wsum[c];
       }
     __syncthreads();
   }
   // outputs with diag(R) >= 0: row i of R and column i of Q change sign where alpha_i < 0
   for (long long e = threadIdx.x; e < (long long)r * nr; e += blockDim.x) {
     const int i = (int)(e % nr), c = (int)(e / nr);
-    Qg[(size_t)c * q + r0 + i] = diag[c] < C(0) ? -Qm[(size_t)c * rb + i] : Qm[(size_t)c * rb + i];
+    Qg[(size_t)c * q + r0 + i] = diag[c] < C(0) ? -Qm[(size_t)c * ld + i] : Qm[(size_t)c * ld + i];
   }
   for (long long e = threadIdx.x; e < (long long)p * nr; e += blockDim.x) {
     const int i = (int)(e % nr), c = (int)(e / nr);
     const int gi = r0 + i;
     if (gi >= r) continue;
-    const C val = gi < c ? X[(size_t)c * rb + i] : (gi == c ? diag[gi] : C(0));
+    const C val = gi < c ? X[(size_t)c * ld + i] : (gi == c ? diag[gi] : C(0));
     Rg[(size_t)c * r + gi] = diag[gi] < C(0) ? -val : val;
   }
   cl.sync();  // no CTA leaves while another may still write into its shared memory
@@ -261,8 +266,8 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
 
 template <typename C>
 size_t qr_cluster_smem(int q, int p) {
-  const size_t rb = (q + JQ - 1) / JQ, r = std::min(q, p);
-  return ((size_t)p * rb + r * rb + 2 * (size_t)JQ * p + JQ + r + 1) * sizeof(C) + 16;
+  const size_t rb = (q + JQ - 1) / JQ, ld = rb | 1, r = std::min(q, p);
+  return ((size_t)p * ld + r * ld + 2 * (size_t)JQ * p + p + JQ + r + 1) * sizeof(C) + 16;
 }
 
 template <typename C, typename S>
@@ -1067,34 +1072,46 @@ template cudaError_t scale_cols_t<df32>(int, int, const double*, const double*, 
 // 2^-e (e the exponent of max |x|) is exact, leaves the singular vectors and
 // every relative rule unchanged, and is undone on the singular values.
 namespace ttfit {
-template <typename T>
-__device__ __forceinline__ double abs_as_double(T x) {
-  return fabs((double)x);
+// frexp exponent of |x| (x = f 2^e, f in [0.5, 1)) from the IEEE bits, integer ops only
+__device__ __forceinline__ int exp_of(float x) {
+  const int E = (__float_as_int(x) >> 23) & 0xFF;
+  return E == 0xFF ? INT_MIN : E - 126;  // Inf / NaN: ignored here (the norm check flags them)
 }
+__device__ __forceinline__ int exp_of(double x) {
+  const int E = (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+  return E == 0x7FF ? INT_MIN : E - 1022;
+}
+__device__ __forceinline__ int exp_of(df32 x) { return exp_of(x.hi); }
 template <typename T>
-__global__ void __launch_bounds__(1024) absmax_exponent_kernel(const T* __restrict__ x, long long n, int* e) {
-  __shared__ double red[32];
-  double m = 0;
-  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-    const double a = abs_as_double(x[i]);
-    m = (a > m) ? a : m;  // NaN is caught by the norm check of the factorisation
-  }
+__device__ __forceinline__ bool is_zero(T x) {
+  return x == T(0);
+}
+template <>
+__device__ __forceinline__ bool is_zero<df32>(df32 x) {
+  return x.hi == 0.f;
+}
+
+// e = max over nonzero x of the exponent of x (left untouched when every x is 0); e must
+// be preset to a very negative value
+template <typename T>
+__global__ void absmax_exponent_kernel(const T* __restrict__ x, long long n, int* e) {
+  int m = INT_MIN;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    if (!is_zero(x[i])) m = max(m, exp_of(x[i]));
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, red[w]);
-    int ex = 0;
-    if (t > 0 && isfinite(t)) frexp(t, &ex);  // t = f 2^ex, f in [0.5, 1)
-    *e = ex;
-  }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m != INT_MIN) atomicMax(e, m);
 }
 template <typename T>
 cudaError_t absmax_exponent(const T* x, long long n, int* e, cudaStream_t st) {
+  // preset: every byte 0x80, i.e. -2139062144; an all-zero input keeps it, and scaling by
+  // 2^(-e) of zeros is still zero
+  cudaError_t err = cudaMemsetAsync(e, 0x80, sizeof(int), st);
+  if (err != cudaSuccess) return err;
+  if (n <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 152);
   ++tl_launches;
-  absmax_exponent_kernel<T><<<1, 1024, 0, st>>>(x, n, e);
+  absmax_exponent_kernel<T><<<blocks, 256, 0, st>>>(x, n, e);
   return cudaGetLastError();
 }
 template cudaError_t absmax_exponent<double>(const double*, long long, int*, cudaStream_t);
