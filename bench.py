@@ -8,8 +8,8 @@ Gaussian-sketch randomized update (oversampling 10) until the relative change
 of ||C||^2 between sweeps is <= 1e-8. A step is one complete fit: input
 preparation, initial guess and right environments, sweeps until converged, and
 the export of C. The default precision schedule runs cheap sweeps first and
-exact ones last: 3xTF32 tensor-core contractions with the FP32 factorisation
-until the change of ||C||^2 falls below 1e-4, then FP64-class double-FP32
+exact ones last: one sweep of 3xTF32 tensor-core contractions with the FP32
+factorisation, then FP64-class double-FP32
 contractions (on the FP32 pipes) with the FP64-polished factorisation to
 convergence. Metric: time-to-tol in seconds
 (lower is better), reported with the local-update TFLOP/s and a roofline entry
@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 METRIC = "MPO-MPO fit time-to-tol (s) & local-update TFLOP/s vs peak, L=30 χ=128"
 WORKLOAD = "kron_L30_chi128"
 L_SITES, CHI, OVERSAMPLE, TOL, MAX_SWEEPS = 30, 128, 10, 1e-8, 14
-SWITCH_DELTA = 1e-4
+LO_SWEEPS = 1  # default: cheap sweeps before the FP64-class ones
 
 
 def parse():
@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--impl", default="native", choices=["native", "reference"])
     p.add_argument("--precision", default=os.environ.get("TTFIT_BENCH_PRECISION", "tf32x3>df32"),
                    help='a precision ("fp64", "df32", "fp32", "tf32x3", ...) or a schedule "lo>hi"')
+    p.add_argument("--lo-sweeps", type=int, default=LO_SWEEPS,
+                   help="sweeps (>= 1) in the cheap precision of a 'lo>hi' schedule before the switch")
     p.add_argument("--workload", default=WORKLOAD,
                    help="synthetic workload (default: the timed one); smaller ones serve profiling captures")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -113,12 +115,11 @@ FMA_LANES = {"f64": 2, "f32": 128}
 DF32_INSTR = 15  # FP32 instructions of one double-FP32 multiply-add (csrc/common.cuh, madd)
 
 
-def run_fit(ttfit, Ain, Bin, schedule, seed, dev, stream, chi=CHI):
+def run_fit(ttfit, Ain, Bin, schedule, seed, dev, stream, chi=CHI, lo_sweeps=LO_SWEEPS):
     """One complete fit. ``schedule`` is a precision name ("fp64", "df32", "tf32x3", ...) for a
     single-precision fit, or "lo>hi", e.g. "tf32x3>df32": sweeps in ``lo`` (FP32-factorised
-    randomized update) until the relative change of ||C||^2 is below SWITCH_DELTA after an even
-    number of sweeps, then FP64-class contractions in ``hi`` with the FP64-polished FP32
-    factorisation until converged."""
+    randomized update) for ``lo_sweeps`` sweeps, then FP64-class contractions in ``hi`` with the
+    FP64-polished FP32 factorisation until converged."""
     lo, hi = (schedule.split(">") + [None])[:2]
     f = ttfit.tt_fit_create(Ain, Bin, chi, TOL, "site", update="rsvd", oversample=OVERSAMPLE, seed=seed,
                             precision=lo, device=dev, stream=stream)
@@ -136,7 +137,7 @@ def run_fit(ttfit, Ain, Bin, schedule, seed, dev, stream, chi=CHI):
             phases[cur][k] += st[k]
         if rep["converged"] and (hi is None or cur == hi):
             break
-        if hi is not None and cur == lo and sweeps % 2 == 0 and rep["delta"] < SWITCH_DELTA:
+        if hi is not None and cur == lo and sweeps >= lo_sweeps:
             f.set_precision(hi, fast_factor=True)
             cur = hi
             phases[hi] = {k: 0.0 for k in STAGES}
@@ -180,7 +181,7 @@ def native(args):
         torch.cuda.synchronize()
 
     for _ in range(args.warmup):
-        run_fit(ttfit, Ad, Bd, args.precision, rank, dev, stream, chi)
+        run_fit(ttfit, Ad, Bd, args.precision, rank, dev, stream, chi, args.lo_sweeps)
         flush.zero_()
     barrier()
     clocks = ClockSampler(local)
@@ -192,7 +193,7 @@ def native(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        res = run_fit(ttfit, Ad, Bd, args.precision, rank, dev, stream, chi)
+        res = run_fit(ttfit, Ad, Bd, args.precision, rank, dev, stream, chi, args.lo_sweeps)
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
@@ -216,7 +217,7 @@ def native(args):
             t0 = time.perf_counter()
             Ain = [a.to(dev, non_blocking=True) for a in Ah]
             Bin = [b.to(dev, non_blocking=True) for b in Bh]
-            _, _, _, _, C, _ = run_fit(ttfit, Ain, Bin, args.precision, rank, dev, stream, chi)
+            _, _, _, _, C, _ = run_fit(ttfit, Ain, Bin, args.precision, rank, dev, stream, chi, args.lo_sweeps)
             Ch = [c.to("cpu") for c in C]
             torch.cuda.synchronize()
             et.append(time.perf_counter() - t0)
@@ -282,7 +283,7 @@ def native(args):
         "config": {"workload": (f"{WORKLOAD}: L=30, d=2x2, K=128 Kronecker terms (w=0.8^k), chi_A=chi_B=128, "
                                f"chi_C=128, randomized update k=chi_C+{OVERSAMPLE}, conv tol {TOL:g} on the "
                                f"relative change of ||C||^2, max {MAX_SWEEPS} sweeps, site gauge") if args.workload == WORKLOAD else args.workload,
-                   "schedule": args.precision, "parallelism": f"replicas x{world} (independent MPO pairs)",
+                   "schedule": args.precision + (f" ({args.lo_sweeps} cheap sweeps)" if ">" in args.precision else ""), "parallelism": f"replicas x{world} (independent MPO pairs)",
                    "l2": "flushed between timed steps (256 MB write)"},
         "sweeps_to_tol": sweeps, "sweeps_per_phase": phase_sweeps, "converged": bool(rep["converged"]),
         "final_delta": rep["delta"], "norm2_C": rep["norm2_C"],

@@ -170,10 +170,11 @@ tt_status tt_fit_sweep(tt_fit* h, int n_sweeps, tt_sweep_report* rep);
 
 /* Change the contraction precision for the following sweeps (the paper's
  * "cheap sweeps first, exact sweeps last", Sec. 5.3): the chain buffers are
- * rebuilt in the new arithmetic and R_L..R_3 recomputed from the current C.
- * Allowed only when the next sweep is a forward one (after create or after a
- * backward sweep), i.e. while C is right-canonical; otherwise TT_ERR_STATE
- * (the handle stays usable). fast_factor as in tt_fit_options. Resets the
+ * rebuilt in the new arithmetic, and the environments the next sweep reads are
+ * recomputed from the current C: R_L..R_3 before a forward sweep, L_1..L_{L-2}
+ * before a backward one. A segment-parallel fit switches only between full sets
+ * of local sweeps (else TT_ERR_STATE; the handle stays usable). fast_factor as
+ * in tt_fit_options; a default cut-off follows the new precision. Resets the
  * converged flag; delta keeps comparing consecutive sweeps. */
 tt_status tt_fit_set_precision(tt_fit* h, int precision, int fast_factor);
 

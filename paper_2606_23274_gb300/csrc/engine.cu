@@ -916,6 +916,22 @@ struct Sweeper {
     }
     CK(cudaStreamSynchronize(W(h).st));
   }
+
+  // The mirror, for a backward sweep from a left-canonical C: the left operands
+  // from C, then L_1..L_{L-2} and the halves H1_0..H1_{L-2}.
+  void precompute_left() {
+    Dims& D = h->D;
+    const int L = D.L;
+    const bool inv = h->gauge == TT_GAUGE_INVERSE_CANONICAL;
+    for (int j = 0; j + 2 < L; ++j)
+      CK(scale_cols_t<T>(D.c[j] * D.ds[j] * D.dt[j], D.c[j + 1], h->C64[j], inv ? h->Y[j + 1] : nullptr,
+                         (T*)h->Ut[j], W(h).st));
+    for (int j = 0; j + 1 < L; ++j) {
+      ch.half_left(j);
+      if (j + 2 < L) ch.finish_left(j);
+    }
+    CK(cudaStreamSynchronize(W(h).st));
+  }
 };
 
 // ---------------------------------------------------------------------------
@@ -1044,10 +1060,11 @@ void allocate_chain(tt_fit* h) {
   h->dn2 = calloc_chain<double>(h, L + 1);
 }
 
-// (Re)build the contraction chain in type T from the current C, which must be
-// right-canonical (after create, or after a backward sweep): operands, buffers,
-// the right-environment operands Vt_j (site gauge C_j, inverse gauge
-// Y_{j-1} Psi_j), trivial end environments and R_L..R_3 with their halves.
+// (Re)build the contraction chain in type T from the current C: operands,
+// buffers, the right-environment operands Vt_j (site gauge C_j, inverse gauge
+// Y_{j-1} Psi_j), trivial end environments, and the environments the next sweep
+// reads: R_L..R_3 with their halves before a forward sweep (C right-canonical),
+// L_1..L_{L-2} with theirs before a backward one (C left-canonical).
 template <typename T>
 void rebuild_chain(tt_fit* h) {
   Dims& D = h->D;
@@ -1067,7 +1084,8 @@ void rebuild_chain(tt_fit* h) {
   CK(cudaMemcpyAsync(h->Renv[L], &one, sizeof(T), cudaMemcpyHostToDevice, W(h).st));
   CK(cudaStreamSynchronize(W(h).st));
   Sweeper<T> sw(h);
-  sw.precompute_right();
+  if (h->forward) sw.precompute_right();
+  else sw.precompute_left();
 }
 
 // ---------------------------------------------------------------------------
@@ -1695,10 +1713,8 @@ tt_status tt_fit_result(const tt_fit* hc, tt_mpo_desc* C, double* lambdas) {
 tt_status tt_fit_set_precision(tt_fit* h, int precision, int fast_factor) {
   if (!h || precision < 0 || precision > 5 || precision == TT_PREC_BF16_SPLIT) return TT_ERR_INVALID_ARGUMENT;
   if (h->poisoned) return TT_ERR_STATE;
-  if (h->segs.size() > 1 ? (h->phases_done % 2 != 0) : !h->forward) {
-    h->last_error = h->segs.size() > 1
-                        ? "tt_fit_set_precision: a segment-parallel fit switches between full sets of local sweeps"
-                        : "tt_fit_set_precision: the next sweep must be a forward sweep (C right-canonical)";
+  if (h->segs.size() > 1 && h->phases_done % 2 != 0) {
+    h->last_error = "tt_fit_set_precision: a segment-parallel fit switches between full sets of local sweeps";
     return TT_ERR_STATE;
   }
   LaunchTally tally(h);

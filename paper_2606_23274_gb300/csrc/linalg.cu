@@ -1038,7 +1038,7 @@ cudaError_t scale_cols(int rows, int cols, const double* in, const double* y, do
 
 }  // namespace ttfit
 
-// out (cols x rows, row-major) = (in diag(y))^T, in rows x cols row-major FP64
+// out (cols x rows, row-major) = (in diag(y))^T, in rows x cols row-major FP64 (y = NULL: 1)
 namespace ttfit {
 template <typename T>
 __global__ void scale_cols_t_kernel(int rows, int cols, const double* __restrict__ in, const double* __restrict__ y,
@@ -1047,7 +1047,7 @@ __global__ void scale_cols_t_kernel(int rows, int cols, const double* __restrict
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
        e += (long long)gridDim.x * blockDim.x) {
     const int c = (int)(e / rows), r = (int)(e % rows);  // e indexes out; the read is strided
-    out[e] = (T)(in[(size_t)r * cols + c] * y[c]);
+    out[e] = (T)(y ? in[(size_t)r * cols + c] * y[c] : in[(size_t)r * cols + c]);
   }
 }
 
