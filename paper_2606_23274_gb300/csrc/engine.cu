@@ -21,6 +21,7 @@
 #include <new>
 #include <stdexcept>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/ttfit.h"
@@ -101,6 +102,11 @@ struct Work {
   double *fX = nullptr, *fQ = nullptr, *fR = nullptr, *fU = nullptr, *fV = nullptr, *fVw = nullptr, *fS = nullptr;
   double *fUM = nullptr, *fVM = nullptr, *fOm = nullptr, *fY = nullptr, *fBt = nullptr, *fQ2 = nullptr, *fR2 = nullptr;
   double *pU = nullptr, *pV = nullptr, *pG = nullptr, *pT = nullptr, *pP = nullptr;  // FP64 polish
+  // digit planes, chunk exponents and partials of the tensor-core FP64-class GEMM (DF32 chains)
+  float *ozA = nullptr, *ozB = nullptr;
+  int *ozEA = nullptr, *ozEB = nullptr;
+  df32* ozWs = nullptr;
+  size_t oz_slice = 0, oz_exp = 0, oz_ws = 0;
   size_t fsz = 0;
   double* dnorm = nullptr;
   int* dk = nullptr;
@@ -148,6 +154,7 @@ struct tt_fit {
   bool use_f32 = false;   // chain type: float (FP32 / TF32 precisions), df32 (DF32) or double (FP64)
   bool use_df = false;
   bool fact_f32 = false;  // FP32 factorisation + FP64 polish (always for float chains; optional for FP64)
+  bool use_oz = true;     // DF32 chains: contractions on the tensor cores by the digit split
   std::vector<void*> chain_bufs;  // buffers rebuilt when the chain precision changes
 };
 
@@ -201,6 +208,18 @@ struct FactT<df32> {
 template <typename T>
 void gemm(tt_fit* h, const GemmArgs<T>& g, bool chain = false) {
   const size_t wse = W(h).gws_elems * sizeof(double) / sizeof(T);
+  if constexpr (std::is_same<T, df32>::value) {
+    Work& w = W(h);
+    if (chain && h->use_oz && w.ozA && (long long)g.M * g.N * g.K >= (1ll << 21)) {
+      cudaError_t e = gemm_oz(g, w.ozA, w.ozB, w.oz_slice, w.ozEA, w.ozEB, w.oz_exp, w.ozWs, w.oz_ws, h->sm_count,
+                              w.errw, w.st);
+      if (e == cudaSuccess) {
+        h->tc_launches += 1;
+        return;
+      }
+      if (e != cudaErrorNotSupported) CK(e);
+    }
+  }
   if constexpr (sizeof(T) == 4) {
     const bool tc = h->precision == TT_PREC_TF32 || h->precision == TT_PREC_TF32_SPLIT;
     if (chain && tc && (long long)g.M * g.N * g.K >= (1ll << 18)) {
@@ -1041,6 +1060,16 @@ void allocate_chain(tt_fit* h) {
   }
   const long long ks = h->chi_max + h->oversample;
   const long long side = std::max(std::max(mmax, nmax), ks);
+  // the largest operand of any chain GEMM (environments, A/B operators, X1, Z, halves)
+  size_t omax = std::max<size_t>(x1, zs);
+  for (int j = 0; j <= L; ++j) omax = std::max<size_t>(omax, prodll({D.a[j], D.b[j], D.cb[j]}));
+  for (int j = 0; j < L; ++j) {
+    omax = std::max<size_t>(omax, prodll({D.cb[j], D.ds[j], D.dt[j], D.a[j + 1], D.b[j + 1]}));
+    omax = std::max<size_t>(omax, prodll({D.a[j], D.b[j], D.ds[j], D.dt[j], D.cb[j + 1]}));
+    omax = std::max<size_t>(omax, prodll({D.a[j], D.ds[j], D.du[j], D.a[j + 1]}));
+    omax = std::max<size_t>(omax, prodll({D.b[j], D.du[j], D.dt[j], D.b[j + 1]}));
+  }
+  omax += 65536;
   auto scratch = [&](Work& w) {
     w.X1 = calloc_chain<T>(h, x1);
     w.Zs = calloc_chain<T>(h, zs);
@@ -1054,6 +1083,16 @@ void allocate_chain(tt_fit* h) {
       *f = calloc_chain<double>(h, w.fsz);
     w.fS = calloc_chain<double>(h, side);
     w.pP = calloc_chain<double>(h, (size_t)side * ks + (size_t)ks * ks + 64);
+    if (std::is_same<T, df32>::value) {  // the tensor-core GEMM of the DF32 chain
+      w.oz_slice = (size_t)OZ_DIGITS * 2 * omax;
+      w.oz_exp = omax;
+      w.oz_ws = 2 * omax;
+      w.ozA = calloc_chain<float>(h, w.oz_slice);
+      w.ozB = calloc_chain<float>(h, w.oz_slice);
+      w.ozEA = calloc_chain<int>(h, w.oz_exp);
+      w.ozEB = calloc_chain<int>(h, w.oz_exp);
+      w.ozWs = calloc_chain<df32>(h, w.oz_ws);
+    }
   };
   scratch(h->w0);
   for (auto& w : h->wseg) scratch(*w);

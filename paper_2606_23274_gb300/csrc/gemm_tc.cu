@@ -18,6 +18,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <climits>
 #include <cstring>
 #include <mutex>
 
@@ -344,6 +345,207 @@ inline bool lin_stride(const IdxMap& m, long long& s) {
   return false;
 }
 
+// ---------------------------------------------------------------------------
+// FP64-class products on the TF32 tensor cores (Ozaki-type fixed-point split).
+// Every row of an operand is cut into chunks of OZ_KC columns; a chunk with
+// max |x| < 2^e is written as x = 2^e sum_i s_i 2^(-7-8i), i < OZ_S, with
+// integer digits |s_i| <= 128 (stored as s_i 2^(-8i), exact in TF32). A
+// product of two chunks is then 2^(eA+eB-14) sum over digit pairs (i, j) of
+// 2^(-8(i+j)) sum_k sA_i sB_j. Pairs with i + j < OZ_S are kept (the dropped ones
+// weigh <= 2^-48 of the largest term). Level 0 (i = j = 0) and level 1 sum
+// integers of <= 2^14 (resp. 2^15 in units of 2^-8) over <= 512 terms, so their
+// FP32 accumulators in tensor memory are exact (checked on integer inputs: the
+// products come out exact); level 2 has an accumulator of its own (rounding
+// weighted 2^-16 x 2^-24) and levels >= 3 share the fourth. The epilogue joins
+// the four in double-FP32 and scales by the chunk exponents; the chunks of K
+// are the split-K partials, summed in double-FP32 by splitk_reduce.
+// ---------------------------------------------------------------------------
+constexpr int OZ_S = 6;
+constexpr int OZ_KC = 512;
+constexpr int OZ_TILES = 2 * OZ_S;
+constexpr int OZ_SMEM = OZ_TILES * TILE_BYTES + 1024 + 256;
+constexpr int OZ_EZERO = -1000;  // exponent of an all-zero chunk
+
+// digits of one operand: X [R][K] (row stride ld, K contiguous) -> sl [OZ_S][R][Kp], ex [R][nch]
+template <typename T>
+__device__ __forceinline__ float2 as_pair(T x);
+template <>
+__device__ __forceinline__ float2 as_pair<df32>(df32 x) { return make_float2(x.hi, x.lo); }
+template <>
+__device__ __forceinline__ float2 as_pair<float>(float x) { return make_float2(x, 0.f); }
+
+template <typename T>
+__global__ void oz_slice_kernel(int R, int K, int Kp, const T* __restrict__ X, long long ld, float* __restrict__ sl,
+                                int* __restrict__ ex, int nch) {
+  const int lane = threadIdx.x & 31;
+  const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  if (gw >= (long long)R * nch) return;
+  const int row = (int)(gw / nch), ch = (int)(gw % nch);
+  const int k0 = ch * OZ_KC, k1 = min(K, k0 + OZ_KC), kp1 = min(Kp, k0 + OZ_KC);
+  const T* x = X + row * ld;
+  int e = INT_MIN;
+  for (int k = k0 + lane; k < k1; k += 32) {
+    const float h = as_pair<T>(x[k]).x;
+    if (h != 0.f) e = max(e, ((__float_as_int(h) >> 23) & 0xFF) - 126);  // |h| < 2^e
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if (e == INT_MIN) e = OZ_EZERO;
+  if (lane == 0) ex[(long long)row * nch + ch] = e;
+  const size_t plane = (size_t)R * Kp;
+  for (int k = k0 + lane; k < kp1; k += 32) {
+    float d[OZ_S];
+    if (k < K) {
+      const float2 v = as_pair<T>(x[k]);
+      // x 2^(7-e) = th + tl exactly; peel one 8-bit digit per level, carrying the exact remainder
+      float th = scalbnf(v.x, 7 - e), tl = scalbnf(v.y, 7 - e);
+#pragma unroll
+      for (int i = 0; i < OZ_S; ++i) {
+        const float si = rintf(th);
+        d[i] = scalbnf(si, -8 * i);
+        const df32 r = two_sum(__fsub_rn(th, si), tl);  // th - si is exact
+        th = __fmul_rn(r.hi, 256.f);
+        tl = __fmul_rn(r.lo, 256.f);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < OZ_S; ++i) d[i] = 0.f;
+    }
+#pragma unroll
+    for (int i = 0; i < OZ_S; ++i) sl[i * plane + (size_t)row * Kp + k] = d[i];
+  }
+}
+
+__device__ __forceinline__ void oz_mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, bool acc) {
+  mma_tf32(tmem, ad, bd, idesc, acc ? 1u : 0u);
+}
+
+// One 128 x 128 output tile of one K-chunk (blockIdx.z) into the double-FP32
+// partial ws[z][M][N]. Warp 0: TMA producer; warp 1: tensor-memory owner and
+// MMA issuer; all four warps: epilogue. One stage holds the 2 OZ_S digit tiles
+// of a k-block (192 KB); the four accumulators fill the 512 tensor-memory columns.
+__global__ void __launch_bounds__(128, 1)
+    gemm_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
+                   int K, const int* __restrict__ eA, const int* __restrict__ eB, int nch, df32* __restrict__ ws,
+                   uint32_t* errw) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(smem + OZ_TILES * TILE_BYTES);  // [0] full, [1] empty, [2] accumulators ready
+  uint32_t* tmem_slot = (uint32_t*)(bars + 3);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN, z = blockIdx.z;
+  const int kb0 = z * OZ_KC, kend = min(K, kb0 + OZ_KC);
+  const int nk = (kend - kb0 + BK - 1) / BK;
+  if (threadIdx.x == 0) {
+    mbar_init(su32(&bars[0]), 1);
+    mbar_init(su32(&bars[1]), 1);
+    mbar_init(su32(&bars[2]), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)), "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  int issued = 0;
+  if (warp == 0 && lane == 0) {
+    for (int kb = 0; kb < nk; ++kb) {
+      if (*abort_flag || !mbar_wait(su32(&bars[1]), (kb & 1) ^ 1)) {
+        *abort_flag = 1;
+        break;
+      }
+      const uint32_t full = su32(&bars[0]);
+      mbar_expect_tx(full, OZ_TILES * TILE_BYTES);
+      const int k = kb0 + kb * BK;
+#pragma unroll
+      for (int i = 0; i < OZ_S; ++i) {
+        tma_load_2d(su32(smem + i * TILE_BYTES), &tmA, full, k, i * M + m0);
+        tma_load_2d(su32(smem + (OZ_S + i) * TILE_BYTES), &tmB, full, k, i * N + n0);
+      }
+      issued = kb + 1;
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t idesc = idesc_tf32(BM, BN, false);
+    bool started[4] = {false, false, false, false};
+    bool ok = true;
+    for (int kb = 0; kb < nk; ++kb) {
+      if (*abort_flag || !mbar_wait(su32(&bars[0]), kb & 1)) {
+        *abort_flag = 1;
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int i = 0; i < OZ_S; ++i)
+#pragma unroll
+        for (int j = 0; j + i < OZ_S; ++j) {
+          const int lev = min(i + j, 3);
+          const uint32_t a_base = su32(smem + i * TILE_BYTES), b_base = su32(smem + (OZ_S + j) * TILE_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < BK / 8; ++kk) {
+            oz_mma(tmem + lev * BN, sdesc(a_base + kk * 32, 16, 1024), sdesc(b_base + kk * 32, 16, 1024), idesc,
+                   started[lev]);
+            started[lev] = true;
+          }
+        }
+      mma_commit(su32(&bars[1]));  // frees the stage once these MMAs have read it
+    }
+    if (ok) mma_commit(su32(&bars[2]));
+  }
+  __syncwarp();
+  bool have = false;
+  if (nk > 0) have = mbar_wait(su32(&bars[2]), 0) && !*abort_flag;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int m = m0 + warp * 32 + lane;
+  df32* wrow = ws + ((size_t)z * M + (m < M ? m : 0)) * N;
+  const int ea = (m < M) ? eA[(size_t)m * nch + z] : OZ_EZERO;
+  if (have) {
+#pragma unroll 1
+    for (int c = 0; c < BN; c += 32) {
+      uint32_t r0[32], r1[32], r2[32], r3[32];
+      const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + c;
+      tmem_ld32(base, r0);
+      tmem_ld32(base + BN, r1);
+      tmem_ld32(base + 2 * BN, r2);
+      tmem_ld32(base + 3 * BN, r3);
+      if (m < M) {
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+          const int n = n0 + c + t;
+          if (n < N) {
+            const df32 s = two_sum(__uint_as_float(r0[t]), __uint_as_float(r1[t]));
+            const df32 u = two_sum(s.hi, __uint_as_float(r2[t]));
+            const df32 u2 = two_sum(u.hi, __uint_as_float(r3[t]));
+            const df32 v = renorm(u2.hi, __fadd_rn(__fadd_rn(u2.lo, u.lo), s.lo));
+            const int sc = max(ea + eB[(size_t)n * nch + z] - 14, -2 * 1000);
+            wrow[n] = df32(scalbnf(v.hi, sc), scalbnf(v.lo, sc));
+          }
+        }
+      }
+    }
+  } else if (nk > 0 && threadIdx.x == 0 && errw) {
+    atomicOr(errw, ERRW_TIMEOUT);
+  }
+  if (nk == 0 && m < M)
+    for (int n = n0; n < min(N, n0 + BN); ++n) wrow[n] = df32(0.f, 0.f);
+  if (warp == 0 && lane == 0 && *abort_flag)
+    for (int kb = 0; kb < issued; ++kb) mbar_wait(su32(&bars[0]), kb & 1);
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+}
+
 }  // namespace tc
 
 // Returns cudaErrorNotSupported when the operand layouts cannot be fed by TMA
@@ -393,6 +595,47 @@ cudaError_t gemm_tf32(const GemmArgs<float>& g, float* ws, size_t ws_elems, int 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || splits == 1) return e;
   return splitk_reduce<float>(g, ws, splits, sm_count, st);
+}
+
+// FP64-class GEMM (double-FP32 operands and result) on the TF32 tensor cores
+// by the fixed-point digit split above. Operands must be K-major with 16-byte
+// aligned rows after padding, like gemm_tf32. sA, sB: digit planes of
+// OZ_S * M * Kp and OZ_S * N * Kp floats; eA, eB: M * nch and N * nch ints;
+// ws: nch * M * N double-FP32 partials. Returns cudaErrorNotSupported when a
+// layout or a capacity does not fit (the caller then uses the CUDA-core kernel).
+cudaError_t gemm_oz(const GemmArgs<df32>& g, float* sA, float* sB, size_t slice_elems, int* eA, int* eB,
+                    size_t exp_elems, df32* ws, size_t ws_elems, int sm_count, uint32_t* errw, cudaStream_t st) {
+  using namespace tc;
+  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+  if (g.K < 1) return cudaErrorNotSupported;
+  long long lda, ldb, one;
+  if (!lin_stride(g.am, lda) || !lin_stride(g.ak, one) || one != 1) return cudaErrorNotSupported;
+  if (!lin_stride(g.bk, one) || one != 1 || !lin_stride(g.bn, ldb)) return cudaErrorNotSupported;
+  const int Kp = (g.K + 3) / 4 * 4;  // 16-byte rows of FP32 digits
+  const int nch = (g.K + OZ_KC - 1) / OZ_KC;
+  if ((size_t)OZ_S * g.M * Kp > slice_elems || (size_t)OZ_S * g.N * Kp > slice_elems) return cudaErrorNotSupported;
+  if ((size_t)g.M * nch > exp_elems || (size_t)g.N * nch > exp_elems) return cudaErrorNotSupported;
+  if ((size_t)nch * g.M * g.N > ws_elems) return cudaErrorNotSupported;
+  auto slice = [&](int R, const df32* X, long long ld, float* sl, int* ex) {
+    const long long warps = (long long)R * nch;
+    const int blocks = (int)((warps * 32 + 255) / 256);
+    ++tl_launches;
+    oz_slice_kernel<df32><<<blocks, 256, 0, st>>>(R, g.K, Kp, X, ld, sl, ex, nch);
+    return cudaGetLastError();
+  };
+  cudaError_t e = slice(g.M, g.A, lda, sA, eA);
+  if (e != cudaSuccess) return e;
+  if ((e = slice(g.N, g.B, ldb, sB, eB)) != cudaSuccess) return e;
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, sA, (uint64_t)Kp, (uint64_t)OZ_S * g.M, (uint64_t)Kp, BK, BM)) return cudaErrorNotSupported;
+  if (!make_map(&tb, sB, (uint64_t)Kp, (uint64_t)OZ_S * g.N, (uint64_t)Kp, BK, BN)) return cudaErrorNotSupported;
+  if ((e = cudaFuncSetAttribute(gemm_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM)) != cudaSuccess)
+    return e;
+  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, nch);
+  ++tl_launches;
+  gemm_oz_kernel<<<grid, 128, OZ_SMEM, st>>>(ta, tb, g.M, g.N, g.K, eA, eB, nch, ws, errw);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return splitk_reduce<df32>(g, ws, nch, sm_count, st);
 }
 
 }  // namespace ttfit
