@@ -120,9 +120,14 @@ def run_fit(ttfit, Ain, Bin, schedule, seed, dev, stream, chi=CHI, lo_sweeps=LO_
     single-precision fit, or "lo>hi", e.g. "tf32x3>df32": sweeps in ``lo`` (FP32-factorised
     randomized update) for ``lo_sweeps`` sweeps, then FP64-class contractions in ``hi`` with the
     FP64-polished FP32 factorisation until converged."""
+    import torch
     lo, hi = (schedule.split(">") + [None])[:2]
+    ev = {k: torch.cuda.Event(enable_timing=True) for k in ("c0", "c1", "s0", "s1", "r0", "r1")}
+    ev["c0"].record(stream)
     f = ttfit.tt_fit_create(Ain, Bin, chi, TOL, "site", update="rsvd", oversample=OVERSAMPLE, seed=seed,
                             precision=lo, device=dev, stream=stream)
+    ev["c1"].record(stream)
+    switched = False
     phases = {lo: {k: 0.0 for k in STAGES}}
     phase_sweeps = {lo: 0}
     cur, sweeps, rep = lo, 0, None
@@ -138,12 +143,22 @@ def run_fit(ttfit, Ain, Bin, schedule, seed, dev, stream, chi=CHI, lo_sweeps=LO_
         if rep["converged"] and (hi is None or cur == hi):
             break
         if hi is not None and cur == lo and sweeps >= lo_sweeps:
+            ev["s0"].record(stream)
             f.set_precision(hi, fast_factor=True)
+            ev["s1"].record(stream)
+            switched = True
             cur = hi
             phases[hi] = {k: 0.0 for k in STAGES}
             phase_sweeps[hi] = 0
+    ev["r0"].record(stream)
     C = f.result()
+    ev["r1"].record(stream)
+    ev["r1"].synchronize()
+    rep["host_ms"] = {"create": ev["c0"].elapsed_time(ev["c1"]),
+                      "switch": ev["s0"].elapsed_time(ev["s1"]) if switched else 0.0,
+                      "export": ev["r0"].elapsed_time(ev["r1"])}
     launches = f.launch_count()
+    rep["bonds"] = f.bonds()
     f.destroy()
     rep["history"] = history
     return rep, sweeps, phase_sweeps, phases, C, launches
@@ -267,6 +282,29 @@ def native(args):
                     "frac": round(tflops / peak, 4), "traffic": None,
                     "kernel": f"gemm_tf32_kernel (contraction chain, {dom_phase} phase)",
                     "peak_source": f"of measured: bf16 sustained / {ratio:g}"}
+    elif dom_stage == "factorize":
+        # algorithmic work of the randomized factorisation of one m x n window with sketch width k:
+        # Y = M Omega and B^T = M^T Q (2 m n k each), Householder QR of Y and of B^T with Q formed
+        # (4 m k^2 - 4/3 k^3 each), SVD of the k x k factor with both bases (~21 k^3, Golub-Kahan count),
+        # U = Q Vr and V = Q2 Ur (2 m k^2 + 2 n k^2); windows with k >= min(m, n) take the exact SVD
+        # (at most 4 per sweep, ends of the chain) and are not counted
+        b = results[-1][0]["bonds"]
+        ks = CHI + OVERSAMPLE
+        per_sweep = 0.0
+        for l in range(len(b) - 3):
+            m, n = b[l] * 4, 4 * b[l + 2]
+            if ks < min(m, n):
+                per_sweep += 4.0 * m * n * ks + 4.0 * m * ks ** 2 + 4.0 * n * ks ** 2 - 8.0 / 3 * ks ** 3 \
+                    + 21.0 * ks ** 3 + 2.0 * m * ks ** 2 + 2.0 * n * ks ** 2
+        sweeps_in = statistics.mean(r[2][dom_phase] for r in results)
+        tflops = per_sweep * sweeps_in / (dom_ms * 1e-3) / 1e12
+        peak = 152 * FMA_LANES["f32"] * 2 * mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(peak, 2), "unit": "TFLOP/s",
+                "frac": round(tflops / peak, 5), "traffic": None,
+                "kernel": f"factorisation stage ({dom_phase} phase): qr_cluster_kernel<float> x2, "
+                          "jacobi_cluster_kernel<float>, sketch GEMMs, per window",
+                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (the cluster kernels occupy 8 "
+                               "SMs and are bound by the latency of their sequential steps)"}
     else:
         roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None, "traffic": None,
                 "kernel": f"{dom_stage} ({dom_phase} phase)"}
@@ -290,6 +328,8 @@ def native(args):
         "delta_history": [float(f"{d:.3e}") if d != float("inf") else None for d in rep["history"]],
         "local_update_tflops": round(local_flops / (local_ms * 1e-3) / 1e12, 3) if local_ms > 0 else None,
         "stage_ms_per_fit": {p: {k: round(agg[p][k], 2) for k in STAGES[:5]} for p in names},
+        "create_switch_export_ms": {k: round(statistics.mean(r[0]["host_ms"][k] for r in results), 2)
+                                    for k in ("create", "switch", "export")},
         "roofline": roof, "clocks": clk, "e2e": e2e, "gpu_launches": int(sum(r[5] for r in results)), "gpu_launches_per_step": int(launches),
         "fits_per_s": round(world / t_step, 4), "wall_s_timed": round(wall, 2),
     }
