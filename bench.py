@@ -301,7 +301,7 @@ def native(args):
         peak = 152 * FMA_LANES["f32"] * 2 * mhz * 1e6 / 1e12
         roof = {"bound": "alu", "achieved": round(tflops, 4), "peak": round(peak, 2), "unit": "TFLOP/s",
                 "frac": round(tflops / peak, 5), "traffic": None,
-                "kernel": f"factorisation stage ({dom_phase} phase): qr_cluster_kernel<float> x2, "
+                "kernel": f"factorisation stage ({dom_phase} phase): qr_cluster_blocked_kernel<float> x2, "
                           "jacobi_cluster_kernel<float>, sketch GEMMs, per window",
                 "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz (the cluster kernels occupy 8 "
                                "SMs and are bound by the latency of their sequential steps)"}

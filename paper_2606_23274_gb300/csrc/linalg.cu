@@ -264,6 +264,224 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
   cl.sync();  // no CTA leaves while another may still write into its shared memory
 }
 
+// Blocked variant: panels of QB columns. Per panel every CTA gathers the
+// panel's rows (>= j0) from all CTAs, factors it redundantly (identical
+// reflectors V, R entries and the compact-WY factor T with H_j0 ... H_j1-1 =
+// I - V T V^T, T_jj = 2, T(:j, j) = -2 T (V^T v_j), for unit-norm v), forms its
+// partial W = V^T A of the trailing columns over its rows, and after one
+// cluster barrier pulls the partials of all CTAs and applies A -= V (T^T W) to
+// its rows. Q is formed backwards panel by panel the same way. Two cluster
+// barriers per panel instead of three per column.
+constexpr int QB = 16;
+
+template <typename C>
+__global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
+    qr_cluster_blocked_kernel(int q, int p, const C* __restrict__ Xg, C* __restrict__ Qg, C* __restrict__ Rg) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int k = (int)cl.block_rank();
+  const int r = min(q, p);
+  const int rb = (q + JQ - 1) / JQ;
+  const int ld = rb | 1;
+  const int ldp = q | 1;                                // panel buffer column stride (all rows)
+  const int r0 = k * rb, nr = max(0, min(rb, q - r0));
+  const int npan = (r + QB - 1) / QB;
+  extern __shared__ __align__(16) unsigned char qbs[];
+  C* X = (C*)qbs;                                       // [p][ld] my rows of X
+  C* U = X + (size_t)p * ld;                            // union: panel [QB][ldp] / my rows of Q [r][ld]
+  const size_t usz = max((size_t)QB * ldp, (size_t)r * ld);
+  C* Wl = U + usz;                                      // [2][QB][p] my partial V^T A (by panel parity)
+  C* Ws = Wl + 2 * (size_t)QB * p;                      // [QB][p] the summed W, then T^T W (or T W)
+  C* Tm = Ws + (size_t)QB * p;                          // [npan][QB][QB] compact-WY factors (column-major)
+  C* diag = Tm + (size_t)npan * QB * QB;                // [r]
+  __shared__ C red[32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (long long e = threadIdx.x; e < (long long)p * rb; e += blockDim.x) {
+    const int i = (int)(e % rb), c = (int)(e / rb);
+    X[(size_t)c * ld + i] = i < nr ? Xg[(size_t)c * q + r0 + i] : C(0);
+  }
+  for (int t = threadIdx.x; t < npan * QB * QB; t += blockDim.x) Tm[t] = C(0);
+  for (int pn = 0; pn < npan; ++pn) {
+    const int j0 = pn * QB, w = min(QB, r - j0);
+    C* T = Tm + (size_t)pn * QB * QB;
+    C* W = Wl + (size_t)(pn & 1) * QB * p;
+    cl.sync();  // the panel's columns are final in every CTA
+    // gather rows j0..q-1 of the panel columns: PB[cc][g - j0]
+    C* PB = U;
+    for (long long e = threadIdx.x; e < (long long)w * (q - j0); e += blockDim.x) {
+      const int cc = (int)(e / (q - j0)), g = j0 + (int)(e % (q - j0));
+      const int owner = g / rb;
+      const C* src = cl.map_shared_rank(X, (unsigned)owner);
+      PB[(size_t)cc * ldp + (g - j0)] = src[(size_t)(j0 + cc) * ld + (g - owner * rb)];
+    }
+    __syncthreads();
+    // factor the panel (rows >= j0), redundantly in every CTA
+    for (int jj = 0; jj < w; ++jj) {
+      C* pj = PB + (size_t)jj * ldp;
+      const int n = q - j0;  // panel rows
+      C ss = 0;
+      for (int i = jj + (int)threadIdx.x; i < n; i += blockDim.x) ss += pj[i] * pj[i];
+      ss = block_sum(ss, red);
+      const C x0 = pj[jj];
+      const C nrm = sqrt(ss);
+      const C alpha = (x0 >= C(0)) ? -nrm : nrm;
+      const C v0 = x0 - alpha;
+      const C vn2 = ss - x0 * x0 + v0 * v0;
+      const bool zero = !(vn2 > C(0));
+      const C inv = zero ? C(0) : C(1) / sqrt(vn2);
+      __syncthreads();  // everyone has read pj before it becomes v
+      for (int i = jj + (int)threadIdx.x; i < n; i += blockDim.x) pj[i] = (i == jj ? v0 : pj[i]) * inv;
+      if (threadIdx.x == 0) diag[j0 + jj] = zero ? C(0) : alpha;
+      __syncthreads();
+      // apply H = I - 2 v v^T to the remaining panel columns; z_i = v_i^T v for the T column
+      for (int cc = jj + 1 + warp; cc < w; cc += nw) {
+        C* pc = PB + (size_t)cc * ldp;
+        C d = 0;
+        for (int i = jj + lane; i < n; i += 32) d += pj[i] * pc[i];
+        d = warp_sum(d);
+        for (int i = jj + lane; i < n; i += 32) pc[i] -= C(2) * d * pj[i];
+      }
+      for (int ii = warp; ii < jj; ii += nw) {
+        const C* pi = PB + (size_t)ii * ldp;
+        C d = 0;
+        for (int i = jj + lane; i < n; i += 32) d += pi[i] * pj[i];
+        d = warp_sum(d);
+        if (lane == 0) Ws[ii] = d;  // scratch: z (Ws is free here)
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {  // T(:jj, jj) = -2 T(:jj, :jj) z, T(jj, jj) = 2 (or 0 for a null reflector)
+        for (int a = 0; a < jj; ++a) {
+          C t = 0;
+          for (int b = a; b < jj; ++b) t += T[b * QB + a] * Ws[b];
+          T[jj * QB + a] = zero ? C(0) : C(-2) * t;
+        }
+        T[jj * QB + jj] = zero ? C(0) : C(2);
+      }
+      __syncthreads();
+    }
+    // my partial W = V^T A over my rows, trailing columns c >= j0 + w
+    const int c1 = j0 + w;
+    for (long long e = threadIdx.x; e < (long long)w * (p - c1); e += blockDim.x) {
+      const int jj = (int)(e % w), c = c1 + (int)(e / w);
+      const C* pj = PB + (size_t)jj * ldp;
+      const C* xc = X + (size_t)c * ld;
+      C d = 0;
+      for (int i = max(0, j0 + jj - r0); i < nr; ++i) d += pj[r0 + i - j0] * xc[i];
+      W[(size_t)jj * p + c] = d;
+    }
+    cl.sync();  // every CTA has gathered the panel and formed its partial W
+    // write my rows of the factored panel back (R entries above, v below the diagonal)
+    for (long long e = threadIdx.x; e < (long long)w * nr; e += blockDim.x) {
+      const int cc = (int)(e / nr), i = (int)(e % nr);
+      const int g = r0 + i;
+      if (g >= j0) X[(size_t)(j0 + cc) * ld + i] = PB[(size_t)cc * ldp + (g - j0)];
+    }
+    // W = sum over CTAs, then Ws = T^T W (column by column)
+    for (int c = c1 + (int)threadIdx.x; c < p; c += blockDim.x) {
+      C wv[QB];
+#pragma unroll
+      for (int jj = 0; jj < QB; ++jj) wv[jj] = C(0);
+      for (int t = 0; t < JQ; ++t) {
+        const C* rw = cl.map_shared_rank(W, (unsigned)t);
+#pragma unroll
+        for (int jj = 0; jj < QB; ++jj)
+          if (jj < w) wv[jj] += rw[(size_t)jj * p + c];
+      }
+#pragma unroll
+      for (int a = 0; a < QB; ++a) {
+        C t = 0;
+#pragma unroll
+        for (int b = 0; b <= a; ++b) t += T[a * QB + b] * wv[b];  // (T^T)(a, b) = T(b, a), b <= a
+        if (a < w) Ws[(size_t)a * p + c] = t;
+      }
+    }
+    __syncthreads();
+    // A(my rows >= j0, c >= c1) -= V W'
+    if (nr > 0)
+      for (long long e = threadIdx.x; e < (long long)(p - c1) * nr; e += blockDim.x) {
+        const int i = (int)(e % nr), c = c1 + (int)(e / nr);
+        const int g = r0 + i;
+        if (g < j0) continue;
+        C d = 0;  // v_jj has support on panel rows >= jj; above it PB holds R entries
+        const int jn = min(w, g - j0 + 1);
+        for (int jj = 0; jj < jn; ++jj) d += PB[(size_t)jj * ldp + (g - j0)] * Ws[(size_t)jj * p + c];
+        X[(size_t)c * ld + i] -= d;
+      }
+    __syncthreads();
+  }
+  cl.sync();  // every CTA is done with the panel buffers before Q reuses the space
+  C* Qm = U;
+  for (long long e = threadIdx.x; e < (long long)r * rb; e += blockDim.x) {
+    const int i = (int)(e % rb), c = (int)(e / rb);
+    Qm[(size_t)c * ld + i] = (r0 + i == c) ? C(1) : C(0);
+  }
+  __syncthreads();
+  for (int pn = npan - 1; pn >= 0; --pn) {
+    const int j0 = pn * QB, w = min(QB, r - j0);
+    const C* T = Tm + (size_t)pn * QB * QB;
+    C* W = Wl + (size_t)(pn & 1) * QB * p;
+    // my partial V^T Q over my rows, columns c >= j0
+    for (long long e = threadIdx.x; e < (long long)w * (r - j0); e += blockDim.x) {
+      const int jj = (int)(e % w), c = j0 + (int)(e / w);
+      const C* vj = X + (size_t)(j0 + jj) * ld;
+      const C* qc = Qm + (size_t)c * ld;
+      C d = 0;
+      for (int i = max(0, j0 + jj - r0); i < nr; ++i) d += vj[i] * qc[i];
+      W[(size_t)jj * p + c] = d;
+    }
+    cl.sync();
+    for (int c = j0 + (int)threadIdx.x; c < r; c += blockDim.x) {
+      C wv[QB];
+#pragma unroll
+      for (int jj = 0; jj < QB; ++jj) wv[jj] = C(0);
+      for (int t = 0; t < JQ; ++t) {
+        const C* rw = cl.map_shared_rank(W, (unsigned)t);
+#pragma unroll
+        for (int jj = 0; jj < QB; ++jj)
+          if (jj < w) wv[jj] += rw[(size_t)jj * p + c];
+      }
+#pragma unroll
+      for (int a = 0; a < QB; ++a) {
+        C t = 0;
+#pragma unroll
+        for (int b = a; b < QB; ++b) t += T[b * QB + a] * wv[b];  // T(a, b), b >= a
+        if (a < w) Ws[(size_t)a * p + c] = t;
+      }
+    }
+    __syncthreads();
+    if (nr > 0)
+      for (long long e = threadIdx.x; e < (long long)(r - j0) * nr; e += blockDim.x) {
+        const int i = (int)(e % nr), c = j0 + (int)(e / nr);
+        const int g = r0 + i;
+        if (g < j0) continue;
+        C d = 0;
+        const int jn = min(w, g - j0 + 1);
+        for (int jj = 0; jj < jn; ++jj) d += X[(size_t)(j0 + jj) * ld + i] * Ws[(size_t)jj * p + c];
+        Qm[(size_t)c * ld + i] -= d;
+      }
+    __syncthreads();
+  }
+  for (long long e = threadIdx.x; e < (long long)r * nr; e += blockDim.x) {
+    const int i = (int)(e % nr), c = (int)(e / nr);
+    Qg[(size_t)c * q + r0 + i] = diag[c] < C(0) ? -Qm[(size_t)c * ld + i] : Qm[(size_t)c * ld + i];
+  }
+  for (long long e = threadIdx.x; e < (long long)p * nr; e += blockDim.x) {
+    const int i = (int)(e % nr), c = (int)(e / nr);
+    const int gi = r0 + i;
+    if (gi >= r) continue;
+    const C val = gi < c ? X[(size_t)c * ld + i] : (gi == c ? diag[gi] : C(0));
+    Rg[(size_t)c * r + gi] = diag[gi] < C(0) ? -val : val;
+  }
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+template <typename C>
+size_t qr_cluster_blocked_smem(int q, int p) {
+  const size_t rb = (q + JQ - 1) / JQ, ld = rb | 1, ldp = (size_t)(q | 1), r = std::min(q, p);
+  const size_t npan = (r + QB - 1) / QB;
+  const size_t usz = std::max((size_t)QB * ldp, r * ld);
+  return ((size_t)p * ld + usz + 3 * (size_t)QB * p + npan * QB * QB + r) * sizeof(C) + 16;
+}
+
 template <typename C>
 size_t qr_cluster_smem(int q, int p) {
   const size_t rb = (q + JQ - 1) / JQ, ld = rb | 1, r = std::min(q, p);
@@ -275,6 +493,15 @@ cudaError_t qr_householder(int q, int p, S* X, S* Q, S* R, cudaStream_t st) {
   if (q <= 0 || p <= 0) return cudaSuccess;
   if (min(q, p) > 1024 || q > 1024) return cudaErrorInvalidValue;
   if constexpr (std::is_same<C, S>::value) {  // rows spread over a cluster when the matrix is large enough
+    const size_t bsm = qr_cluster_blocked_smem<C>(q, p);
+    if (q >= 128 && p >= 16 && bsm <= 220 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(qr_cluster_blocked_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)bsm);
+      if (e != cudaSuccess) return e;
+      ++tl_launches;
+      qr_cluster_blocked_kernel<C><<<JQ, 256, bsm, st>>>(q, p, X, Q, R);
+      return cudaGetLastError();
+    }
     const size_t csm = qr_cluster_smem<C>(q, p);
     if (q >= 128 && p >= 16 && csm <= 200 * 1024) {
       if (csm > 48 * 1024) {
