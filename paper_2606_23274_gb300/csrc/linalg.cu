@@ -264,222 +264,379 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
   cl.sync();  // no CTA leaves while another may still write into its shared memory
 }
 
-// Blocked variant: panels of QB columns. Per panel every CTA gathers the
-// panel's rows (>= j0) from all CTAs, factors it redundantly (identical
-// reflectors V, R entries and the compact-WY factor T with H_j0 ... H_j1-1 =
-// I - V T V^T, T_jj = 2, T(:j, j) = -2 T (V^T v_j), for unit-norm v), forms its
-// partial W = V^T A of the trailing columns over its rows, and after one
-// cluster barrier pulls the partials of all CTAs and applies A -= V (T^T W) to
-// its rows. Q is formed backwards panel by panel the same way. Two cluster
-// barriers per panel instead of three per column.
+// Blocked variant: panels of QB columns, compact-WY updates.
+//
+// Per panel every CTA gathers the panel's rows (>= j0) from all CTAs into
+// registers (RPT rows x QB columns per thread) and factors it redundantly, so
+// all CTAs hold identical reflectors. One block reduction per column gives the
+// column's Gram row g_c = a_j^T a_c (rows >= j), from which the reflector
+// (alpha, unit v) and v^T a_c = (g_c - alpha a_c[j]) / ||v|| follow; the same
+// reduction carries v_i^T v_{j-1} (i < j-1), the strictly upper part of
+// G = V^T V. The product of the panel's reflectors (tau = 2, unit v) is
+// I - V T V^T with T^{-1} = I/2 + striu(G) (the UT transform of Joffrain,
+// Low, Quintana-Orti, van de Geijn and Puglisi, ACM TOMS 32 (2006)), so T is
+// never formed: the trailing update A -= V T^T (V^T A) solves a triangular
+// system per column instead. V^T A is a sum over the CTAs' rows: each CTA
+// forms its partial, and after one cluster barrier pulls those of all CTAs.
+// Q is formed backwards panel by panel with Q -= V T (V^T Q). A null column
+// gives v = 0, which leaves everything unchanged. Two cluster barriers per
+// panel in the factorisation, one in the formation of Q.
 constexpr int QB = 16;
 
 template <typename C>
+__device__ __forceinline__ void ld16(const C* __restrict__ src, C (&v)[QB]) {
+  if constexpr (sizeof(C) == 4) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+    for (int t = 0; t < QB / 4; ++t) {
+      const float4 x = s4[t];
+      v[4 * t] = x.x;
+      v[4 * t + 1] = x.y;
+      v[4 * t + 2] = x.z;
+      v[4 * t + 3] = x.w;
+    }
+  } else {
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+#pragma unroll
+    for (int t = 0; t < QB / 2; ++t) {
+      const double2 x = s2[t];
+      v[2 * t] = x.x;
+      v[2 * t + 1] = x.y;
+    }
+  }
+}
+
+template <typename C>
+__device__ __forceinline__ void st16(C* __restrict__ dst, const C (&v)[QB]) {
+  if constexpr (sizeof(C) == 4) {
+    float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+    for (int t = 0; t < QB / 4; ++t) d4[t] = make_float4(v[4 * t], v[4 * t + 1], v[4 * t + 2], v[4 * t + 3]);
+  } else {
+    double2* d2 = reinterpret_cast<double2*>(dst);
+#pragma unroll
+    for (int t = 0; t < QB / 2; ++t) d2[t] = make_double2(v[2 * t], v[2 * t + 1]);
+  }
+}
+
+// Sum over the warp of 16 slots (reduce-scatter by halving: 8 + 4 + 2 + 1 + 1
+// shuffles); lanes 2s and 2s + 1 return the sum of slot s.
+template <typename C>
+__device__ __forceinline__ C warp_reduce16(C (&v)[QB], int lane) {
+#pragma unroll
+  for (int h = QB / 2, m = 16; h >= 1; h >>= 1, m >>= 1) {
+    const bool hi = (lane & m) != 0;
+#pragma unroll
+    for (int t = 0; t < h; ++t) {
+      const C send = hi ? v[t] : v[t + h];
+      const C keep = hi ? v[t + h] : v[t];
+      v[t] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+__host__ __device__ constexpr size_t qr_al4(size_t n) { return (n + 3) & ~(size_t)3; }
+
+// Shared memory layout (elements of C, every region a multiple of 4 long).
+struct QrbLayout {
+  size_t X, U, P, Qm, Vmy, Wl, Ys, Gm, Gt, diag, red, xrow, total;
+  __host__ __device__ QrbLayout(int q, int p) {
+    const size_t rb = (q + JQ - 1) / JQ, ld = rb | 1, r = q < p ? q : p, npan = (r + QB - 1) / QB;
+    X = 0;
+    U = qr_al4((size_t)p * ld);
+    P = U;                                   // factorisation: V of the panel, row-major [q - j0][QB]
+    Qm = U;                                  // formation of Q: my rows of Q [r][ld], then my rows of V [rb][QB]
+    Vmy = U + qr_al4(r * ld);
+    const size_t usz = (size_t)q * QB > qr_al4(r * ld) + rb * QB ? (size_t)q * QB : qr_al4(r * ld) + rb * QB;
+    Wl = U + qr_al4(usz);                    // [2][p][QB] my partial V^T A (by panel parity)
+    Ys = Wl + 2 * (size_t)p * QB;            // [p][QB] T^T W or T W
+    Gm = Ys + (size_t)p * QB;                // [npan][QB][QB] G = V^T V per panel (column-major, strict upper)
+    Gt = Gm + npan * QB * QB;                // [QB][QB] G of the current panel, row-major
+    diag = Gt + QB * QB;                     // [r]
+    red = diag + qr_al4(r);                  // [2][8][QB] warp partials (by column parity)
+    xrow = red + 2 * 8 * QB;                 // [2][QB] row j0 + j of the panel
+    total = xrow + 2 * QB;
+  }
+};
+
+template <typename C, int RPT>
 __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
     qr_cluster_blocked_kernel(int q, int p, const C* __restrict__ Xg, C* __restrict__ Qg, C* __restrict__ Rg) {
   cg::cluster_group cl = cg::this_cluster();
   const int k = (int)cl.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int r = min(q, p);
   const int rb = (q + JQ - 1) / JQ;
   const int ld = rb | 1;
-  const int ldp = q | 1;                                // panel buffer column stride (all rows)
   const int r0 = k * rb, nr = max(0, min(rb, q - r0));
   const int npan = (r + QB - 1) / QB;
   extern __shared__ __align__(16) unsigned char qbs[];
-  C* X = (C*)qbs;                                       // [p][ld] my rows of X
-  C* U = X + (size_t)p * ld;                            // union: panel [QB][ldp] / my rows of Q [r][ld]
-  const size_t usz = max((size_t)QB * ldp, (size_t)r * ld);
-  C* Wl = U + usz;                                      // [2][QB][p] my partial V^T A (by panel parity)
-  C* Ws = Wl + 2 * (size_t)QB * p;                      // [QB][p] the summed W, then T^T W (or T W)
-  C* Tm = Ws + (size_t)QB * p;                          // [npan][QB][QB] compact-WY factors (column-major)
-  C* diag = Tm + (size_t)npan * QB * QB;                // [r]
-  __shared__ C red[32];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (long long e = threadIdx.x; e < (long long)p * rb; e += blockDim.x) {
-    const int i = (int)(e % rb), c = (int)(e / rb);
-    X[(size_t)c * ld + i] = i < nr ? Xg[(size_t)c * q + r0 + i] : C(0);
-  }
-  for (int t = threadIdx.x; t < npan * QB * QB; t += blockDim.x) Tm[t] = C(0);
+  const QrbLayout Lay(q, p);
+  C* sm = (C*)qbs;
+  C* X = sm + Lay.X;
+  C* P = sm + Lay.P;
+  C* Wl = sm + Lay.Wl;
+  C* Ys = sm + Lay.Ys;
+  C* Gm = sm + Lay.Gm;
+  C* Gt = sm + Lay.Gt;
+  C* diag = sm + Lay.diag;
+  C* red = sm + Lay.red;
+  C* xrow = sm + Lay.xrow;
+  for (int c = 0; c < p; ++c)
+    for (int i = tid; i < rb; i += blockDim.x) X[(size_t)c * ld + i] = i < nr ? Xg[(size_t)c * q + r0 + i] : C(0);
+  for (int t = tid; t < npan * QB * QB; t += blockDim.x) Gm[t] = C(0);
   for (int pn = 0; pn < npan; ++pn) {
-    const int j0 = pn * QB, w = min(QB, r - j0);
-    C* T = Tm + (size_t)pn * QB * QB;
-    C* W = Wl + (size_t)(pn & 1) * QB * p;
+    for (int t = tid; t < QB * QB; t += blockDim.x) Gt[t] = C(0);  // read after the barriers below
+    const int j0 = pn * QB, w = min(QB, r - j0), c1 = j0 + w;
+    C* G = Gm + (size_t)pn * QB * QB;
+    C* W = Wl + (size_t)(pn & 1) * p * QB;
     cl.sync();  // the panel's columns are final in every CTA
-    // gather rows j0..q-1 of the panel columns: PB[cc][g - j0]
-    C* PB = U;
-    for (long long e = threadIdx.x; e < (long long)w * (q - j0); e += blockDim.x) {
-      const int cc = (int)(e / (q - j0)), g = j0 + (int)(e % (q - j0));
-      const int owner = g / rb;
-      const C* src = cl.map_shared_rank(X, (unsigned)owner);
-      PB[(size_t)cc * ldp + (g - j0)] = src[(size_t)(j0 + cc) * ld + (g - owner * rb)];
+    C a[RPT][QB];
+#pragma unroll
+    for (int s = 0; s < RPT; ++s) {
+      const int g = j0 + tid + 256 * s;
+      if (g < q) {
+        const int owner = g / rb;
+        const C* src = cl.map_shared_rank(X, (unsigned)owner) + (g - owner * rb);
+#pragma unroll
+        for (int c = 0; c < QB; ++c) a[s][c] = c < w ? src[(size_t)(j0 + c) * ld] : C(0);
+      } else {
+#pragma unroll
+        for (int c = 0; c < QB; ++c) a[s][c] = C(0);
+      }
     }
-    __syncthreads();
-    // factor the panel (rows >= j0), redundantly in every CTA
-    for (int jj = 0; jj < w; ++jj) {
-      C* pj = PB + (size_t)jj * ldp;
-      const int n = q - j0;  // panel rows
-      C ss = 0;
-      for (int i = jj + (int)threadIdx.x; i < n; i += blockDim.x) ss += pj[i] * pj[i];
-      ss = block_sum(ss, red);
-      const C x0 = pj[jj];
+#pragma unroll
+    for (int jj = 0; jj <= QB; ++jj) {
+      if (jj > w) break;
+      const int buf = jj & 1;
+      C rv[QB];
+#pragma unroll
+      for (int c = 0; c < QB; ++c) rv[c] = C(0);
+#pragma unroll
+      for (int s = 0; s < RPT; ++s) {
+        const int g = j0 + tid + 256 * s;
+        if (g < q) {
+          if (jj < w && g >= j0 + jj) {
+#pragma unroll
+            for (int c = jj; c < QB; ++c) rv[c] += a[s][jj] * a[s][c];
+          }
+          if (jj >= 2 && g >= j0 + jj - 1) {
+#pragma unroll
+            for (int ii = 0; ii < jj - 1; ++ii) rv[ii] += a[s][ii] * a[s][jj - 1];
+          }
+        }
+      }
+      if (jj < w && tid == jj) {
+#pragma unroll
+        for (int c = jj; c < QB; ++c) xrow[buf * QB + c] = a[0][c];
+      }
+      const C sv = warp_reduce16(rv, lane);
+      if (!(lane & 1)) red[(buf * 8 + warp) * QB + (lane >> 1)] = sv;
+      __syncthreads();
+      C tot[QB];
+      {  // lane (w8, grp) loads slots 4 grp .. 4 grp + 3 of warp w8; sum over w8, then broadcast
+        const int w8 = lane & 7, grp = lane >> 3;
+        const C* src = red + (buf * 8 + w8) * QB + grp * 4;
+        C v4[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) v4[t] = src[t];
+#pragma unroll
+        for (int m = 1; m < 8; m <<= 1)
+#pragma unroll
+          for (int t = 0; t < 4; ++t) v4[t] += __shfl_xor_sync(0xffffffffu, v4[t], m);
+#pragma unroll
+        for (int c = 0; c < QB; ++c) tot[c] = __shfl_sync(0xffffffffu, v4[c & 3], (c >> 2) * 8);
+      }
+      if (jj >= 2 && tid == 0) {
+#pragma unroll
+        for (int ii = 0; ii < jj - 1; ++ii) {
+          G[(jj - 1) * QB + ii] = tot[ii];
+          Gt[ii * QB + (jj - 1)] = tot[ii];
+        }
+      }
+      if (jj == w) break;
+      const C ss = tot[jj];
+      const C x0 = xrow[buf * QB + jj];
       const C nrm = sqrt(ss);
       const C alpha = (x0 >= C(0)) ? -nrm : nrm;
       const C v0 = x0 - alpha;
       const C vn2 = ss - x0 * x0 + v0 * v0;
       const bool zero = !(vn2 > C(0));
       const C inv = zero ? C(0) : C(1) / sqrt(vn2);
-      __syncthreads();  // everyone has read pj before it becomes v
-      for (int i = jj + (int)threadIdx.x; i < n; i += blockDim.x) pj[i] = (i == jj ? v0 : pj[i]) * inv;
-      if (threadIdx.x == 0) diag[j0 + jj] = zero ? C(0) : alpha;
-      __syncthreads();
-      // apply H = I - 2 v v^T to the remaining panel columns; z_i = v_i^T v for the T column
-      for (int cc = jj + 1 + warp; cc < w; cc += nw) {
-        C* pc = PB + (size_t)cc * ldp;
-        C d = 0;
-        for (int i = jj + lane; i < n; i += 32) d += pj[i] * pc[i];
-        d = warp_sum(d);
-        for (int i = jj + lane; i < n; i += 32) pc[i] -= C(2) * d * pj[i];
-      }
-      for (int ii = warp; ii < jj; ii += nw) {
-        const C* pi = PB + (size_t)ii * ldp;
-        C d = 0;
-        for (int i = jj + lane; i < n; i += 32) d += pi[i] * pj[i];
-        d = warp_sum(d);
-        if (lane == 0) Ws[ii] = d;  // scratch: z (Ws is free here)
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) {  // T(:jj, jj) = -2 T(:jj, :jj) z, T(jj, jj) = 2 (or 0 for a null reflector)
-        for (int a = 0; a < jj; ++a) {
-          C t = 0;
-          for (int b = a; b < jj; ++b) t += T[b * QB + a] * Ws[b];
-          T[jj * QB + a] = zero ? C(0) : C(-2) * t;
+      if (tid == 0) diag[j0 + jj] = zero ? C(0) : alpha;
+      C dv[QB];
+#pragma unroll
+      for (int c = jj + 1; c < QB; ++c) dv[c] = C(2) * (tot[c] - alpha * xrow[buf * QB + c]) * inv;
+#pragma unroll
+      for (int s = 0; s < RPT; ++s) {
+        const int g = j0 + tid + 256 * s;
+        if (g < q && g >= j0 + jj) {
+          const C vi = (g == j0 + jj ? v0 : a[s][jj]) * inv;
+          a[s][jj] = vi;
+#pragma unroll
+          for (int c = jj + 1; c < QB; ++c) a[s][c] -= dv[c] * vi;
         }
-        T[jj * QB + jj] = zero ? C(0) : C(2);
       }
-      __syncthreads();
     }
-    // my partial W = V^T A over my rows, trailing columns c >= j0 + w
-    const int c1 = j0 + w;
-    for (long long e = threadIdx.x; e < (long long)w * (p - c1); e += blockDim.x) {
-      const int jj = (int)(e % w), c = c1 + (int)(e / w);
-      const C* pj = PB + (size_t)jj * ldp;
+    // V (zero above its diagonal) for the partial products and the trailing update
+#pragma unroll
+    for (int s = 0; s < RPT; ++s) {
+      const int g = j0 + tid + 256 * s;
+      if (g < q) {
+        C t[QB];
+#pragma unroll
+        for (int c = 0; c < QB; ++c) t[c] = (c < w && g - j0 >= c) ? a[s][c] : C(0);
+        st16(P + (size_t)(g - j0) * QB, t);
+      }
+    }
+    __syncthreads();
+    const int i0 = max(0, j0 - r0);
+    for (int c = c1 + tid; c < p; c += blockDim.x) {  // my partial W = V^T A, trailing columns
+      C acc[QB];
+#pragma unroll
+      for (int jj = 0; jj < QB; ++jj) acc[jj] = C(0);
       const C* xc = X + (size_t)c * ld;
-      C d = 0;
-      for (int i = max(0, j0 + jj - r0); i < nr; ++i) d += pj[r0 + i - j0] * xc[i];
-      W[(size_t)jj * p + c] = d;
+      for (int i = i0; i < nr; ++i) {
+        C v[QB];
+        ld16(P + (size_t)(r0 + i - j0) * QB, v);
+        const C x = xc[i];
+#pragma unroll
+        for (int jj = 0; jj < QB; ++jj) acc[jj] += v[jj] * x;
+      }
+      st16(W + (size_t)c * QB, acc);
     }
     cl.sync();  // every CTA has gathered the panel and formed its partial W
-    // write my rows of the factored panel back (R entries above, v below the diagonal)
-    for (long long e = threadIdx.x; e < (long long)w * nr; e += blockDim.x) {
-      const int cc = (int)(e / nr), i = (int)(e % nr);
-      const int g = r0 + i;
-      if (g >= j0) X[(size_t)(j0 + cc) * ld + i] = PB[(size_t)cc * ldp + (g - j0)];
+#pragma unroll
+    for (int s = 0; s < RPT; ++s) {  // my rows of the factored panel (R above, v below the diagonal)
+      const int g = j0 + tid + 256 * s;
+      if (g < q && g >= r0 && g < r0 + nr) {
+#pragma unroll
+        for (int c = 0; c < QB; ++c)
+          if (c < w) X[(size_t)(j0 + c) * ld + (g - r0)] = a[s][c];
+      }
     }
-    // W = sum over CTAs, then Ws = T^T W (column by column)
-    for (int c = c1 + (int)threadIdx.x; c < p; c += blockDim.x) {
+    for (int c = c1 + tid; c < p; c += blockDim.x) {  // W summed over the CTAs; y = T^T w
       C wv[QB];
 #pragma unroll
       for (int jj = 0; jj < QB; ++jj) wv[jj] = C(0);
       for (int t = 0; t < JQ; ++t) {
-        const C* rw = cl.map_shared_rank(W, (unsigned)t);
+        C x[QB];
+        ld16(cl.map_shared_rank(W, (unsigned)t) + (size_t)c * QB, x);
 #pragma unroll
-        for (int jj = 0; jj < QB; ++jj)
-          if (jj < w) wv[jj] += rw[(size_t)jj * p + c];
+        for (int jj = 0; jj < QB; ++jj) wv[jj] += x[jj];
       }
+      // (I/2 + striu(G)^T) y = w, forward substitution by rows of G (Gt row-major)
 #pragma unroll
-      for (int a = 0; a < QB; ++a) {
-        C t = 0;
+      for (int b = 0; b < QB; ++b) {
+        wv[b] *= C(2);
+        C g[QB];
+        ld16(Gt + b * QB, g);
 #pragma unroll
-        for (int b = 0; b <= a; ++b) t += T[a * QB + b] * wv[b];  // (T^T)(a, b) = T(b, a), b <= a
-        if (a < w) Ws[(size_t)a * p + c] = t;
+        for (int a2 = b + 1; a2 < QB; ++a2) wv[a2] -= g[a2] * wv[b];
+      }
+      st16(Ys + (size_t)c * QB, wv);
+    }
+    __syncthreads();
+    for (int i = i0 + (tid & 63); i < nr; i += 64) {  // A(my rows >= j0, c >= c1) -= V y
+      C v[QB];
+      ld16(P + (size_t)(r0 + i - j0) * QB, v);
+      for (int c = c1 + (tid >> 6); c < p; c += 4) {
+        C y[QB];
+        ld16(Ys + (size_t)c * QB, y);
+        C x = X[(size_t)c * ld + i];
+#pragma unroll
+        for (int jj = 0; jj < QB; ++jj) x -= v[jj] * y[jj];
+        X[(size_t)c * ld + i] = x;
       }
     }
     __syncthreads();
-    // A(my rows >= j0, c >= c1) -= V W'
-    if (nr > 0)
-      for (long long e = threadIdx.x; e < (long long)(p - c1) * nr; e += blockDim.x) {
-        const int i = (int)(e % nr), c = c1 + (int)(e / nr);
-        const int g = r0 + i;
-        if (g < j0) continue;
-        C d = 0;  // v_jj has support on panel rows >= jj; above it PB holds R entries
-        const int jn = min(w, g - j0 + 1);
-        for (int jj = 0; jj < jn; ++jj) d += PB[(size_t)jj * ldp + (g - j0)] * Ws[(size_t)jj * p + c];
-        X[(size_t)c * ld + i] -= d;
-      }
-    __syncthreads();
   }
-  cl.sync();  // every CTA is done with the panel buffers before Q reuses the space
-  C* Qm = U;
-  for (long long e = threadIdx.x; e < (long long)r * rb; e += blockDim.x) {
-    const int i = (int)(e % rb), c = (int)(e / rb);
-    Qm[(size_t)c * ld + i] = (r0 + i == c) ? C(1) : C(0);
-  }
-  __syncthreads();
+  cl.sync();  // no CTA reads another's partial W of the last panel any more
+  C* Qm = sm + Lay.Qm;
+  C* Vmy = sm + Lay.Vmy;
+  for (int c = 0; c < r; ++c)
+    for (int i = tid; i < rb; i += blockDim.x) Qm[(size_t)c * ld + i] = (r0 + i == c) ? C(1) : C(0);
   for (int pn = npan - 1; pn >= 0; --pn) {
     const int j0 = pn * QB, w = min(QB, r - j0);
-    const C* T = Tm + (size_t)pn * QB * QB;
-    C* W = Wl + (size_t)(pn & 1) * QB * p;
-    // my partial V^T Q over my rows, columns c >= j0
-    for (long long e = threadIdx.x; e < (long long)w * (r - j0); e += blockDim.x) {
-      const int jj = (int)(e % w), c = j0 + (int)(e / w);
-      const C* vj = X + (size_t)(j0 + jj) * ld;
+    const C* G = Gm + (size_t)pn * QB * QB;
+    C* W = Wl + (size_t)(pn & 1) * p * QB;
+    const int i0 = max(0, j0 - r0);
+    for (int i = tid; i < nr; i += blockDim.x) {  // my rows of V (zero above its diagonal)
+      const int g = r0 + i;
+      C t[QB];
+#pragma unroll
+      for (int jj = 0; jj < QB; ++jj) t[jj] = (jj < w && g >= j0 + jj) ? X[(size_t)(j0 + jj) * ld + i] : C(0);
+      st16(Vmy + (size_t)i * QB, t);
+    }
+    __syncthreads();
+    for (int c = j0 + tid; c < r; c += blockDim.x) {  // my partial W = V^T Q
+      C acc[QB];
+#pragma unroll
+      for (int jj = 0; jj < QB; ++jj) acc[jj] = C(0);
       const C* qc = Qm + (size_t)c * ld;
-      C d = 0;
-      for (int i = max(0, j0 + jj - r0); i < nr; ++i) d += vj[i] * qc[i];
-      W[(size_t)jj * p + c] = d;
+      for (int i = i0; i < nr; ++i) {
+        C v[QB];
+        ld16(Vmy + (size_t)i * QB, v);
+        const C x = qc[i];
+#pragma unroll
+        for (int jj = 0; jj < QB; ++jj) acc[jj] += v[jj] * x;
+      }
+      st16(W + (size_t)c * QB, acc);
     }
     cl.sync();
-    for (int c = j0 + (int)threadIdx.x; c < r; c += blockDim.x) {
+    for (int c = j0 + tid; c < r; c += blockDim.x) {  // y = T w: (I/2 + striu(G)) y = w, back substitution
       C wv[QB];
 #pragma unroll
       for (int jj = 0; jj < QB; ++jj) wv[jj] = C(0);
       for (int t = 0; t < JQ; ++t) {
-        const C* rw = cl.map_shared_rank(W, (unsigned)t);
+        C x[QB];
+        ld16(cl.map_shared_rank(W, (unsigned)t) + (size_t)c * QB, x);
 #pragma unroll
-        for (int jj = 0; jj < QB; ++jj)
-          if (jj < w) wv[jj] += rw[(size_t)jj * p + c];
+        for (int jj = 0; jj < QB; ++jj) wv[jj] += x[jj];
       }
+      // (I/2 + striu(G)) y = w, back substitution by columns of G
 #pragma unroll
-      for (int a = 0; a < QB; ++a) {
-        C t = 0;
+      for (int b = QB - 1; b >= 0; --b) {
+        wv[b] *= C(2);
+        C g[QB];
+        ld16(G + b * QB, g);
 #pragma unroll
-        for (int b = a; b < QB; ++b) t += T[b * QB + a] * wv[b];  // T(a, b), b >= a
-        if (a < w) Ws[(size_t)a * p + c] = t;
+        for (int a2 = 0; a2 < b; ++a2) wv[a2] -= g[a2] * wv[b];
+      }
+      st16(Ys + (size_t)c * QB, wv);
+    }
+    __syncthreads();
+    for (int i = i0 + (tid & 63); i < nr; i += 64) {
+      C v[QB];
+      ld16(Vmy + (size_t)i * QB, v);
+      for (int c = j0 + (tid >> 6); c < r; c += 4) {
+        C y[QB];
+        ld16(Ys + (size_t)c * QB, y);
+        C x = Qm[(size_t)c * ld + i];
+#pragma unroll
+        for (int jj = 0; jj < QB; ++jj) x -= v[jj] * y[jj];
+        Qm[(size_t)c * ld + i] = x;
       }
     }
     __syncthreads();
-    if (nr > 0)
-      for (long long e = threadIdx.x; e < (long long)(r - j0) * nr; e += blockDim.x) {
-        const int i = (int)(e % nr), c = j0 + (int)(e / nr);
-        const int g = r0 + i;
-        if (g < j0) continue;
-        C d = 0;
-        const int jn = min(w, g - j0 + 1);
-        for (int jj = 0; jj < jn; ++jj) d += X[(size_t)(j0 + jj) * ld + i] * Ws[(size_t)jj * p + c];
-        Qm[(size_t)c * ld + i] -= d;
-      }
-    __syncthreads();
   }
-  for (long long e = threadIdx.x; e < (long long)r * nr; e += blockDim.x) {
-    const int i = (int)(e % nr), c = (int)(e / nr);
-    Qg[(size_t)c * q + r0 + i] = diag[c] < C(0) ? -Qm[(size_t)c * ld + i] : Qm[(size_t)c * ld + i];
-  }
-  for (long long e = threadIdx.x; e < (long long)p * nr; e += blockDim.x) {
-    const int i = (int)(e % nr), c = (int)(e / nr);
-    const int gi = r0 + i;
-    if (gi >= r) continue;
-    const C val = gi < c ? X[(size_t)c * ld + i] : (gi == c ? diag[gi] : C(0));
-    Rg[(size_t)c * r + gi] = diag[gi] < C(0) ? -val : val;
-  }
+  for (int c = 0; c < r; ++c)
+    for (int i = tid; i < nr; i += blockDim.x)
+      Qg[(size_t)c * q + r0 + i] = diag[c] < C(0) ? -Qm[(size_t)c * ld + i] : Qm[(size_t)c * ld + i];
+  for (int c = 0; c < p; ++c)
+    for (int i = tid; i < nr; i += blockDim.x) {
+      const int gi = r0 + i;
+      if (gi >= r) continue;
+      const C val = gi < c ? X[(size_t)c * ld + i] : (gi == c ? diag[gi] : C(0));
+      Rg[(size_t)c * r + gi] = diag[gi] < C(0) ? -val : val;
+    }
   cl.sync();  // no CTA leaves while another may still read its shared memory
 }
 
 template <typename C>
 size_t qr_cluster_blocked_smem(int q, int p) {
-  const size_t rb = (q + JQ - 1) / JQ, ld = rb | 1, ldp = (size_t)(q | 1), r = std::min(q, p);
-  const size_t npan = (r + QB - 1) / QB;
-  const size_t usz = std::max((size_t)QB * ldp, r * ld);
-  return ((size_t)p * ld + usz + 3 * (size_t)QB * p + npan * QB * QB + r) * sizeof(C) + 16;
+  return QrbLayout(q, p).total * sizeof(C) + 16;
 }
 
 template <typename C>
@@ -495,12 +652,16 @@ cudaError_t qr_householder(int q, int p, S* X, S* Q, S* R, cudaStream_t st) {
   if constexpr (std::is_same<C, S>::value) {  // rows spread over a cluster when the matrix is large enough
     const size_t bsm = qr_cluster_blocked_smem<C>(q, p);
     if (q >= 128 && p >= 16 && bsm <= 220 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(qr_cluster_blocked_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)bsm);
-      if (e != cudaSuccess) return e;
-      ++tl_launches;
-      qr_cluster_blocked_kernel<C><<<JQ, 256, bsm, st>>>(q, p, X, Q, R);
-      return cudaGetLastError();
+      auto launch = [&](auto kern) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
+        if (e != cudaSuccess) return e;
+        ++tl_launches;
+        kern<<<JQ, 256, bsm, st>>>(q, p, X, Q, R);
+        return cudaGetLastError();
+      };
+      if (q <= 256) return launch(qr_cluster_blocked_kernel<C, 1>);
+      if (q <= 512) return launch(qr_cluster_blocked_kernel<C, 2>);
+      return launch(qr_cluster_blocked_kernel<C, 4>);
     }
     const size_t csm = qr_cluster_smem<C>(q, p);
     if (q >= 128 && p >= 16 && csm <= 200 * 1024) {
