@@ -210,6 +210,17 @@ tt_status tt_fit_stage_times(const tt_fit* h, double out[7]);
  * timed ran in this library's kernels. */
 tt_status tt_fit_launch_count(const tt_fit* h, long long* n);
 
+/* Device memory of the handles comes from a process-wide cache of blocks
+ * binned by size: tt_fit_destroy (and the release of buffers that a handle no
+ * longer needs) returns blocks to it instead of freeing them, and the next
+ * handle of the same shapes reuses them without allocating. At most 64 GiB
+ * stay cached; when an allocation fails the cache of that device is emptied
+ * and the allocation retried. This call frees every cached block of `device`
+ * (all devices if device < 0) and returns the number of bytes it held. Safe to
+ * call at any time: cached blocks are not in use. Host-only otherwise (no
+ * stream work). */
+size_t tt_device_cache_release(int device);
+
 /* The segments a fit with these options uses (Sec. 4.1): n_segments
  * contiguous ranges of >= 2 sites, first[i]..last[i] (0-based, inclusive,
  * arrays of n_segments). Sites are shared out evenly, the first L mod

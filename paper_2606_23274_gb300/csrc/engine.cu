@@ -45,33 +45,116 @@ struct TTError : std::runtime_error {
                     std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_));                                \
   } while (0)
 
-// Device allocations owned by a handle.
+// Process-wide cache of device blocks, binned by device and size (rounded up
+// to 512 bytes). A handle takes a cached block of the size it asks for, or
+// allocates a new one; on allocation failure every cached block of the device
+// is freed and the allocation retried. Released blocks return to the cache
+// (cudaFree would also synchronise the whole device); above a cap on the
+// cached bytes a released block is freed instead. A block is released only
+// after the streams that used it have been synchronised (the preparation
+// streams, the handle's lanes), so a block handed out again is idle.
+struct BlockCache {
+  static constexpr size_t kCap = size_t(64) << 30;
+  std::mutex mu;
+  std::vector<std::pair<std::pair<int, size_t>, void*>> free_blocks;
+  size_t cached = 0;
+  void* take(int dev, size_t bytes) {
+    std::lock_guard<std::mutex> g(mu);
+    for (size_t i = 0; i < free_blocks.size(); ++i)
+      if (free_blocks[i].first == std::make_pair(dev, bytes)) {
+        void* p = free_blocks[i].second;
+        free_blocks[i] = free_blocks.back();
+        free_blocks.pop_back();
+        cached -= bytes;
+        return p;
+      }
+    return nullptr;
+  }
+  void give(int dev, size_t bytes, void* p) {
+    {
+      std::lock_guard<std::mutex> g(mu);
+      if (cached + bytes <= kCap) {
+        free_blocks.push_back({{dev, bytes}, p});
+        cached += bytes;
+        return;
+      }
+    }
+    cudaFree(p);
+  }
+  size_t trim(int dev) {  // dev < 0: every device; returns the bytes freed
+    std::vector<std::pair<std::pair<int, size_t>, void*>> drop;
+    {
+      std::lock_guard<std::mutex> g(mu);
+      for (size_t i = 0; i < free_blocks.size();)
+        if (dev < 0 || free_blocks[i].first.first == dev) {
+          drop.push_back(free_blocks[i]);
+          cached -= free_blocks[i].first.second;
+          free_blocks[i] = free_blocks.back();
+          free_blocks.pop_back();
+        } else {
+          ++i;
+        }
+    }
+    int cur = 0;
+    cudaGetDevice(&cur);
+    size_t bytes = 0;
+    for (auto& d : drop) {
+      cudaSetDevice(d.first.first);
+      cudaFree(d.second);
+      bytes += d.first.second;
+    }
+    cudaSetDevice(cur);
+    return bytes;
+  }
+};
+
+BlockCache& block_cache() {
+  static BlockCache* c = new BlockCache;  // lives for the process; the driver reclaims device memory at exit
+  return *c;
+}
+
+// Device allocations owned by a handle (from the block cache).
 struct DevPool {
-  std::vector<void*> ptrs;
+  struct Blk {
+    void* p;
+    size_t bytes;
+    int dev;
+  };
+  std::vector<Blk> blks;
   uint32_t fault = 0;
   template <typename T>
   T* alloc(size_t n) {
     if (fault & TT_FAULT_ALLOC_FAIL) throw TTError(TT_ERR_OUT_OF_MEMORY, "injected allocation failure");
-    void* p = nullptr;
     if (n == 0) n = 1;
-    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      throw TTError(TT_ERR_OUT_OF_MEMORY, "cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes failed");
+    const size_t bytes = (n * sizeof(T) + 511) & ~(size_t)511;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    void* p = block_cache().take(dev, bytes);
+    if (!p) {
+      cudaError_t e = cudaMalloc(&p, bytes);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        block_cache().trim(dev);
+        e = cudaMalloc(&p, bytes);
+      }
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw TTError(TT_ERR_OUT_OF_MEMORY, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+      }
     }
-    ptrs.push_back(p);
+    blks.push_back({p, bytes, dev});
     return (T*)p;
   }
   void release(void* p) {
-    for (auto& q : ptrs)
-      if (q == p) {
-        cudaFree(q);
-        q = nullptr;
+    for (auto& b : blks)
+      if (b.p == p) {
+        block_cache().give(b.dev, b.bytes, b.p);
+        b.p = nullptr;
       }
   }
   ~DevPool() {
-    for (void* p : ptrs)
-      if (p) cudaFree(p);
+    for (auto& b : blks)
+      if (b.p) block_cache().give(b.dev, b.bytes, b.p);
   }
 };
 
@@ -1109,6 +1192,8 @@ void rebuild_chain(tt_fit* h) {
   Dims& D = h->D;
   const int L = D.L;
   CK(cudaStreamSynchronize(W(h).st));
+  for (auto* w : lanes(h))
+    if (w->st) CK(cudaStreamSynchronize(w->st));
   for (void* p : h->chain_bufs) h->pool.release(p);
   h->chain_bufs.clear();
   build_operands<T>(h);
@@ -1614,8 +1699,10 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
         all_envs<double>(h);
       }
     }
-    for (int j = 0; j < L; ++j) h->pool.release(C0[j]);
     CK(cudaStreamSynchronize(W(h).st));
+    for (auto* w : lanes(h))
+    if (w->st) CK(cudaStreamSynchronize(w->st));
+    for (int j = 0; j < L; ++j) h->pool.release(C0[j]);
     *out = h;
     return TT_OK;
   } catch (const TTError& e) {
@@ -1872,6 +1959,8 @@ tt_status tt_fit_launch_count(const tt_fit* h, long long* n) {
   *n = h->launches;
   return TT_OK;
 }
+
+size_t tt_device_cache_release(int device) { return block_cache().trim(device); }
 
 void tt_fit_destroy(tt_fit* h) {
   if (!h) return;

@@ -94,6 +94,8 @@ def load():
                                     ct.c_int, ct.c_int, ct.c_int, ct.c_void_p, ct.POINTER(tt_mpo_desc),
                                     ct.POINTER(tt_mpo_desc), ct.POINTER(ct.c_double)]
         lib.tt_mpo_grad.restype = ct.c_int
+        lib.tt_device_cache_release.argtypes = [ct.c_int]
+        lib.tt_device_cache_release.restype = ct.c_size_t
         _lib = lib
     return _lib
 
@@ -294,6 +296,12 @@ def tt_svd_truncated(M, chi_max: int, tau_rel: float = 0.0, stream=None):
                                 Vt.data_ptr(), ct.byref(k), ct.c_void_p(stream.cuda_stream))
     _check(code, None, "tt_svd_truncated")
     return U, S, Vt, k.value
+
+
+def tt_device_cache_release(device: int = -1) -> int:
+    """Frees the device blocks cached for reuse by later fits (all devices if
+    device < 0); returns the bytes freed (tt_device_cache_release)."""
+    return int(load().tt_device_cache_release(int(device)))
 
 
 def tt_fit_sweep(fit: "Fit", n_sweeps: int):

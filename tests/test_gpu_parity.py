@@ -340,3 +340,25 @@ def test_fp32_factorisation_of_a_tiny_first_window(precision, fast):
     tol = 1e-3 if precision in ("tf32x3", "fp32") else 1e-6
     assert abs(r["norm2_C"] - r0["norm2_C"]) <= tol * r0["norm2_C"]
     assert abs(mpo_norm(C) ** 2 - r["norm2_C"]) <= 10 * tol * r["norm2_C"]
+
+
+def test_block_cache_reuse_and_release():
+    """Handles take their device blocks from a process-wide cache. A fit of
+    (A, B) on fresh blocks, then a fit of other inputs with the same shapes
+    (its blocks go back to the cache holding its data), then (A, B) again on
+    those reused blocks: the two (A, B) results are bitwise equal, so nothing
+    reads a block before writing it. Releasing the cache frees what it held."""
+    A = kron_sum_mpo(10, 8, 2, 0)
+    B = kron_sum_mpo(10, 8, 2, 1)
+    A2 = kron_sum_mpo(10, 8, 2, 5)
+    B2 = kron_sum_mpo(10, 8, 2, 6)
+    kw = dict(precision="tf32x3", update="rsvd", seed=3)
+    ttfit.tt_device_cache_release(-1)
+    C0, r0, _, _ = _gpu_fit(A, B, 24, 0.0, 3, **kw)
+    _gpu_fit(A2, B2, 24, 0.0, 3, **kw)
+    C1, r1, _, _ = _gpu_fit(A, B, 24, 0.0, 3, **kw)
+    for a, b in zip(C0, C1):
+        assert np.array_equal(a, b)
+    assert [r["norm2_C"] for r in r0] == [r["norm2_C"] for r in r1]
+    assert ttfit.tt_device_cache_release(-1) > 0
+    assert ttfit.tt_device_cache_release(-1) == 0
