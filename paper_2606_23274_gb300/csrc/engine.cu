@@ -346,8 +346,11 @@ struct Prep {
   std::vector<void*> dead;
 };
 
+// The FP64 path keeps FP64 arithmetic here; the others factorise in df32
+// arithmetic (rounding ~1e-14, below what their sweeps resolve).
 void prep_qr(tt_fit* h, Prep& P, int q, int p) {
-  CK(qr_householder<double, double>(q, p, P.X, P.Q, P.R, P.st));
+  if (h->precision == TT_PREC_FP64) CK(qr_householder<double, double>(q, p, P.X, P.Q, P.R, P.st));
+  else CK(qr_householder_df32(q, p, P.X, P.Q, P.R, P.st));
 }
 
 void prep_gemm(tt_fit* h, Prep& P, const GemmArgs<double>& g) {
@@ -1639,7 +1642,8 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
           const int q = D.ds[j] * D.dt[j] * cbond[j + 1], p = cbond[j];
           double* R = h->pool.alloc<double>((size_t)p * p);
           double* Q = h->pool.alloc<double>((size_t)q * p);
-          CK(qr_householder<double, double>(q, p, C0[j], Q, R, sj));
+          if (h->precision == TT_PREC_FP64) CK(qr_householder<double, double>(q, p, C0[j], Q, R, sj));
+          else CK(qr_householder_df32(q, p, C0[j], Q, R, sj));
           dead.push_back(C0[j]);
           dead.push_back(R);
           C0[j] = Q;

@@ -5,6 +5,8 @@
 // It serves the FP64 path, the double-FP32 (df32) path that reaches FP64-class
 // accuracy on the FP32 pipes, and the plain-FP32 baseline; the tensor-core
 // path lives in gemm_tc.cu.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -140,8 +142,12 @@ cudaError_t gemm_simt(const GemmArgs<T>& g, T* ws, size_t ws_elems, int sm_count
   int tiles = gm * gn;
   int splits = 1;
   // split K while the grid covers fewer than two waves of the SMs and each
-  // split keeps at least 256 k-steps
-  while (tiles * splits < 2 * sm_count && g.K / (splits * 2) >= 256 &&
+  // split keeps at least kmin k-steps: a tile's time is bound by its SM's
+  // arithmetic rate, which for FP64 is 1/64 of the FP32 rate on this GPU (and
+  // a df32 multiply-add takes 15 FP32 instructions), so the small GEMMs of
+  // those types split deeper
+  const int kmin = std::is_same<T, double>::value ? 16 : (std::is_same<T, df32>::value ? 64 : 256);
+  while (tiles * splits < 2 * sm_count && g.K / (splits * 2) >= kmin &&
          (size_t)(splits * 2) * g.M * g.N <= ws_elems)
     splits *= 2;
   int kps = (g.K + splits - 1) / splits;

@@ -58,6 +58,10 @@ cudaError_t philox_fill(F* out, long long count, uint64_t seed, uint64_t stream,
 // diag(R) >= 0. One CTA. C: arithmetic type, S: storage type.
 template <typename C, typename S>
 cudaError_t qr_householder(int q, int p, S* X, S* Q, S* R, cudaStream_t st);
+// The same factorisation of FP64 storage in double-FP32 arithmetic (about 4x
+// the FP64 rate of this GPU, rounding ~1e-14 instead of 1e-16); shapes the
+// cluster kernel does not take run in FP64.
+cudaError_t qr_householder_df32(int q, int p, double* X, double* Q, double* R, cudaStream_t st);
 
 // One-sided Jacobi SVD of the q x p column-major W (q >= p, ld q; overwritten):
 // W = U diag(S) V^T with U (q x p, col-major), S sorted descending, V (p x p,

@@ -283,9 +283,40 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
 // panel in the factorisation, one in the formation of Q.
 constexpr int QB = 16;
 
+// Element helpers of the blocked QR for float, double and df32 arithmetic
+// (df32: the scalar square root and reciprocal of a column go through FP64).
+__device__ __forceinline__ float qsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double qsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ df32 qsqrt(df32 x) { return df32(sqrt((double)x)); }
+__device__ __forceinline__ float qrcp(float x) { return 1.0f / x; }
+__device__ __forceinline__ double qrcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ df32 qrcp(df32 x) { return df32(1.0 / (double)x); }
+__device__ __forceinline__ bool qneg(float x) { return x < 0.0f; }
+__device__ __forceinline__ bool qneg(double x) { return x < 0.0; }
+__device__ __forceinline__ bool qneg(df32 x) { return x.hi < 0.0f; }  // a normalised pair has the sign of hi
+__device__ __forceinline__ bool qpos(float x) { return x > 0.0f; }
+__device__ __forceinline__ bool qpos(double x) { return x > 0.0; }
+__device__ __forceinline__ bool qpos(df32 x) { return x.hi > 0.0f; }
+template <typename C>
+__device__ __forceinline__ C qshfl_xor(C v, int m) {
+  return __shfl_xor_sync(0xffffffffu, v, m);
+}
+template <>
+__device__ __forceinline__ df32 qshfl_xor<df32>(df32 v, int m) {
+  return df32(__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m));
+}
+template <typename C>
+__device__ __forceinline__ C qshfl(C v, int src) {
+  return __shfl_sync(0xffffffffu, v, src);
+}
+template <>
+__device__ __forceinline__ df32 qshfl<df32>(df32 v, int src) {
+  return df32(__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src));
+}
+
 template <typename C>
 __device__ __forceinline__ void ld16(const C* __restrict__ src, C (&v)[QB]) {
-  if constexpr (sizeof(C) == 4) {
+  if constexpr (std::is_same<C, float>::value) {
     const float4* s4 = reinterpret_cast<const float4*>(src);
 #pragma unroll
     for (int t = 0; t < QB / 4; ++t) {
@@ -295,7 +326,7 @@ __device__ __forceinline__ void ld16(const C* __restrict__ src, C (&v)[QB]) {
       v[4 * t + 2] = x.z;
       v[4 * t + 3] = x.w;
     }
-  } else {
+  } else if constexpr (std::is_same<C, double>::value) {
     const double2* s2 = reinterpret_cast<const double2*>(src);
 #pragma unroll
     for (int t = 0; t < QB / 2; ++t) {
@@ -303,19 +334,31 @@ __device__ __forceinline__ void ld16(const C* __restrict__ src, C (&v)[QB]) {
       v[2 * t] = x.x;
       v[2 * t + 1] = x.y;
     }
+  } else {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+    for (int t = 0; t < QB / 2; ++t) {
+      const float4 x = s4[t];
+      v[2 * t] = df32(x.x, x.y);
+      v[2 * t + 1] = df32(x.z, x.w);
+    }
   }
 }
 
 template <typename C>
 __device__ __forceinline__ void st16(C* __restrict__ dst, const C (&v)[QB]) {
-  if constexpr (sizeof(C) == 4) {
+  if constexpr (std::is_same<C, float>::value) {
     float4* d4 = reinterpret_cast<float4*>(dst);
 #pragma unroll
     for (int t = 0; t < QB / 4; ++t) d4[t] = make_float4(v[4 * t], v[4 * t + 1], v[4 * t + 2], v[4 * t + 3]);
-  } else {
+  } else if constexpr (std::is_same<C, double>::value) {
     double2* d2 = reinterpret_cast<double2*>(dst);
 #pragma unroll
     for (int t = 0; t < QB / 2; ++t) d2[t] = make_double2(v[2 * t], v[2 * t + 1]);
+  } else {
+    float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+    for (int t = 0; t < QB / 2; ++t) d4[t] = make_float4(v[2 * t].hi, v[2 * t].lo, v[2 * t + 1].hi, v[2 * t + 1].lo);
   }
 }
 
@@ -330,10 +373,10 @@ __device__ __forceinline__ C warp_reduce16(C (&v)[QB], int lane) {
     for (int t = 0; t < h; ++t) {
       const C send = hi ? v[t] : v[t + h];
       const C keep = hi ? v[t + h] : v[t];
-      v[t] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+      v[t] = keep + qshfl_xor(send, m);
     }
   }
-  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+  return v[0] + qshfl_xor(v[0], 1);
 }
 
 __host__ __device__ constexpr size_t qr_al4(size_t n) { return (n + 3) & ~(size_t)3; }
@@ -360,9 +403,9 @@ struct QrbLayout {
   }
 };
 
-template <typename C, int RPT>
+template <typename S, typename C, int RPT>
 __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
-    qr_cluster_blocked_kernel(int q, int p, const C* __restrict__ Xg, C* __restrict__ Qg, C* __restrict__ Rg) {
+    qr_cluster_blocked_kernel(int q, int p, const S* __restrict__ Xg, S* __restrict__ Qg, S* __restrict__ Rg) {
   cg::cluster_group cl = cg::this_cluster();
   const int k = (int)cl.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -384,7 +427,7 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
   C* red = sm + Lay.red;
   C* xrow = sm + Lay.xrow;
   for (int c = 0; c < p; ++c)
-    for (int i = tid; i < rb; i += blockDim.x) X[(size_t)c * ld + i] = i < nr ? Xg[(size_t)c * q + r0 + i] : C(0);
+    for (int i = tid; i < rb; i += blockDim.x) X[(size_t)c * ld + i] = i < nr ? C(Xg[(size_t)c * q + r0 + i]) : C(0);
   for (int t = tid; t < npan * QB * QB; t += blockDim.x) Gm[t] = C(0);
   for (int pn = 0; pn < npan; ++pn) {
     for (int t = tid; t < QB * QB; t += blockDim.x) Gt[t] = C(0);  // read after the barriers below
@@ -419,11 +462,11 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
         if (g < q) {
           if (jj < w && g >= j0 + jj) {
 #pragma unroll
-            for (int c = jj; c < QB; ++c) rv[c] += a[s][jj] * a[s][c];
+            for (int c = jj; c < QB; ++c) rv[c] = madd(a[s][jj], a[s][c], rv[c]);
           }
           if (jj >= 2 && g >= j0 + jj - 1) {
 #pragma unroll
-            for (int ii = 0; ii < jj - 1; ++ii) rv[ii] += a[s][ii] * a[s][jj - 1];
+            for (int ii = 0; ii < jj - 1; ++ii) rv[ii] = madd(a[s][ii], a[s][jj - 1], rv[ii]);
           }
         }
       }
@@ -444,9 +487,9 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
 #pragma unroll
         for (int m = 1; m < 8; m <<= 1)
 #pragma unroll
-          for (int t = 0; t < 4; ++t) v4[t] += __shfl_xor_sync(0xffffffffu, v4[t], m);
+          for (int t = 0; t < 4; ++t) v4[t] = v4[t] + qshfl_xor(v4[t], m);
 #pragma unroll
-        for (int c = 0; c < QB; ++c) tot[c] = __shfl_sync(0xffffffffu, v4[c & 3], (c >> 2) * 8);
+        for (int c = 0; c < QB; ++c) tot[c] = qshfl(v4[c & 3], (c >> 2) * 8);
       }
       if (jj >= 2 && tid == 0) {
 #pragma unroll
@@ -458,16 +501,16 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
       if (jj == w) break;
       const C ss = tot[jj];
       const C x0 = xrow[buf * QB + jj];
-      const C nrm = sqrt(ss);
-      const C alpha = (x0 >= C(0)) ? -nrm : nrm;
+      const C nrm = qsqrt(ss);
+      const C alpha = qneg(x0) ? nrm : -nrm;
       const C v0 = x0 - alpha;
-      const C vn2 = ss - x0 * x0 + v0 * v0;
-      const bool zero = !(vn2 > C(0));
-      const C inv = zero ? C(0) : C(1) / sqrt(vn2);
+      const C vn2 = madd(v0, v0, madd(-x0, x0, ss));
+      const bool zero = !qpos(vn2);
+      const C inv = zero ? C(0) : qrcp(qsqrt(vn2));
       if (tid == 0) diag[j0 + jj] = zero ? C(0) : alpha;
       C dv[QB];
 #pragma unroll
-      for (int c = jj + 1; c < QB; ++c) dv[c] = C(2) * (tot[c] - alpha * xrow[buf * QB + c]) * inv;
+      for (int c = jj + 1; c < QB; ++c) dv[c] = C(2) * (madd(-alpha, xrow[buf * QB + c], tot[c]) * inv);
 #pragma unroll
       for (int s = 0; s < RPT; ++s) {
         const int g = j0 + tid + 256 * s;
@@ -475,7 +518,7 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
           const C vi = (g == j0 + jj ? v0 : a[s][jj]) * inv;
           a[s][jj] = vi;
 #pragma unroll
-          for (int c = jj + 1; c < QB; ++c) a[s][c] -= dv[c] * vi;
+          for (int c = jj + 1; c < QB; ++c) a[s][c] = madd(-dv[c], vi, a[s][c]);
         }
       }
     }
@@ -502,7 +545,7 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
         ld16(P + (size_t)(r0 + i - j0) * QB, v);
         const C x = xc[i];
 #pragma unroll
-        for (int jj = 0; jj < QB; ++jj) acc[jj] += v[jj] * x;
+        for (int jj = 0; jj < QB; ++jj) acc[jj] = madd(v[jj], x, acc[jj]);
       }
       st16(W + (size_t)c * QB, acc);
     }
@@ -524,16 +567,16 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
         C x[QB];
         ld16(cl.map_shared_rank(W, (unsigned)t) + (size_t)c * QB, x);
 #pragma unroll
-        for (int jj = 0; jj < QB; ++jj) wv[jj] += x[jj];
+        for (int jj = 0; jj < QB; ++jj) wv[jj] = wv[jj] + x[jj];
       }
       // (I/2 + striu(G)^T) y = w, forward substitution by rows of G (Gt row-major)
 #pragma unroll
       for (int b = 0; b < QB; ++b) {
-        wv[b] *= C(2);
+        wv[b] = C(2) * wv[b];
         C g[QB];
         ld16(Gt + b * QB, g);
 #pragma unroll
-        for (int a2 = b + 1; a2 < QB; ++a2) wv[a2] -= g[a2] * wv[b];
+        for (int a2 = b + 1; a2 < QB; ++a2) wv[a2] = madd(-g[a2], wv[b], wv[a2]);
       }
       st16(Ys + (size_t)c * QB, wv);
     }
@@ -546,7 +589,7 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
         ld16(Ys + (size_t)c * QB, y);
         C x = X[(size_t)c * ld + i];
 #pragma unroll
-        for (int jj = 0; jj < QB; ++jj) x -= v[jj] * y[jj];
+        for (int jj = 0; jj < QB; ++jj) x = madd(-v[jj], y[jj], x);
         X[(size_t)c * ld + i] = x;
       }
     }
@@ -580,7 +623,7 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
         ld16(Vmy + (size_t)i * QB, v);
         const C x = qc[i];
 #pragma unroll
-        for (int jj = 0; jj < QB; ++jj) acc[jj] += v[jj] * x;
+        for (int jj = 0; jj < QB; ++jj) acc[jj] = madd(v[jj], x, acc[jj]);
       }
       st16(W + (size_t)c * QB, acc);
     }
@@ -593,16 +636,16 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
         C x[QB];
         ld16(cl.map_shared_rank(W, (unsigned)t) + (size_t)c * QB, x);
 #pragma unroll
-        for (int jj = 0; jj < QB; ++jj) wv[jj] += x[jj];
+        for (int jj = 0; jj < QB; ++jj) wv[jj] = wv[jj] + x[jj];
       }
       // (I/2 + striu(G)) y = w, back substitution by columns of G
 #pragma unroll
       for (int b = QB - 1; b >= 0; --b) {
-        wv[b] *= C(2);
+        wv[b] = C(2) * wv[b];
         C g[QB];
         ld16(G + b * QB, g);
 #pragma unroll
-        for (int a2 = 0; a2 < b; ++a2) wv[a2] -= g[a2] * wv[b];
+        for (int a2 = 0; a2 < b; ++a2) wv[a2] = madd(-g[a2], wv[b], wv[a2]);
       }
       st16(Ys + (size_t)c * QB, wv);
     }
@@ -615,7 +658,7 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
         ld16(Ys + (size_t)c * QB, y);
         C x = Qm[(size_t)c * ld + i];
 #pragma unroll
-        for (int jj = 0; jj < QB; ++jj) x -= v[jj] * y[jj];
+        for (int jj = 0; jj < QB; ++jj) x = madd(-v[jj], y[jj], x);
         Qm[(size_t)c * ld + i] = x;
       }
     }
@@ -623,13 +666,13 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
   }
   for (int c = 0; c < r; ++c)
     for (int i = tid; i < nr; i += blockDim.x)
-      Qg[(size_t)c * q + r0 + i] = diag[c] < C(0) ? -Qm[(size_t)c * ld + i] : Qm[(size_t)c * ld + i];
+      Qg[(size_t)c * q + r0 + i] = (S)(qneg(diag[c]) ? -Qm[(size_t)c * ld + i] : Qm[(size_t)c * ld + i]);
   for (int c = 0; c < p; ++c)
     for (int i = tid; i < nr; i += blockDim.x) {
       const int gi = r0 + i;
       if (gi >= r) continue;
       const C val = gi < c ? X[(size_t)c * ld + i] : (gi == c ? diag[gi] : C(0));
-      Rg[(size_t)c * r + gi] = diag[gi] < C(0) ? -val : val;
+      Rg[(size_t)c * r + gi] = (S)(qneg(diag[gi]) ? -val : val);
     }
   cl.sync();  // no CTA leaves while another may still read its shared memory
 }
@@ -659,9 +702,9 @@ cudaError_t qr_householder(int q, int p, S* X, S* Q, S* R, cudaStream_t st) {
         kern<<<JQ, 256, bsm, st>>>(q, p, X, Q, R);
         return cudaGetLastError();
       };
-      if (q <= 256) return launch(qr_cluster_blocked_kernel<C, 1>);
-      if (q <= 512) return launch(qr_cluster_blocked_kernel<C, 2>);
-      return launch(qr_cluster_blocked_kernel<C, 4>);
+      if (q <= 256) return launch(qr_cluster_blocked_kernel<C, C, 1>);
+      if (q <= 512) return launch(qr_cluster_blocked_kernel<C, C, 2>);
+      return launch(qr_cluster_blocked_kernel<C, C, 4>);
     }
     const size_t csm = qr_cluster_smem<C>(q, p);
     if (q >= 128 && p >= 16 && csm <= 200 * 1024) {
@@ -684,6 +727,22 @@ cudaError_t qr_householder(int q, int p, S* X, S* Q, S* R, cudaStream_t st) {
   return cudaGetLastError();
 }
 template cudaError_t qr_householder<double, double>(int, int, double*, double*, double*, cudaStream_t);
+
+cudaError_t qr_householder_df32(int q, int p, double* X, double* Q, double* R, cudaStream_t st) {
+  if (q <= 0 || p <= 0) return cudaSuccess;
+  const size_t bsm = qr_cluster_blocked_smem<df32>(q, p);
+  if (q < 128 || p < 16 || q > 1024 || bsm > 220 * 1024) return qr_householder<double, double>(q, p, X, Q, R, st);
+  auto launch = [&](auto kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
+    if (e != cudaSuccess) return e;
+    ++tl_launches;
+    kern<<<JQ, 256, bsm, st>>>(q, p, X, Q, R);
+    return cudaGetLastError();
+  };
+  if (q <= 256) return launch(qr_cluster_blocked_kernel<double, df32, 1>);
+  if (q <= 512) return launch(qr_cluster_blocked_kernel<double, df32, 2>);
+  return launch(qr_cluster_blocked_kernel<double, df32, 4>);
+}
 template cudaError_t qr_householder<float, float>(int, int, float*, float*, float*, cudaStream_t);
 
 // ---------------------------------------------------------------------------
