@@ -158,6 +158,7 @@ def run_fit(ttfit, Ain, Bin, schedule, seed, dev, stream, chi=CHI, lo_sweeps=LO_
                       "switch": ev["s0"].elapsed_time(ev["s1"]) if switched else 0.0,
                       "export": ev["r0"].elapsed_time(ev["r1"])}
     launches = f.launch_count()
+    rep["jacobi_max_sweeps"] = f.jacobi_sweeps()
     rep["bonds"] = f.bonds()
     f.destroy()
     rep["history"] = history
@@ -332,6 +333,7 @@ def native(args):
                                     for k in ("create", "switch", "export")},
         "roofline": roof, "clocks": clk, "e2e": e2e, "gpu_launches": int(sum(r[5] for r in results)), "gpu_launches_per_step": int(launches),
         "fits_per_s": round(world / t_step, 4), "wall_s_timed": round(wall, 2),
+        "jacobi_max_sweeps": rep.get("jacobi_max_sweeps"),
     }
     if rank == 0 and not args.no_cpu_baseline and args.workload == WORKLOAD:
         out["cpu_baseline"] = cpu_baseline(sweeps)

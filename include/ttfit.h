@@ -221,6 +221,12 @@ tt_status tt_fit_launch_count(const tt_fit* h, long long* n);
  * stream work). */
 size_t tt_device_cache_release(int device);
 
+/* The largest number of Jacobi sweeps that one singular value decomposition of
+ * a two-site tensor (or of its randomized sketch) needed since tt_fit_create,
+ * as of the last window that completed. A diagnostic of the factorisation
+ * stage; the sweeps stop when no column pair is rotated. */
+tt_status tt_fit_jacobi_sweeps(const tt_fit* h, int* max_sweeps);
+
 /* The segments a fit with these options uses (Sec. 4.1): n_segments
  * contiguous ranges of >= 2 sites, first[i]..last[i] (0-based, inclusive,
  * arrays of n_segments). Sites are shared out evenly, the first L mod

@@ -924,7 +924,7 @@ struct Sweeper {
     CK(cudaEventRecord(W(h).ev[4], W(h).st));
     CK(cudaMemcpyAsync(W(h).hk, W(h).dk, sizeof(int), cudaMemcpyDeviceToHost, W(h).st));
     CK(cudaMemcpyAsync(W(h).hdinfo, W(h).ddinfo, 2 * sizeof(double), cudaMemcpyDeviceToHost, W(h).st));
-    CK(cudaMemcpyAsync(W(h).herrw, W(h).errw, sizeof(uint32_t), cudaMemcpyDeviceToHost, W(h).st));
+    CK(cudaMemcpyAsync(W(h).herrw, W(h).errw, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, W(h).st));
     CK(cudaStreamSynchronize(W(h).st));
     add(2, 0, 1);
     add(0, 1, 2);
@@ -1293,7 +1293,7 @@ void vidal_init(tt_fit* h) {
       const int p = factorize<T, F>(h, m, n, 0, j + 1);
       CK(truncate_rule<F>((const F*)W(h).fS, p, W(h).dnorm, 0.0, p, h->cutoff, W(h).dk, W(h).ddinfo, W(h).st));
       CK(cudaMemcpyAsync(W(h).hk, W(h).dk, sizeof(int), cudaMemcpyDeviceToHost, W(h).st));
-      CK(cudaMemcpyAsync(W(h).herrw, W(h).errw, sizeof(uint32_t), cudaMemcpyDeviceToHost, W(h).st));
+      CK(cudaMemcpyAsync(W(h).herrw, W(h).errw, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, W(h).st));
       CK(cudaStreamSynchronize(W(h).st));
       check_errw(h, "the inverse-gauge initialisation");
       const int k = *W(h).hk;
@@ -1965,6 +1965,15 @@ tt_status tt_fit_launch_count(const tt_fit* h, long long* n) {
 }
 
 size_t tt_device_cache_release(int device) { return block_cache().trim(device); }
+
+tt_status tt_fit_jacobi_sweeps(const tt_fit* h, int* max_sweeps) {
+  if (!h || !max_sweeps) return TT_ERR_INVALID_ARGUMENT;
+  int m = 0;
+  for (Work* w : lanes(const_cast<tt_fit*>(h)))
+    if (w->herrw) m = std::max(m, (int)w->herrw[1]);
+  *max_sweeps = m;
+  return TT_OK;
+}
 
 void tt_fit_destroy(tt_fit* h) {
   if (!h) return;

@@ -283,14 +283,26 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
 // panel in the factorisation, one in the formation of Q.
 constexpr int QB = 16;
 
-// Element helpers of the blocked QR for float, double and df32 arithmetic
-// (df32: the scalar square root and reciprocal of a column go through FP64).
+// Element helpers of the blocked QR for float, double and df32 arithmetic.
+// The df32 square root and reciprocal start from the FP32 result of the high
+// word and take one Newton step in df32 arithmetic, which doubles the number
+// of correct bits (Dekker, Numer. Math. 18 (1971); Karp and Markstein, ACM
+// TOMS 23 (1997)): sqrt(x) = s + (x - s^2) / (2 s), 1/x = r + r (1 - x r).
 __device__ __forceinline__ float qsqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double qsqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ df32 qsqrt(df32 x) { return df32(sqrt((double)x)); }
+__device__ __forceinline__ df32 qsqrt(df32 x) {
+  if (!(x.hi > 0.0f)) return df32(0.0f, 0.0f);
+  const float s = sqrtf(x.hi);
+  const df32 e = madd(df32(-s, 0.0f), df32(s, 0.0f), x);  // x - s^2
+  return two_sum(s, e.hi * (0.5f / s));
+}
 __device__ __forceinline__ float qrcp(float x) { return 1.0f / x; }
 __device__ __forceinline__ double qrcp(double x) { return 1.0 / x; }
-__device__ __forceinline__ df32 qrcp(df32 x) { return df32(1.0 / (double)x); }
+__device__ __forceinline__ df32 qrcp(df32 x) {
+  const df32 r(1.0f / x.hi, 0.0f);
+  const df32 e = madd(-x, r, df32(1.0f, 0.0f));  // 1 - x r
+  return madd(r, e, r);
+}
 __device__ __forceinline__ bool qneg(float x) { return x < 0.0f; }
 __device__ __forceinline__ bool qneg(double x) { return x < 0.0; }
 __device__ __forceinline__ bool qneg(df32 x) { return x.hi < 0.0f; }  // a normalised pair has the sign of hi

@@ -94,6 +94,8 @@ def load():
                                     ct.c_int, ct.c_int, ct.c_int, ct.c_void_p, ct.POINTER(tt_mpo_desc),
                                     ct.POINTER(tt_mpo_desc), ct.POINTER(ct.c_double)]
         lib.tt_mpo_grad.restype = ct.c_int
+        lib.tt_fit_jacobi_sweeps.argtypes = [ct.c_void_p, ct.POINTER(ct.c_int)]
+        lib.tt_fit_jacobi_sweeps.restype = ct.c_int
         lib.tt_device_cache_release.argtypes = [ct.c_int]
         lib.tt_device_cache_release.restype = ct.c_size_t
         _lib = lib
@@ -388,6 +390,11 @@ class Fit:
         _check(load().tt_fit_launch_count(self.h, ct.byref(n)), self.h, "tt_fit_launch_count")
         return int(n.value)
 
+    def jacobi_sweeps(self) -> int:
+        """Most Jacobi sweeps one factorisation has needed (tt_fit_jacobi_sweeps)."""
+        n = ct.c_int(0)
+        _check(load().tt_fit_jacobi_sweeps(self.h, ct.byref(n)), self.h, "tt_fit_jacobi_sweeps")
+        return n.value
     def destroy(self):
         if self.h is not None and self.h.value:
             load().tt_fit_destroy(self.h)
