@@ -982,13 +982,15 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(1024)
   const int P = 2 * JC;
   const bool want_v = Vo != nullptr;
   const int rows = q + (want_v ? p : 0);  // a column: its w part, then its v part
+  constexpr int V16 = 16 / (int)sizeof(C);
+  const int ld = (rows + V16 - 1) / V16 * V16;            // column stride: every column 16-byte aligned
   extern __shared__ __align__(16) unsigned char jcs[];
-  C* buf = (C*)jcs;                                       // [2 buffers][2 slots][b][rows]
-  int* ids = (int*)(buf + (size_t)4 * b * rows);          // [2 buffers][2 slots][b] global column or -1
+  C* buf = (C*)jcs;                                       // [2 buffers][2 slots][b][ld]
+  int* ids = (int*)(buf + (size_t)4 * b * ld);            // [2 buffers][2 slots][b] global column or -1
   C* nrm = (C*)(ids + 4 * b + 4);                         // [2 slots][b] final column norms (16-byte aligned)
   __shared__ int flag[2];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  auto col = [&](int bi, int sl, int k) { return buf + ((size_t)(bi * 2 + sl) * b + k) * rows; };
+  auto col = [&](int bi, int sl, int k) { return buf + ((size_t)(bi * 2 + sl) * b + k) * ld; };
   auto cid = [&](int bi, int sl, int k) -> int& { return ids[(bi * 2 + sl) * b + k]; };
   const C tol2 = (C)(tol * tol);
 
@@ -999,9 +1001,9 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(1024)
       const int gid = blk * b + k;
       if (threadIdx.x == 0) cid(0, sl, k) = gid < p ? gid : -1;
       C* x = col(0, sl, k);
-      for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+      for (int r = threadIdx.x; r < ld; r += blockDim.x) {
         C v = C(0);
-        if (gid < p) v = r < q ? Win[(size_t)gid * q + r] : ((r - q) == gid ? C(1) : C(0));
+        if (gid < p && r < rows) v = r < q ? Win[(size_t)gid * q + r] : ((r - q) == gid ? C(1) : C(0));
         x[r] = v;
       }
     }
@@ -1038,15 +1040,39 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(1024)
       // rotate the positions 1..P-1 by one (position 0 stays): pull the next two blocks
       cl.sync();
       const int nb = cur ^ 1;
-      for (int sl = 0; sl < 2; ++sl) {
-        const int x = sl == 0 ? rank : P - 1 - rank;
-        const int src = x == 0 ? 0 : (x == 1 ? P - 1 : x - 1);
-        const int scta = src < JC ? src : P - 1 - src, ssl = src < JC ? 0 : 1;
-        const C* rsrc = cl.map_shared_rank(col(cur, ssl, 0), scta);
-        const int* rid = cl.map_shared_rank(&cid(cur, ssl, 0), scta);
-        C* dst = col(nb, sl, 0);
-        for (long long e = threadIdx.x; e < (long long)b * rows; e += blockDim.x) dst[e] = rsrc[e];
-        if (threadIdx.x < b) cid(nb, sl, threadIdx.x) = rid[threadIdx.x];
+      {  // both slots in 16-byte words, every remote load issued before the first store
+        const uint4* rsrc[2];
+        const int* rid[2];
+#pragma unroll
+        for (int sl = 0; sl < 2; ++sl) {
+          const int x = sl == 0 ? rank : P - 1 - rank;
+          const int src = x == 0 ? 0 : (x == 1 ? P - 1 : x - 1);
+          const int scta = src < JC ? src : P - 1 - src, ssl = src < JC ? 0 : 1;
+          rsrc[sl] = reinterpret_cast<const uint4*>(cl.map_shared_rank(col(cur, ssl, 0), scta));
+          rid[sl] = cl.map_shared_rank(&cid(cur, ssl, 0), scta);
+        }
+        const int n16 = b * ld / V16;  // 16-byte words per slot
+        for (int e0 = threadIdx.x; e0 < n16; e0 += 2 * blockDim.x) {
+          uint4 v[2][2];
+#pragma unroll
+          for (int sl = 0; sl < 2; ++sl)
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const int e = e0 + u * blockDim.x;
+              if (e < n16) v[sl][u] = rsrc[sl][e];
+            }
+#pragma unroll
+          for (int sl = 0; sl < 2; ++sl)
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const int e = e0 + u * blockDim.x;
+              if (e < n16) reinterpret_cast<uint4*>(col(nb, sl, 0))[e] = v[sl][u];
+            }
+        }
+        if (threadIdx.x < b) {
+          cid(nb, 0, threadIdx.x) = rid[0][threadIdx.x];
+          cid(nb, 1, threadIdx.x) = rid[1][threadIdx.x];
+        }
       }
       cur = nb;
       __syncthreads();
@@ -1102,8 +1128,9 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(1024)
 template <typename C>
 size_t jacobi_cluster_smem(int q, int p, bool want_v) {
   const int b = (p + 2 * JC - 1) / (2 * JC);
-  const size_t rows = (size_t)q + (want_v ? p : 0);
-  return 4 * (size_t)b * rows * sizeof(C) + (4 * (size_t)b + 4) * sizeof(int) + 2 * (size_t)b * sizeof(C) + 16;
+  const size_t V16 = 16 / sizeof(C);
+  const size_t rows = (size_t)q + (want_v ? p : 0), ld = (rows + V16 - 1) / V16 * V16;
+  return 4 * (size_t)b * ld * sizeof(C) + (4 * (size_t)b + 4) * sizeof(int) + 2 * (size_t)b * sizeof(C) + 16;
 }
 
 template <typename C, typename S>
