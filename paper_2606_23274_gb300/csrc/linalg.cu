@@ -973,8 +973,72 @@ __device__ __forceinline__ bool jacobi_pair(C* __restrict__ xi, C* __restrict__ 
   return true;
 }
 
-template <typename C>
-__global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(1024)
+// The angle of a rotation only steers convergence; its orthogonality comes
+// from cs = 1/sqrt(1 + t^2), sn = cs t. So t may take approximate division
+// and square root (the next sweep corrects a slightly wrong angle).
+__device__ __forceinline__ void rotation_params_fast(float a, float b, float g, float& cs, float& sn) {
+  const float zeta = __fdividef(b - a, 2.f * g);
+  const float z2 = fmaf(zeta, zeta, 1.f);
+  const float t = __fdividef(copysignf(1.f, zeta), fabsf(zeta) + z2 * rsqrtf(z2));
+  cs = rsqrtf(fmaf(t, t, 1.f));
+  sn = cs * t;
+}
+__device__ __forceinline__ void rotation_params_fast(double a, double b, double g, double& cs, double& sn) {
+  rotation_params(a, b, g, cs, sn);
+}
+
+// A column pair with each lane's RPL entries held in registers (rows <= 32 RPL):
+// one round of independent loads, the three dot products over the first q rows,
+// and the rotated values stored without reloading.
+template <typename C, int RPL>
+__device__ __forceinline__ bool jacobi_pair_r(C* __restrict__ xi, C* __restrict__ xj, int q, int rows, C tol2) {
+  const int lane = threadIdx.x & 31;
+  C x[RPL], y[RPL];
+#pragma unroll
+  for (int t = 0; t < RPL; ++t) {
+    const int r = lane + 32 * t;
+    x[t] = r < rows ? xi[r] : C(0);
+    y[t] = r < rows ? xj[r] : C(0);
+  }
+  C a = 0, b = 0, g = 0;
+#pragma unroll
+  for (int t = 0; t < RPL; ++t)
+    if (lane + 32 * t < q) {
+      a = madd(x[t], x[t], a);
+      b = madd(y[t], y[t], b);
+      g = madd(x[t], y[t], g);
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {  // the three butterflies interleaved: 5 shuffle latencies, not 15
+    const C sa = __shfl_xor_sync(0xffffffffu, a, o);
+    const C sb = __shfl_xor_sync(0xffffffffu, b, o);
+    const C sg = __shfl_xor_sync(0xffffffffu, g, o);
+    a += sa;
+    b += sb;
+    g += sg;
+  }
+  if (!(a > C(0) && b > C(0) && g * g > tol2 * a * b)) return false;
+  C cs, sn;
+  rotation_params_fast(a, b, g, cs, sn);
+#pragma unroll
+  for (int t = 0; t < RPL; ++t) {
+    const int r = lane + 32 * t;
+    if (r < rows) {
+      xi[r] = cs * x[t] - sn * y[t];
+      xj[r] = sn * x[t] + cs * y[t];
+    }
+  }
+  return true;
+}
+
+template <typename C, int RPL>
+__device__ __forceinline__ bool jacobi_pair_any(C* __restrict__ xi, C* __restrict__ xj, int q, int rows, C tol2) {
+  if constexpr (RPL > 0) return jacobi_pair_r<C, RPL>(xi, xj, q, rows, tol2);
+  else return jacobi_pair<C>(xi, xj, q, rows, tol2);
+}
+
+template <typename C, int RPL>
+__global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(RPL > 0 ? 640 : 1024)
     jacobi_cluster_kernel(int q, int p, int b, const C* __restrict__ Win, int max_sweeps, double tol, uint32_t* errw,
                           C* __restrict__ Uo, C* __restrict__ So, C* __restrict__ Vo) {
   cg::cluster_group cl = cg::this_cluster();
@@ -1024,18 +1088,23 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(1024)
             int i, j;
             rr_pair(mr, k, B, i, j);
             if (i < b && j < b && cid(cur, sl, i) >= 0 && cid(cur, sl, j) >= 0)
-              rot |= jacobi_pair<C>(col(cur, sl, i), col(cur, sl, j), q, rows, tol2);
+              rot |= jacobi_pair_any<C, RPL>(col(cur, sl, i), col(cur, sl, j), q, rows, tol2);
           }
           __syncthreads();
         }
       }
-      for (int mr = 0; mr < b; ++mr) {  // pairs between the two blocks
-        for (int w = warp; w < b; w += nw) {
-          const int j = (w + mr) % b;
-          if (cid(cur, 0, w) >= 0 && cid(cur, 1, j) >= 0)
-            rot |= jacobi_pair<C>(col(cur, 0, w), col(cur, 1, j), q, rows, tol2);
+      // pairs between the two blocks: warp w keeps column w of slot 0 and meets
+      // column (w + mr) mod b of slot 1 (padding columns are zero and never rotate)
+      if (warp < b) {
+        C* xi = col(cur, 0, warp);
+        int j = warp;
+        for (int mr = 0; mr < b; ++mr) {
+          rot |= jacobi_pair_any<C, RPL>(xi, col(cur, 1, j), q, rows, tol2);
+          j = (j + 1 == b) ? 0 : j + 1;
+          __syncthreads();
         }
-        __syncthreads();
+      } else {
+        for (int mr = 0; mr < b; ++mr) __syncthreads();
       }
       // rotate the positions 1..P-1 by one (position 0 stays): pull the next two blocks
       cl.sync();
@@ -1148,14 +1217,19 @@ cudaError_t jacobi_svd(int q, int p, S* W, S* U, S* Sv, S* V, S* Vwork, int max_
     const size_t csm = jacobi_cluster_smem<C>(q, p, V != nullptr);
     const int bc = (p + 2 * JC - 1) / (2 * JC), B = bc + (bc & 1);
     if (p >= 32 && csm <= 200 * 1024 && 32 * B <= 1024) {
-      if (csm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(jacobi_cluster_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)csm);
-        if (e != cudaSuccess) return e;
-      }
-      ++tl_launches;
-      jacobi_cluster_kernel<C><<<JC, 32 * B, csm, st>>>(q, p, bc, W, max_sweeps, tol, errw, U, Sv, V);
-      return cudaGetLastError();
+      auto launch = [&](auto kern) {
+        if (csm > 48 * 1024) {
+          cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+          if (e != cudaSuccess) return e;
+        }
+        ++tl_launches;
+        kern<<<JC, 32 * B, csm, st>>>(q, p, bc, W, max_sweeps, tol, errw, U, Sv, V);
+        return cudaGetLastError();
+      };
+      const int rows = q + (V != nullptr ? p : 0);
+      if (rows <= 160 && 32 * B <= 640) return launch(jacobi_cluster_kernel<C, 5>);
+      if (rows <= 288 && 32 * B <= 640) return launch(jacobi_cluster_kernel<C, 9>);
+      return launch(jacobi_cluster_kernel<C, 0>);
     }
   }
   const size_t need = ((size_t)q * p + (V ? (size_t)p * p : 0)) * sizeof(S);
