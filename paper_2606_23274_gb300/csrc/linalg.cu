@@ -296,6 +296,12 @@ __device__ __forceinline__ df32 qsqrt(df32 x) {
   const df32 e = madd(df32(-s, 0.0f), df32(s, 0.0f), x);  // x - s^2
   return two_sum(s, e.hi * (0.5f / s));
 }
+// 1/sqrt(x): FP32 from the hardware estimate and one Newton step (r (3 - x r^2) / 2)
+__device__ __forceinline__ float qrsqrt(float x) {
+  const float r = rsqrtf(x);
+  return r * fmaf(-0.5f * x * r, r, 1.5f);
+}
+__device__ __forceinline__ double qrsqrt(double x) { return 1.0 / sqrt(x); }
 __device__ __forceinline__ float qrcp(float x) { return 1.0f / x; }
 __device__ __forceinline__ double qrcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ df32 qrcp(df32 x) {
@@ -303,6 +309,7 @@ __device__ __forceinline__ df32 qrcp(df32 x) {
   const df32 e = madd(-x, r, df32(1.0f, 0.0f));  // 1 - x r
   return madd(r, e, r);
 }
+__device__ __forceinline__ df32 qrsqrt(df32 x) { return qrcp(qsqrt(x)); }
 __device__ __forceinline__ bool qneg(float x) { return x < 0.0f; }
 __device__ __forceinline__ bool qneg(double x) { return x < 0.0; }
 __device__ __forceinline__ bool qneg(df32 x) { return x.hi < 0.0f; }  // a normalised pair has the sign of hi
@@ -438,8 +445,9 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
   C* diag = sm + Lay.diag;
   C* red = sm + Lay.red;
   C* xrow = sm + Lay.xrow;
-  for (int c = 0; c < p; ++c)
-    for (int i = tid; i < rb; i += blockDim.x) X[(size_t)c * ld + i] = i < nr ? C(Xg[(size_t)c * q + r0 + i]) : C(0);
+  for (int i = tid & 63; i < rb; i += 64)  // 64 rows x 4 column groups, loads unrolled for overlap
+#pragma unroll 4
+    for (int c = tid >> 6; c < p; c += 4) X[(size_t)c * ld + i] = i < nr ? C(Xg[(size_t)c * q + r0 + i]) : C(0);
   for (int t = tid; t < npan * QB * QB; t += blockDim.x) Gm[t] = C(0);
   for (int pn = 0; pn < npan; ++pn) {
     for (int t = tid; t < QB * QB; t += blockDim.x) Gt[t] = C(0);  // read after the barriers below
@@ -518,7 +526,7 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
       const C v0 = x0 - alpha;
       const C vn2 = madd(v0, v0, madd(-x0, x0, ss));
       const bool zero = !qpos(vn2);
-      const C inv = zero ? C(0) : qrcp(qsqrt(vn2));
+      const C inv = zero ? C(0) : qrsqrt(vn2);
       if (tid == 0) diag[j0 + jj] = zero ? C(0) : alpha;
       C dv[QB];
 #pragma unroll
@@ -552,6 +560,7 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
 #pragma unroll
       for (int jj = 0; jj < QB; ++jj) acc[jj] = C(0);
       const C* xc = X + (size_t)c * ld;
+#pragma unroll 4
       for (int i = i0; i < nr; ++i) {
         C v[QB];
         ld16(P + (size_t)(r0 + i - j0) * QB, v);
@@ -575,7 +584,8 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
       C wv[QB];
 #pragma unroll
       for (int jj = 0; jj < QB; ++jj) wv[jj] = C(0);
-      for (int t = 0; t < JQ; ++t) {
+#pragma unroll(sizeof(C) == 4 ? 4 : 2)
+      for (int t = 0; t < JQ; ++t) {  // several CTAs' partials in flight at once
         C x[QB];
         ld16(cl.map_shared_rank(W, (unsigned)t) + (size_t)c * QB, x);
 #pragma unroll
@@ -610,8 +620,8 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
   cl.sync();  // no CTA reads another's partial W of the last panel any more
   C* Qm = sm + Lay.Qm;
   C* Vmy = sm + Lay.Vmy;
-  for (int c = 0; c < r; ++c)
-    for (int i = tid; i < rb; i += blockDim.x) Qm[(size_t)c * ld + i] = (r0 + i == c) ? C(1) : C(0);
+  for (int i = tid & 63; i < rb; i += 64)
+    for (int c = tid >> 6; c < r; c += 4) Qm[(size_t)c * ld + i] = (r0 + i == c) ? C(1) : C(0);
   for (int pn = npan - 1; pn >= 0; --pn) {
     const int j0 = pn * QB, w = min(QB, r - j0);
     const C* G = Gm + (size_t)pn * QB * QB;
@@ -630,6 +640,7 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
 #pragma unroll
       for (int jj = 0; jj < QB; ++jj) acc[jj] = C(0);
       const C* qc = Qm + (size_t)c * ld;
+#pragma unroll 4
       for (int i = i0; i < nr; ++i) {
         C v[QB];
         ld16(Vmy + (size_t)i * QB, v);
@@ -644,7 +655,8 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
       C wv[QB];
 #pragma unroll
       for (int jj = 0; jj < QB; ++jj) wv[jj] = C(0);
-      for (int t = 0; t < JQ; ++t) {
+#pragma unroll(sizeof(C) == 4 ? 4 : 2)
+      for (int t = 0; t < JQ; ++t) {  // several CTAs' partials in flight at once
         C x[QB];
         ld16(cl.map_shared_rank(W, (unsigned)t) + (size_t)c * QB, x);
 #pragma unroll
@@ -676,16 +688,20 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
     }
     __syncthreads();
   }
-  for (int c = 0; c < r; ++c)
-    for (int i = tid; i < nr; i += blockDim.x)
+  for (int i = tid & 63; i < nr; i += 64)
+#pragma unroll 4
+    for (int c = tid >> 6; c < r; c += 4)
       Qg[(size_t)c * q + r0 + i] = (S)(qneg(diag[c]) ? -Qm[(size_t)c * ld + i] : Qm[(size_t)c * ld + i]);
-  for (int c = 0; c < p; ++c)
-    for (int i = tid; i < nr; i += blockDim.x) {
-      const int gi = r0 + i;
-      if (gi >= r) continue;
+  for (int i = tid & 63; i < nr; i += 64) {
+    const int gi = r0 + i;
+    if (gi >= r) continue;
+    const bool flip = qneg(diag[gi]);
+#pragma unroll 4
+    for (int c = tid >> 6; c < p; c += 4) {
       const C val = gi < c ? X[(size_t)c * ld + i] : (gi == c ? diag[gi] : C(0));
-      Rg[(size_t)c * r + gi] = (S)(qneg(diag[gi]) ? -val : val);
+      Rg[(size_t)c * r + gi] = (S)(flip ? -val : val);
     }
+  }
   cl.sync();  // no CTA leaves while another may still read its shared memory
 }
 
