@@ -95,6 +95,7 @@ struct BlockCache {
           ++i;
         }
     }
+    if (drop.empty()) return 0;
     int cur = 0;
     cudaGetDevice(&cur);
     size_t bytes = 0;
@@ -1536,7 +1537,7 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
     if (o.update != 0 && o.update != 1) return TT_ERR_INVALID_ARGUMENT;
     if (o.precision < 0 || o.precision > 5 || o.oversample < 0) return TT_ERR_INVALID_ARGUMENT;
     if (o.init < 0 || o.init > 2 || (o.init == TT_INIT_GIVEN && !o.init_C)) return TT_ERR_INVALID_ARGUMENT;
-    if (o.precision == TT_PREC_BF16_SPLIT) return TT_ERR_INVALID_ARGUMENT;  // not in this build
+    if (o.precision == TT_PREC_BF16_SPLIT) return TT_ERR_INVALID_ARGUMENT;  // reserved, not implemented
     if (o.n_segments > 1 && gauge != TT_GAUGE_INVERSE_CANONICAL) return TT_ERR_INVALID_ARGUMENT;
     if (o.edge_extra < 0) return TT_ERR_INVALID_ARGUMENT;
     int LA, LB;

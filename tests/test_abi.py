@@ -42,6 +42,12 @@ def test_status_strings_without_gpu():
     h = ct.c_void_p()
     assert lib.tt_fit_create(None, None, 4, 0.0, 0, None, ct.byref(h)) == ttfit.TT_ERR_INVALID_ARGUMENT
     assert lib.tt_fit_sweep(None, 1, None) == ttfit.TT_ERR_INVALID_ARGUMENT
+    n = ct.c_int(-1)
+    assert lib.tt_fit_jacobi_sweeps(None, ct.byref(n)) == ttfit.TT_ERR_INVALID_ARGUMENT
+    cnt = ct.c_longlong(-1)
+    assert lib.tt_fit_launch_count(None, ct.byref(cnt)) == ttfit.TT_ERR_INVALID_ARGUMENT
+    # the block cache is empty in a process that made no fit: nothing to free, no device call
+    assert ttfit.tt_device_cache_release(-1) == 0
 
 
 def test_ctypes_structs_match_c_layout():
