@@ -1711,19 +1711,28 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
     *out = h;
     return TT_OK;
   } catch (const TTError& e) {
+    // preparation and guess streams may still run: let everything finish before
+    // the handle's blocks go back to the process-wide cache
     g_create_error = std::string("tt_fit_create: ") + e.what();
     if (h) {
       cudaGetLastError();
+      cudaDeviceSynchronize();
       free_lanes(h);
       delete h;
     }
     return e.code;
   } catch (const std::bad_alloc&) {
-    if (h) free_lanes(h);
+    if (h) {
+      cudaDeviceSynchronize();
+      free_lanes(h);
+    }
     delete h;
     return TT_ERR_OUT_OF_MEMORY;
   } catch (...) {
-    if (h) free_lanes(h);
+    if (h) {
+      cudaDeviceSynchronize();
+      free_lanes(h);
+    }
     delete h;
     return TT_ERR_CUDA;
   }
