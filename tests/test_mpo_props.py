@@ -1,0 +1,33 @@
+"""Pins of the PyTorch checkers in tests/mpo_props.py (used by the full-size GPU
+test) against dense matrices and the oracle, on CPU."""
+import numpy as np
+import pytest
+
+from oracle.grad import inner
+from oracle.mpo import to_dense
+from paper_2606_23274_gb300.synth import gaussian_mpo, kron_sum_mpo
+
+torch = pytest.importorskip("torch")
+from mpo_props import inner_ab, norm2  # noqa: E402
+
+
+def _t(X):
+    return [torch.from_numpy(np.ascontiguousarray(x)) for x in X]
+
+
+def test_norm2_matches_dense():
+    C = gaussian_mpo(5, 2, 3, 4, 0, 0.7)
+    D = to_dense(C)
+    assert np.isclose(norm2(_t(C)), np.sum(D * D), rtol=1e-12)
+
+
+def test_inner_ab_matches_dense_and_oracle():
+    A = kron_sum_mpo(5, 3, 2, 0)
+    B = gaussian_mpo(5, 2, 2, 2, 1, 0.6)
+    C = gaussian_mpo(5, 2, 4, 2, 2, 0.6)
+    dense = np.sum(to_dense(C) * (to_dense(A) @ to_dense(B)))
+    got = inner_ab(_t(C), _t(A), _t(B))
+    assert np.isclose(got, dense, rtol=1e-11)
+    assert np.isclose(got, inner(C, A, B), rtol=1e-11)
+    # a transposed operand (B A) or a swapped leg gives a different number
+    assert not np.isclose(inner_ab(_t(C), _t(B), _t(A)), dense, rtol=1e-6)
