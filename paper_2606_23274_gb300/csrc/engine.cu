@@ -776,32 +776,42 @@ int factorize(tt_fit* h, int m, int n, int sweep, int site1, int need = 3) {
 
 // ---------------------------------------------------------------------------
 // Gauge update of the non-FP64 paths. The FP32 factorisation gives singular
-// vectors accurate to the FP32 level; one Newton-Schulz step in FP64,
-// X <- X (3 I - X^T X) / 2, makes the kept ones an isometry to ~1e-12, and the
-// other factor is the projection of the two-site tensor on it (the optimal
-// factor for that isometry, Eq. fit_pde). Because ||C||^2 is stationary under
-// small rotations of the kept subspace, the FP32 rounding of the subspace
-// enters ||C||^2 only at second order. Writes ||C_window||^2 to dn2[l].
+// vectors accurate to the FP32 level; Newton-Schulz steps in FP64,
+// X <- X (3 I - X^T X) / 2, make the kept ones an isometry, and the other
+// factor is the projection of the two-site tensor on it (the optimal factor for
+// that isometry, Eq. fit_pde). One step maps a Gram deviation E to about
+// (3/4) E^2: from the FP32 factor (|E| up to ~3e-5 at 512 rows) that is ~1e-9
+// per core, and the deviations of the L-1 cores outside the orthogonality
+// centre add up in ||C||^2, which the sweep reads off the last window alone.
+// A second step takes each core to the FP64 rounding level. Because ||C||^2 is
+// stationary under small rotations of the kept subspace, the FP32 rounding of
+// the subspace enters ||C||^2 only at second order. Writes ||C_window|| to dn2[l].
 // ---------------------------------------------------------------------------
+constexpr int kNewtonSchulzSteps = 2;
+
 template <typename F>
 void ns_orthonormalize(tt_fit* h, const F* X32, int rows, int k, double* X64) {
   double* G = W(h).pG;
-  copymap<F, double>(h, rows, k, X32, IdxMap::lin(1), IdxMap::lin(rows), W(h).pT, IdxMap::lin(1), IdxMap::lin(rows));
-  GemmArgs<double> g;  // G = X^T X (k x k)
-  g.M = k; g.N = k; g.K = rows;
-  g.A = W(h).pT; g.am = IdxMap::lin(rows); g.ak = IdxMap::lin(1);
-  g.B = W(h).pT; g.bn = IdxMap::lin(rows); g.bk = IdxMap::lin(1);
-  g.C = G; g.cm = IdxMap::lin(k); g.cn = IdxMap::lin(1);
-  gemm<double>(h, g);
-  CK(cudaMemcpyAsync(X64, W(h).pT, sizeof(double) * (size_t)rows * k, cudaMemcpyDeviceToDevice, W(h).st));
-  GemmArgs<double> g2;  // X64 = 1.5 X - 0.5 X G
-  g2.M = rows; g2.N = k; g2.K = k;
-  g2.A = W(h).pT; g2.am = IdxMap::lin(1); g2.ak = IdxMap::lin(rows); g2.a_kfast = false;
-  g2.B = G; g2.bn = IdxMap::lin(k); g2.bk = IdxMap::lin(1);
-  g2.C = X64; g2.cm = IdxMap::lin(1); g2.cn = IdxMap::lin(rows);
-  g2.alpha = -0.5;
-  g2.beta = 1.5;
-  gemm<double>(h, g2);
+  double* X = W(h).pT;
+  copymap<F, double>(h, rows, k, X32, IdxMap::lin(1), IdxMap::lin(rows), X, IdxMap::lin(1), IdxMap::lin(rows));
+  for (int it = 0; it < kNewtonSchulzSteps; ++it) {
+    if (it > 0) CK(cudaMemcpyAsync(X, X64, sizeof(double) * (size_t)rows * k, cudaMemcpyDeviceToDevice, W(h).st));
+    GemmArgs<double> g;  // G = X^T X (k x k)
+    g.M = k; g.N = k; g.K = rows;
+    g.A = X; g.am = IdxMap::lin(rows); g.ak = IdxMap::lin(1);
+    g.B = X; g.bn = IdxMap::lin(rows); g.bk = IdxMap::lin(1);
+    g.C = G; g.cm = IdxMap::lin(k); g.cn = IdxMap::lin(1);
+    gemm<double>(h, g);
+    CK(cudaMemcpyAsync(X64, X, sizeof(double) * (size_t)rows * k, cudaMemcpyDeviceToDevice, W(h).st));
+    GemmArgs<double> g2;  // X64 = 1.5 X - 0.5 X G
+    g2.M = rows; g2.N = k; g2.K = k;
+    g2.A = X; g2.am = IdxMap::lin(1); g2.ak = IdxMap::lin(rows); g2.a_kfast = false;
+    g2.B = G; g2.bn = IdxMap::lin(k); g2.bk = IdxMap::lin(1);
+    g2.C = X64; g2.cm = IdxMap::lin(1); g2.cn = IdxMap::lin(rows);
+    g2.alpha = -0.5;
+    g2.beta = 1.5;
+    gemm<double>(h, g2);
+  }
 }
 
 template <typename T, typename F>

@@ -789,15 +789,25 @@ __device__ __forceinline__ void rr_pair(int round, int k, int P, int& i, int& j)
   }
 }
 
+// 1/sqrt(x) for x in [1, 2]: the hardware estimate refined by one Newton step
+// r <- r + r (1 - x r^2) / 2, so that cs^2 + sn^2 = cs^2 (1 + t^2) is 1 to the
+// FP32 rounding. An estimate left unrefined makes every rotation a rotation
+// times sqrt(cs^2 + sn^2), and the accumulated right factor drifts away from
+// orthonormal over the thousands of rotations of a decomposition.
+__device__ __forceinline__ float rot_rsqrt(float x) {
+  const float r = rsqrtf(x);
+  return fmaf(0.5f * r, fmaf(-x * r, r, 1.f), r);
+}
+
 // Jacobi rotation (c, s) that zeroes the (i, j) entry of the 2x2 Gram block
-// [[a, g], [g, b]] (Rutishauser's formulas). In FP32 the fast reciprocal square
-// root and division serve: any rotation this close to the exact one still
-// drives the pair towards orthogonality, and convergence is decided on the
-// recomputed Gram entries, not on these values.
+// [[a, g], [g, b]] (Rutishauser's formulas). In FP32 the fast division serves
+// for the angle: any rotation this close to the exact one still drives the
+// pair towards orthogonality, and convergence is decided on the recomputed
+// Gram entries, not on these values.
 __device__ __forceinline__ void rotation_params(float a, float b, float g, float& cs, float& sn) {
   const float zeta = __fdividef(b - a, 2.f * g);
   const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-  cs = rsqrtf(1.f + t * t);
+  cs = rot_rsqrt(1.f + t * t);
   sn = cs * t;
 }
 __device__ __forceinline__ void rotation_params(double a, double b, double g, double& cs, double& sn) {
@@ -990,13 +1000,14 @@ __device__ __forceinline__ bool jacobi_pair(C* __restrict__ xi, C* __restrict__ 
 }
 
 // The angle of a rotation only steers convergence; its orthogonality comes
-// from cs = 1/sqrt(1 + t^2), sn = cs t. So t may take approximate division
-// and square root (the next sweep corrects a slightly wrong angle).
+// from cs = 1/sqrt(1 + t^2), sn = cs t, which is computed accurately. So t may
+// take approximate division and square root (the next sweep corrects a
+// slightly wrong angle).
 __device__ __forceinline__ void rotation_params_fast(float a, float b, float g, float& cs, float& sn) {
   const float zeta = __fdividef(b - a, 2.f * g);
   const float z2 = fmaf(zeta, zeta, 1.f);
   const float t = __fdividef(copysignf(1.f, zeta), fabsf(zeta) + z2 * rsqrtf(z2));
-  cs = rsqrtf(fmaf(t, t, 1.f));
+  cs = rot_rsqrt(fmaf(t, t, 1.f));
   sn = cs * t;
 }
 __device__ __forceinline__ void rotation_params_fast(double a, double b, double g, double& cs, double& sn) {

@@ -27,3 +27,33 @@ def inner_ab(C, A, B) -> float:
         T2 = torch.tensordot(T1, b, dims=([0, 3], [0, 1]))              # [c0, s, a1, t, b1]
         E = torch.tensordot(T2, c, dims=([0, 1, 3], [0, 1, 2]))         # [a1, b1, c1]
     return float(E.reshape(-1)[0])
+
+
+def diff_norm(X, Y) -> float:
+    """||X - Y||_F, computed stably: the direct-sum MPO X (+) (-Y) (block bonds)
+    is left-orthogonalised by Householder QR in FP64 and the norm read off its
+    last core, so the result does not suffer the cancellation of
+    ||X||^2 + ||Y||^2 - 2 <X, Y> (the error metric of Sec. 5)."""
+    L = len(X)
+    dev = X[0].device
+    if L == 1:
+        return float(torch.linalg.norm(X[0].double() - Y[0].double().to(dev)))
+    R = None
+    for l in range(L):
+        x, y = X[l].double(), Y[l].double().to(dev)
+        if l == 0:
+            D = torch.cat([x, -y], dim=3)
+        elif l == L - 1:
+            D = torch.cat([x, y], dim=0)
+        else:
+            a0, d, dp, a1 = x.shape
+            b0, _, _, b1 = y.shape
+            D = torch.zeros((a0 + b0, d, dp, a1 + b1), dtype=torch.float64, device=dev)
+            D[:a0, :, :, :a1] = x
+            D[a0:, :, :, a1:] = y
+        if R is not None:
+            D = torch.tensordot(R, D, dims=([1], [0]))
+        if l == L - 1:
+            return float(torch.linalg.norm(D))
+        a0, d, dp, a1 = D.shape
+        _, R = torch.linalg.qr(D.reshape(a0 * d * dp, a1))

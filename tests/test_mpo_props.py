@@ -8,7 +8,7 @@ from oracle.mpo import to_dense
 from paper_2606_23274_gb300.synth import gaussian_mpo, kron_sum_mpo
 
 torch = pytest.importorskip("torch")
-from mpo_props import inner_ab, norm2  # noqa: E402
+from mpo_props import diff_norm, inner_ab, norm2  # noqa: E402
 
 
 def _t(X):
@@ -31,3 +31,20 @@ def test_inner_ab_matches_dense_and_oracle():
     assert np.isclose(got, inner(C, A, B), rtol=1e-11)
     # a transposed operand (B A) or a swapped leg gives a different number
     assert not np.isclose(inner_ab(_t(C), _t(B), _t(A)), dense, rtol=1e-6)
+
+
+def test_diff_norm_matches_dense_and_oracle():
+    from oracle.mpo import mpo_diff_norm
+    X = gaussian_mpo(6, 2, 3, 4, 3, 0.7)
+    Y = gaussian_mpo(6, 2, 3, 3, 4, 0.7)
+    dense = np.linalg.norm(to_dense(X) - to_dense(Y))
+    got = diff_norm(_t(X), _t(Y))
+    assert np.isclose(got, dense, rtol=1e-11)
+    assert np.isclose(got, mpo_diff_norm(X, Y), rtol=1e-11)
+    # a near-identical pair: the result is the size of the perturbation, with no
+    # cancellation floor at sqrt(eps) ||X||
+    Z = [x.copy() for x in X]
+    Z[3] = Z[3] + 1e-9 * gaussian_mpo(6, 2, 3, 4, 5, 0.7)[3]
+    dz = np.linalg.norm(to_dense(X) - to_dense(Z))
+    assert np.isclose(diff_norm(_t(X), _t(Z)), dz, rtol=1e-5)
+    assert diff_norm(_t(X), _t(X)) <= 1e-14 * np.linalg.norm(to_dense(X))
