@@ -6,7 +6,7 @@ and bench.py's CPU-baseline / reference leg; never by the product path. It
 shares no code with the CUDA path; only the seeded inputs of
 paper_2606_23274_gb300.synth are common.
 
-Readings of the paper taken here (each also listed in the design doc):
+Readings of the paper taken here, where it is silent or ambiguous:
 
 * Env/sweep indices (Alg. 5): L_0 = R_{L+1} = [1] (Sec. 2.3.3); R_L..R_3 are
   precomputed; a forward step at site l first builds L_{l-1} (l >= 2), a

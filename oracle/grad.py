@@ -6,7 +6,7 @@ FP64 numpy; nothing here is used by the CUDA path.
 
 The paper states the fit's objective (Eq. fit_min, ||A B - C||_F^2 minimised
 over C) and builds it from environments (Fig. envs); it does not differentiate
-with respect to A or B. Readings (also in the design doc):
+with respect to A or B. Readings taken here, where the paper is silent:
 
 * "At fixed gauge": C (or W) is a constant MPO; nothing is differentiated
   through the fit's SVDs or iterations.

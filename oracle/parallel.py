@@ -14,7 +14,7 @@ disjoint environments. A full set of local sweeps is:
   (5) odd segments sweep backward, even segments forward;
   (6) connection updates at the even|odd boundaries.
 
-Readings (also in DESIGN.md):
+Readings taken here, where the paper is silent or ambiguous:
 * Segments are numbered from 1, so the first segment is odd.
 * Initialisation (Sec. 4.2): the initial guess is brought to inverse canonical
   form by a left-to-right SVD sweep of the right-canonical guess (Psi_l = U S,

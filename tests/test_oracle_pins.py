@@ -293,3 +293,33 @@ def test_uniform_workload_fit_converges():
     C, f = fit(A, B, 12, 0.0, 6, stop_on_converge=False)
     d = [h.delta for h in f.st.history]
     assert d[-1] < 1e-3
+
+
+def test_mpo_inner_matches_dense():
+    from oracle.mpo import mpo_inner
+    X = gaussian_mpo(5, 2, 3, 11, 0, 0.7)
+    Y = gaussian_mpo(5, 2, 4, 11, 1, 0.6)
+    assert np.isclose(mpo_inner(X, Y), np.sum(to_dense(X) * to_dense(Y)), rtol=1e-12)
+    # <X, X> is the squared norm, and a transposed leg order gives another number
+    assert np.isclose(mpo_inner(X, X), mpo_norm(X) ** 2, rtol=1e-12)
+    Xt = [np.ascontiguousarray(x.transpose(0, 2, 1, 3)) for x in X]
+    assert not np.isclose(mpo_inner(Xt, Y), mpo_inner(X, Y), rtol=1e-6)
+
+
+def test_bond_spectra_match_dense_matricisations():
+    """The singular values across bond l are those of the dense operator
+    reshaped to (x_1 y_1 .. x_l y_l) x (x_{l+1} y_{l+1} .. x_L y_L) (C13 order)."""
+    from oracle.mpo import bond_spectra
+    L, d = 5, 2
+    X = gaussian_mpo(L, d, 3, 12, 0, 0.7)
+    D = to_dense(X).reshape([d] * L + [d] * L)              # (x_1..x_L, y_1..y_L)
+    perm = [i for l in range(L) for i in (l, L + l)]          # (x_1, y_1, x_2, y_2, ...)
+    T = D.transpose(perm)
+    got = bond_spectra(X)
+    assert len(got) == L - 1
+    for l in range(1, L):
+        M = T.reshape(d ** (2 * l), -1)
+        ref = np.linalg.svd(M, compute_uv=False)
+        r = len(got[l - 1])
+        assert np.allclose(got[l - 1], ref[:r], rtol=1e-10, atol=1e-13 * ref[0])
+        assert np.all(ref[r:] <= 1e-12 * ref[0])               # the bond holds the whole rank
