@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--workload", default=WORKLOAD,
                    help="synthetic workload (default: the timed one); smaller ones serve profiling captures")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-accuracy", action="store_true", help="skip the (untimed) FP64 reference fit")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
 
@@ -109,6 +110,38 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- native arm
+def rel_frobenius(X, Y) -> float:
+    """||X - Y||_F / ||Y||_F for two MPOs (torch, FP64 on their device): the direct-sum MPO
+    X (+) (-Y) and Y are left-orthogonalised by QR and the norms read off their last cores."""
+    import torch
+
+    def norm_of(cores):
+        R = None
+        for l, c in enumerate(cores):
+            D = c if R is None else torch.tensordot(R, c, dims=([1], [0]))
+            if l == len(cores) - 1:
+                return float(torch.linalg.norm(D))
+            a0, d, dp, a1 = D.shape
+            _, R = torch.linalg.qr(D.reshape(a0 * d * dp, a1))
+
+    L = len(X)
+    S = []
+    for l in range(L):
+        x, y = X[l].double(), Y[l].double()
+        if l == 0:
+            S.append(torch.cat([x, -y], dim=3))
+        elif l == L - 1:
+            S.append(torch.cat([x, y], dim=0))
+        else:
+            a0, d, dp, a1 = x.shape
+            b0, _, _, b1 = y.shape
+            Z = torch.zeros((a0 + b0, d, dp, a1 + b1), dtype=torch.float64, device=x.device)
+            Z[:a0, :, :, :a1] = x
+            Z[a0:, :, :, a1:] = y
+            S.append(Z)
+    return norm_of(S) / norm_of([y.double() for y in Y])
+
+
 STAGES = ("halves_ms", "join_ms", "env_finish_ms", "factorize_ms", "gauge_ms", "contraction_flops", "launches")
 # peaks of the plain CUDA-core pipes (ALU bound): 152 SMs x FMA lanes per SM x 2 flop x max SM clock
 FMA_LANES = {"f64": 2, "f32": 128}
@@ -242,6 +275,22 @@ def native(args):
         e2e = {"value": round(statistics.mean(et), 4), "unit": "s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
+    # accuracy of the timed fit (untimed): relative Frobenius distance of its C to the FP64 fit (FP64
+    # contractions and factorisation, the path pinned to the oracle) of the same inputs, seed and sweep
+    # count, by the stable difference norm (direct-sum MPO, QR sweep in FP64 on the device)
+    accuracy = None
+    if not args.no_accuracy:
+        _, sw_t, _, _, C_t, _ = results[-1]
+        g = ttfit.tt_fit_create(Ad, Bd, chi, TOL, "site", update="rsvd", oversample=OVERSAMPLE, seed=rank,
+                                precision="fp64", device=dev, stream=stream, conv_tol=0.0)
+        g.sweep(sw_t)
+        C_ref = g.result()
+        g.destroy()
+        accuracy = {"rel_frobenius_vs_fp64_fit": float(f"{rel_frobenius(C_t, C_ref):.3e}"),
+                    "reference": f"FP64 contractions + FP64 factorisation fit, same inputs, seed and sweep count "
+                                 f"({sw_t}); that path matches the FP64 oracle to ~1e-12 in ||C||^2 at this size",
+                    "bound": 1e-6}
+
     # live per-stage times: CUDA events recorded by the library on the caller's stream, inside the
     # timed steps, accumulated per precision phase and averaged over the steps
     names = list(results[0][3].keys())
@@ -334,6 +383,7 @@ def native(args):
         "roofline": roof, "clocks": clk, "e2e": e2e, "gpu_launches": int(sum(r[5] for r in results)), "gpu_launches_per_step": int(launches),
         "fits_per_s": round(world / t_step, 4), "wall_s_timed": round(wall, 2),
         "jacobi_max_sweeps": rep.get("jacobi_max_sweeps"),
+        "accuracy": accuracy,
     }
     if rank == 0 and not args.no_cpu_baseline and args.workload == WORKLOAD:
         out["cpu_baseline"] = cpu_baseline(sweeps)
@@ -366,32 +416,66 @@ def _oracle_windows(n_windows: int, seed: int = 0):
     return (time.perf_counter() - t0) / n_windows
 
 
+THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS")
+
+
+def _time_window_subprocess(threads):
+    """Seconds of one bulk window of the oracle, in a fresh interpreter with `threads`
+    BLAS/OpenMP threads (None: the library default, all cores)."""
+    env = dict(os.environ)
+    for v in THREAD_VARS:
+        if threads is None:
+            env.pop(v, None)
+        else:
+            env[v] = str(threads)
+    code = "import sys; sys.path.insert(0, %r); import bench; print(bench._oracle_windows(1))" % ROOT
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return float(r.stdout.strip().splitlines()[-1])
+
+
 def cpu_baseline(sweeps: int):
-    n = 2
-    per_window = _oracle_windows(n)
-    est = per_window * (L_SITES - 1) * sweeps
-    return {"value": round(est, 2), "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{n} bulk windows (chi=128, d=2: two-site tensor, randomized SVD, environment) on random "
-                      f"tensors of the workload's shapes, {per_window:.2f} s/window, scaled to "
-                      f"{L_SITES - 1} windows x {sweeps} sweeps (input preparation not included)"}
+    """The oracle on the host cores: one bulk window (two-site tensor, randomized SVD,
+    environment at chi = 128) timed with 1 thread and with all threads, scaled to the fit's
+    windows x sweeps. `value` is the all-threads figure."""
+    t1 = _time_window_subprocess(1)
+    tn = _time_window_subprocess(None)
+    n = os.cpu_count()
+    scale = (L_SITES - 1) * sweeps
+    return {"value": round(tn * scale, 2), "unit": "s", "cores": n, "kind": "oracle",
+            "single_thread": {"value": round(t1 * scale, 2), "cores": 1},
+            "sample": f"1 bulk window (chi=128, d=2: two-site tensor, randomized SVD, environment) on random "
+                      f"tensors of the workload's shapes, timed once with 1 thread ({t1:.2f} s) and once with "
+                      f"all {n} threads ({tn:.2f} s), scaled to {L_SITES - 1} windows x {sweeps} sweeps "
+                      f"(factor {scale}); input preparation not included"}
 
 
 def reference(args):
+    """The FP64 oracle on the host cores. A step is one bulk window of the workload, measured;
+    `value` is that window time scaled to a full fit (29 windows x 3 sweeps), and ms_per_step is
+    the measured per-step time of the sample itself."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    times = []
+    windows, sweeps = L_SITES - 1, 3
     for _ in range(args.warmup):
         _oracle_windows(1)
-    for _ in range(args.steps):
-        times.append(_oracle_windows(1) * (L_SITES - 1) * 3)
-    v = statistics.mean(times)
+    t0 = time.perf_counter()
+    per = [_oracle_windows(1) for _ in range(args.steps)]
+    wall = time.perf_counter() - t0
+    w = statistics.mean(per)
+    v = w * windows * sweeps
+    n = os.cpu_count()
     out = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "s", "n_gpus": args.gpus,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v * 1e3, 1), "higher_is_better": False,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(w * 1e3, 1), "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"{WORKLOAD} (oracle, bounded sample)", "precision": "fp64"},
-           "cpu_baseline": {"value": round(v, 3), "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
-                            "sample": f"1 bulk window per step scaled to {L_SITES - 1} windows x 3 sweeps"},
+           "config": {"workload": f"{WORKLOAD} (oracle, one bulk window per step)", "precision": "fp64"},
+           "extrapolation": {"measured_s_per_window": round(w, 3), "windows_per_sweep": windows, "sweeps": sweeps,
+                             "factor": windows * sweeps, "timed_wall_s": round(wall, 2)},
+           "cpu_baseline": {"value": round(v, 3), "unit": "s", "cores": n, "kind": "oracle",
+                            "sample": f"1 bulk window per step (measured {w:.2f} s, all {n} threads), scaled to "
+                                      f"{windows} windows x {sweeps} sweeps"},
            "e2e": {"value": round(v, 3), "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

@@ -63,8 +63,8 @@ typedef enum { TT_UPDATE_2SITE_SVD = 0, TT_UPDATE_2SITE_RSVD = 1 } tt_update;
  * is an exact FP32 product plus a compensated sum, all on the FP32 pipes
  * (FP64-class contractions at several times the FP64 rate of this GPU);
  * factorisation as for FP64. The FP32, TF32 and TF32_SPLIT paths factorise in
- * FP32 and make the kept singular vectors an FP64 isometry (one
- * Newton-Schulz step) before the gauge update; C is returned in FP64. */
+ * FP32 and make the kept singular vectors an FP64 isometry (two
+ * Newton-Schulz steps) before the gauge update; C is returned in FP64. */
 typedef enum {
   TT_PREC_FP64 = 0,
   TT_PREC_FP32 = 1,
@@ -112,8 +112,14 @@ typedef struct {
   void* stream;        /* cudaStream_t; NULL = legacy default stream                       */
   int prepare_inputs;  /* 1 (default): RQ + QR sweep of A and B (Alg. 5 left_orthogonalize) */
   uint32_t fault_inject; /* host-side fault injection for tests (TT_FAULT_*), default 0     */
-  int fast_factor;     /* FP64 / DF32 only: 1 = FP32 factorisation + FP64 Newton-Schulz     */
-                       /* polish (fast; subspace to FP32 accuracy), 0 (default) = FP64 SVD  */
+  int fast_factor;     /* FP64 / DF32 only. 0 (default): FP64 SVD. 1-3: FP32 SVD, the kept     */
+                       /* vectors made an FP64 isometry by Newton-Schulz steps. With DF32      */
+                       /* contractions and the randomized update, 3 forms the sketch          */
+                       /* Y = M Omega, its orthonormal basis Q and Q^T M in double-FP32 in     */
+                       /* every sweep (kept subspace FP64-class, ~1e-10 of ||C||); 2 does the */
+                       /* whole update in FP32 (~1e-6 of ||C||); 1 uses the FP32 update until */
+                       /* a sweep changes ||C||^2 by <= 1e-3, then the double-FP32 basis, so  */
+                       /* that the converged C is FP64-class.                                  */
   int n_segments;      /* segment-parallel fit (Sec. 4, Alg. 6): number of contiguous       */
                        /* segments N_p, each >= 2 sites; <= 1 (default) = serial Alg. 5.    */
                        /* N_p > 1 needs the inverse canonical gauge (the site gauge needs a  */

@@ -161,6 +161,7 @@ enum : uint32_t {
   ERRW_NOCONV = 2u,     // Jacobi sweeps hit their limit
   ERRW_BADSHAPE = 4u,   // a kernel saw dimensions outside its compiled limits
   ERRW_TIMEOUT = 8u,    // a bounded mbarrier wait expired
+  ERRW_HPFAIL = 16u,    // the FP64-class sketch basis could not be formed (the window falls back to FP32)
 };
 
 }  // namespace ttfit

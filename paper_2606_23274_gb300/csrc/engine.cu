@@ -192,6 +192,9 @@ struct Work {
   df32* ozWs = nullptr;
   size_t oz_slice = 0, oz_exp = 0, oz_ws = 0;
   size_t fsz = 0;
+  bool hp = false;      // the last factorisation used the FP64-class sketch basis (factors in df32)
+  bool hp_off = false;  // fall back to the all-FP32 factorisation for the current window
+  long long hp_fallbacks = 0;  // windows that fell back (diagnostic)
   double* dnorm = nullptr;
   int* dk = nullptr;
   double* ddinfo = nullptr;
@@ -238,6 +241,8 @@ struct tt_fit {
   bool use_f32 = false;   // chain type: float (FP32 / TF32 precisions), df32 (DF32) or double (FP64)
   bool use_df = false;
   bool fact_f32 = false;  // FP32 factorisation + FP64 polish (always for float chains; optional for FP64)
+  int fast_factor = 0;    // tt_fit_options.fast_factor of the current precision (1, 3: FP64-class sketch basis)
+  bool hp_sweep = false;  // the current sweep uses the FP64-class sketch basis (factorize_rsvd_hp)
   bool use_oz = true;     // DF32 chains: contractions on the tensor cores by the digit split
   std::vector<void*> chain_bufs;  // buffers rebuilt when the chain precision changes
 };
@@ -667,8 +672,156 @@ struct Chain {
 // (double on the FP64 path, float otherwise): U_M (m x p col-major, ld m),
 // S (p, sorted), V_M (n x p, ld n). Returns p (computed singular triplets).
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Factorisation of a DF32 two-site matrix with an FP64-class basis and an FP32
+// singular value decomposition: the randomized one (Sec. 3.1, exact = false),
+// or the exact one of a window whose sketch would not be narrower than the
+// matrix (exact = true: the basis of a tall Theta is that of Theta itself, the
+// basis of a wide one the identity).
+//
+// The kept singular vectors sit at s_k ~ 1e-5 s_1 in this workload, so any step
+// that rounds Theta, Y = Theta Omega or the basis Q to FP32 (absolute error
+// ~6e-8 s_1) tilts them by ~1e-2 and moves C by ~1e-6 of its norm. Here every
+// product with Theta and with the basis is double-FP32, and the two FP32 steps
+// that remain are harmless:
+//  * Q: the FP32 Householder R of the scaled Y (R only) is inverted in FP32 and
+//    applied in double-FP32, Z = Y R^-1. Any non-singular right factor keeps
+//    range(Y) exactly; it only conditions Z (cond(Z) ~ eps32 cond(Y)). The same
+//    step once more on Z, then three double-FP32 Newton-Schulz steps, make it
+//    orthonormal without moving its range. (An FP32 Cholesky factor of Z^T Z
+//    would square cond(Z) and break down for the worst sketches of this fit.)
+//  * B = Q^T Theta is formed in double-FP32. Its rows are graded (row i ~ s_i),
+//    so rounding it entrywise to FP32 perturbs each row relative to itself, and
+//    the one-sided Jacobi SVD (after an R-only QR of B^T) stays relatively
+//    accurate (Demmel and Veselic, SIAM J. Matrix Anal. Appl. 13 (1992)).
+//  * U = Q U_B and, when wanted, V = B^T U_B S^-1 in double-FP32.
+// Writes U_M (m x r) and V_M (n x r, need != 1) as df32 into fUM / fVM, the
+// FP32 singular values (of 2^-e B) into fS; returns r (the sketch width, or
+// min(m, n) for an exact factorisation). A zero pivot of an R
+// factor or a basis that is not orthonormal after the steps sets ERRW_HPFAIL:
+// the caller then redoes the window with the all-FP32 factorisation.
+// ---------------------------------------------------------------------------
+int factorize_hp(tt_fit* h, int m, int n, int sweep, int site1, int need, bool exact) {
+  Work& w = W(h);
+  // basis width r: the sketch width, or for an exact factorisation the rank bound min(m, n)
+  const int r = exact ? std::min(m, n) : h->chi_max + h->oversample;
+  const bool ident = exact && m <= n;  // the basis of a wide exact window is the identity
+  const df32* Th = (const df32*)w.Th;
+  int* ex = w.dk + 1;  // exponent of max |Theta| (set by the caller)
+  int* ey = w.dk + 2;  // exponent of max |Y|
+  df32 *Om = (df32*)w.fOm, *Yd = (df32*)w.fY, *Zd = (df32*)w.fQ, *Gd = (df32*)w.pG, *Wd = (df32*)w.fVw;
+  float *Y32 = (float*)w.fX, *R32 = (float*)w.fR, *Bt32 = (float*)w.fBt, *R2 = (float*)w.fR2;
+  auto gram = [&](const df32* X, int rows) {  // Gd = X^T X (r x r), X rows x r column-major
+    GemmArgs<df32> g;
+    g.M = r; g.N = r; g.K = rows;
+    g.A = X; g.am = IdxMap::lin(rows); g.ak = IdxMap::lin(1);
+    g.B = X; g.bn = IdxMap::lin(rows); g.bk = IdxMap::lin(1);
+    g.C = Gd; g.cm = IdxMap::lin(1); g.cn = IdxMap::lin(r);
+    gemm<df32>(h, g);
+  };
+  auto apply = [&](const df32* X, int rows, const df32* Wm, df32* out, df32 alpha, df32 beta) {  // out = a X Wm + b out
+    GemmArgs<df32> g;
+    g.M = rows; g.N = r; g.K = r;
+    g.A = X; g.am = IdxMap::lin(1); g.ak = IdxMap::lin(rows); g.a_kfast = false;
+    g.B = Wm; g.bn = IdxMap::lin(r); g.bk = IdxMap::lin(1);
+    g.C = out; g.cm = IdxMap::lin(1); g.cn = IdxMap::lin(rows);
+    g.alpha = alpha;
+    g.beta = beta;
+    gemm<df32>(h, g);
+  };
+  auto rqr = [&](int q, float* X, float* R) {  // R (r x r) of the FP32 Householder QR of X (q x r)
+    const bool cluster = q >= 128 && r >= 16;
+    CK(qr_householder<float, float>(q, r, X, cluster ? nullptr : (float*)w.fUM, R, w.st));
+  };
+  const df32* Q = nullptr;  // m x r orthonormal basis (null: the identity, r = m)
+  if (!ident) {
+    if (exact) {  // Y = Theta, column-major
+      copymap<df32, df32>(h, m, n, Th, IdxMap::lin(n), IdxMap::lin(1), Yd, IdxMap::lin(1), IdxMap::lin(m));
+    } else {  // Y = Theta Omega (m x r, column-major); Omega is n x r row-major, as in the oracle
+      CK(philox_fill<df32>(Om, (long long)n * r, h->seed, omega_stream(sweep, site1), 1.0, w.st));
+      GemmArgs<df32> g;
+      g.M = m; g.N = r; g.K = n;
+      g.A = Th; g.am = IdxMap::lin(n); g.ak = IdxMap::lin(1);
+      g.B = Om; g.bn = IdxMap::lin(1); g.bk = IdxMap::lin(r); g.b_kfast = false;
+      g.C = Yd; g.cm = IdxMap::lin(1); g.cn = IdxMap::lin(m);
+      gemm<df32>(h, g);
+    }
+    // FP32 preconditioner, twice: R of the scaled Y, inverted; Z1 = Y (2^-ey R^-1) has
+    // cond ~ eps32 cond(Y) (up to ~1e4 for the sketches of this fit), and the same step on
+    // Z1 leaves Z2 = Z1 R(Z1)^-1 within ~1e-3 of orthonormal
+    CK(absmax_exponent<df32>(Yd, (long long)m * r, ey, w.st));
+    CK(copy_pow2<df32, float>((long long)m * r, Yd, Y32, ey, w.st));
+    rqr(m, Y32, R32);
+    CK(tri_inv(r, R32, r, ey, Wd, w.errw, w.st));
+    apply(Yd, m, Wd, Zd, df32(1.f, 0.f), df32(0.f, 0.f));
+    copymap<df32, float>(h, m, r, Zd, IdxMap::lin(1), IdxMap::lin(m), Y32, IdxMap::lin(1), IdxMap::lin(m));
+    rqr(m, Y32, R32);
+    CK(tri_inv(r, R32, r, nullptr, Wd, w.errw, w.st));
+    apply(Zd, m, Wd, Yd, df32(1.f, 0.f), df32(0.f, 0.f));
+    df32 *X = Yd, *Xn = Zd;
+    for (int it = 0; it < 3; ++it) {  // X <- X (3 I - X^T X) / 2; |X^T X - I| ~1e-3 -> 1e-6 -> 1e-12 -> rounding
+      gram(X, m);
+      if (it == 2) CK(ortho_check(r, Gd, 1e-6, w.errw, w.st));
+      CK(cudaMemcpyAsync(Xn, X, sizeof(df32) * (size_t)m * r, cudaMemcpyDeviceToDevice, w.st));
+      apply(X, m, Gd, Xn, df32(-0.5f, 0.f), df32(1.5f, 0.f));
+      std::swap(X, Xn);
+    }
+    Q = X;
+  }
+  // B^T = Theta^T Q (n x r, column-major; Theta itself when the basis is the identity), its FP32
+  // copy scaled by 2^-e (e of Theta), R-only QR
+  const df32* Btd = Th;  // row-major m x n Theta is column-major n x m Theta^T
+  if (!ident) {
+    df32* bt = (df32*)w.fQ2;
+    GemmArgs<df32> g;
+    g.M = n; g.N = r; g.K = m;
+    g.A = Th; g.am = IdxMap::lin(1); g.ak = IdxMap::lin(n); g.a_kfast = false;
+    g.B = Q; g.bn = IdxMap::lin(m); g.bk = IdxMap::lin(1);
+    g.C = bt; g.cm = IdxMap::lin(1); g.cn = IdxMap::lin(n);
+    gemm<df32>(h, g);
+    Btd = bt;
+  }
+  CK(copy_pow2<df32, float>((long long)n * r, Btd, Bt32, ex, w.st));
+  rqr(n, Bt32, R2);
+  // B = R2^T Q2^T: the left singular vectors U_B of B are the right ones of R2
+  float *fX = (float*)w.fX, *fU = (float*)w.fU, *fV = (float*)w.fV, *fS = (float*)w.fS, *fVw = (float*)w.fVw;
+  if (need == 1) {  // one-sided Jacobi on R2^T: U_B = its normalised columns
+    copymap<float, float>(h, r, r, R2, IdxMap::lin(1), IdxMap::lin(r), fX, IdxMap::lin(r), IdxMap::lin(1));
+    CK(jacobi_svd<float, float>(r, r, fX, fV, fS, nullptr, fVw, 60, w.errw, w.st));
+  } else {          // on R2: U_B = the accumulated rotations
+    CK(jacobi_svd<float, float>(r, r, R2, fU, fS, fV, fVw, 60, w.errw, w.st));
+  }
+  // U_M = Q U_B; V_M = B^T U_B S^-1 (S of 2^-e B, so the scale 2^-e comes back in)
+  df32* UBd = (df32*)w.fR;
+  copymap<float, df32>(h, r, r, fV, IdxMap::lin(r), IdxMap::lin(1), UBd, IdxMap::lin(r), IdxMap::lin(1));
+  if (ident) {
+    CK(cudaMemcpyAsync(w.fUM, UBd, sizeof(df32) * (size_t)r * r, cudaMemcpyDeviceToDevice, w.st));
+  } else {
+    GemmArgs<df32> g;
+    g.M = m; g.N = r; g.K = r;
+    g.A = Q; g.am = IdxMap::lin(1); g.ak = IdxMap::lin(m); g.a_kfast = false;
+    g.B = UBd; g.bn = IdxMap::lin(r); g.bk = IdxMap::lin(1);
+    g.C = (df32*)w.fUM; g.cm = IdxMap::lin(1); g.cn = IdxMap::lin(m);
+    gemm<df32>(h, g);
+  }
+  if (need != 1) {
+    df32* Dd = (df32*)w.fVw;
+    CK(scale_cols_inv(r, r, fV, fS, ex, Dd, w.st));
+    GemmArgs<df32> g;
+    g.M = n; g.N = r; g.K = r;
+    g.A = Btd; g.am = IdxMap::lin(1); g.ak = IdxMap::lin(n); g.a_kfast = false;
+    g.B = Dd; g.bn = IdxMap::lin(r); g.bk = IdxMap::lin(1);
+    g.C = (df32*)w.fVM; g.cm = IdxMap::lin(1); g.cn = IdxMap::lin(n);
+    gemm<df32>(h, g);
+  }
+  CK(fix_signs<df32>(m, n, r, (df32*)w.fUM, m, need != 1 ? (df32*)w.fVM : nullptr, n, w.st));
+  w.hp = true;
+  return r;
+}
+
 template <typename T, typename F>
 int factorize_body(tt_fit* h, int m, int n, int sweep, int site1, int need) {
+  W(h).hp = false;
   F *fX = (F*)W(h).fX, *fQ = (F*)W(h).fQ, *fR = (F*)W(h).fR, *fU = (F*)W(h).fU, *fV = (F*)W(h).fV, *fVw = (F*)W(h).fVw;
   F *fS = (F*)W(h).fS, *fUM = (F*)W(h).fUM, *fVM = (F*)W(h).fVM, *fOm = (F*)W(h).fOm, *MF = (F*)W(h).fY;
   F *fBt = (F*)W(h).fBt, *fQ2 = (F*)W(h).fQ2, *fR2 = (F*)W(h).fR2;
@@ -686,6 +839,11 @@ int factorize_body(tt_fit* h, int m, int n, int sweep, int site1, int need) {
   CK(frob_norm<F>(MF, (long long)m * n, W(h).dnorm, W(h).errw, W(h).st));
   const int ks = h->chi_max + h->oversample;
   if (h->update == TT_UPDATE_2SITE_RSVD && ks < std::min(m, n)) {
+    if constexpr (std::is_same<T, df32>::value && std::is_same<F, float>::value) {
+      if (h->hp_sweep && !W(h).hp_off && ks >= 16 && ks <= TRI_INV_MAX && std::min(m, n) >= 128 &&
+          std::max(m, n) <= 1024)
+        return factorize_hp(h, m, n, sweep, site1, need, false);
+    }
     CK(philox_fill<F>(fOm, (long long)n * ks, h->seed, omega_stream(sweep, site1), 1.0, W(h).st));
     GemmArgs<F> g;  // Ysk = M Omega (m x ks, col-major)
     g.M = m; g.N = ks; g.K = n;
@@ -731,6 +889,12 @@ int factorize_body(tt_fit* h, int m, int n, int sweep, int site1, int need) {
     gemm<F>(h, g4);
     CK(fix_signs<F>(m, n, ks, fUM, m, fVM, n, W(h).st));
     return ks;
+  }
+  if constexpr (std::is_same<T, df32>::value && std::is_same<F, float>::value) {
+    // an exact factorisation keeps the whole range of a tall Theta: its basis in FP64-class
+    // arithmetic too (a wide one needs none)
+    if (h->hp_sweep && !W(h).hp_off && std::min(m, n) <= TRI_INV_MAX && std::max(m, n) <= 1024)
+      return factorize_hp(h, m, n, sweep, site1, need, true);
   }
   // exact: work on the tall orientation X (q x p col-major)
   const bool tr = m < n;
@@ -789,29 +953,33 @@ int factorize(tt_fit* h, int m, int n, int sweep, int site1, int need = 3) {
 // ---------------------------------------------------------------------------
 constexpr int kNewtonSchulzSteps = 2;
 
-template <typename F>
-void ns_orthonormalize(tt_fit* h, const F* X32, int rows, int k, double* X64) {
-  double* G = W(h).pG;
-  double* X = W(h).pT;
-  copymap<F, double>(h, rows, k, X32, IdxMap::lin(1), IdxMap::lin(rows), X, IdxMap::lin(1), IdxMap::lin(rows));
+// The steps run in double-FP32 (about 4x the FP64 rate of this GPU; rounding
+// ~1e-14, far below what the sweeps resolve). X64 serves as the second buffer.
+template <typename Fin>
+void ns_orthonormalize(tt_fit* h, const Fin* Xin, int rows, int k, double* X64) {
+  df32* G = (df32*)W(h).pG;
+  df32 *X = (df32*)W(h).pT, *Xn = (df32*)X64;
+  copymap<Fin, df32>(h, rows, k, Xin, IdxMap::lin(1), IdxMap::lin(rows), X, IdxMap::lin(1), IdxMap::lin(rows));
   for (int it = 0; it < kNewtonSchulzSteps; ++it) {
-    if (it > 0) CK(cudaMemcpyAsync(X, X64, sizeof(double) * (size_t)rows * k, cudaMemcpyDeviceToDevice, W(h).st));
-    GemmArgs<double> g;  // G = X^T X (k x k)
+    GemmArgs<df32> g;  // G = X^T X (k x k)
     g.M = k; g.N = k; g.K = rows;
     g.A = X; g.am = IdxMap::lin(rows); g.ak = IdxMap::lin(1);
     g.B = X; g.bn = IdxMap::lin(rows); g.bk = IdxMap::lin(1);
     g.C = G; g.cm = IdxMap::lin(k); g.cn = IdxMap::lin(1);
-    gemm<double>(h, g);
-    CK(cudaMemcpyAsync(X64, X, sizeof(double) * (size_t)rows * k, cudaMemcpyDeviceToDevice, W(h).st));
-    GemmArgs<double> g2;  // X64 = 1.5 X - 0.5 X G
+    gemm<df32>(h, g);
+    CK(cudaMemcpyAsync(Xn, X, sizeof(df32) * (size_t)rows * k, cudaMemcpyDeviceToDevice, W(h).st));
+    GemmArgs<df32> g2;  // Xn = 1.5 X - 0.5 X G
     g2.M = rows; g2.N = k; g2.K = k;
     g2.A = X; g2.am = IdxMap::lin(1); g2.ak = IdxMap::lin(rows); g2.a_kfast = false;
     g2.B = G; g2.bn = IdxMap::lin(k); g2.bk = IdxMap::lin(1);
-    g2.C = X64; g2.cm = IdxMap::lin(1); g2.cn = IdxMap::lin(rows);
-    g2.alpha = -0.5;
-    g2.beta = 1.5;
-    gemm<double>(h, g2);
+    g2.C = Xn; g2.cm = IdxMap::lin(1); g2.cn = IdxMap::lin(rows);
+    g2.alpha = df32(-0.5f, 0.f);
+    g2.beta = df32(1.5f, 0.f);
+    gemm<df32>(h, g2);
+    std::swap(X, Xn);
   }
+  // the result is in X: convert in place if it is X64 already, else copy across
+  copymap<df32, double>(h, rows, k, X, IdxMap::lin(1), IdxMap::lin(rows), X64, IdxMap::lin(1), IdxMap::lin(rows));
 }
 
 template <typename T, typename F>
@@ -868,6 +1036,18 @@ void polish_update(tt_fit* h, int mode, int m, int n, int k, int l) {
     CK(inverse_gauge_update<T>(m, n, k, W(h).pU, W(h).pV, Pk, h->C64[l], h->C64[l + 1], h->Y[l + 1], W(h).st));
     CK(frob_norm<T>(Pk, (long long)k * k, h->dn2 + l, nullptr, W(h).st));
   }
+}
+
+// Whether the next sweep forms the randomized sketch basis in FP64-class
+// arithmetic (fast_factor 3: always; 1: once the previous sweep changed ||C||^2
+// by at most kHpDelta, i.e. near convergence, so that the sweeps that decide
+// the converged C are FP64-class while the early ones keep the all-FP32
+// update; the sweep map contracts what the early sweeps leave, and an accurate
+// sweep from their state lands on the accurate fixed point).
+constexpr double kHpDelta = 1e-3;
+inline bool use_hp_basis(const tt_fit* h) {
+  if (h->fast_factor == 3) return true;
+  return h->fast_factor == 1 && h->delta <= kHpDelta;
 }
 
 template <typename T>
@@ -937,6 +1117,28 @@ struct Sweeper {
     CK(cudaMemcpyAsync(W(h).hdinfo, W(h).ddinfo, 2 * sizeof(double), cudaMemcpyDeviceToHost, W(h).st));
     CK(cudaMemcpyAsync(W(h).herrw, W(h).errw, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, W(h).st));
     CK(cudaStreamSynchronize(W(h).st));
+    if (*W(h).herrw & ERRW_HPFAIL) {
+      // the FP64-class sketch basis could not be formed (a rank-deficient sketch): clear the
+      // flag and factorise this window again with the all-FP32 randomized update
+      CK(cudaMemsetAsync(W(h).errw, 0, sizeof(uint32_t), W(h).st));
+      W(h).hp_off = true;
+      const bool left_only = h->gauge != TT_GAUGE_INVERSE_CANONICAL && fwd;
+      try {
+        p = factorize<T, float>(h, m, n, sweep, l + 1, left_only ? 1 : 3);
+      } catch (...) {
+        W(h).hp_off = false;
+        throw;
+      }
+      W(h).hp_off = false;
+      CK(truncate_rule<float>((const float*)W(h).fS, p, W(h).dnorm, h->tol / L, h->chi_max, h->cutoff, W(h).dk,
+                              W(h).ddinfo, W(h).st));
+      CK(cudaEventRecord(W(h).ev[4], W(h).st));
+      CK(cudaMemcpyAsync(W(h).hk, W(h).dk, sizeof(int), cudaMemcpyDeviceToHost, W(h).st));
+      CK(cudaMemcpyAsync(W(h).hdinfo, W(h).ddinfo, 2 * sizeof(double), cudaMemcpyDeviceToHost, W(h).st));
+      CK(cudaMemcpyAsync(W(h).herrw, W(h).errw, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, W(h).st));
+      CK(cudaStreamSynchronize(W(h).st));
+      ++W(h).hp_fallbacks;
+    }
     add(2, 0, 1);
     add(0, 1, 2);
     add(1, 2, 3);
@@ -966,7 +1168,8 @@ struct Sweeper {
       CK(gauge_update<T, FX>(mode, m, n, (const FX*)W(h).fUM, m, (const FX*)W(h).fS, (const FX*)W(h).fVM, n, W(h).dk, h->C64[l],
                             h->C64[l + 1], h->Y[l + 1], (T*)h->Ut[l], (T*)h->Vt[l + 1], W(h).st));
     } else {
-      polish_update<T, float>(h, mode, m, n, k, l);
+      if (W(h).hp) polish_update<T, df32>(h, mode, m, n, k, l);
+      else polish_update<T, float>(h, mode, m, n, k, l);
     }
     CK(cudaEventRecord(W(h).ev[6], W(h).st));
     W(h).gauge_pending = true;
@@ -994,6 +1197,7 @@ struct Sweeper {
     for (int s = 0; s < n_sweeps; ++s) {
       if (h->converged) break;
       const int sweep = h->sweeps_done;
+      h->hp_sweep = use_hp_basis(h);
       double n2 = 0, disc = 0, maxd = 0;
       if (h->forward) {
         for (int l = 0; l <= L - 2; ++l) {
@@ -1550,6 +1754,7 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
     if (o.precision == TT_PREC_BF16_SPLIT) return TT_ERR_INVALID_ARGUMENT;  // reserved, not implemented
     if (o.n_segments > 1 && gauge != TT_GAUGE_INVERSE_CANONICAL) return TT_ERR_INVALID_ARGUMENT;
     if (o.edge_extra < 0) return TT_ERR_INVALID_ARGUMENT;
+    if (o.fast_factor < 0 || o.fast_factor > 3) return TT_ERR_INVALID_ARGUMENT;
     int LA, LB;
     std::vector<int> doA, diA, bA, doB, diB, bB;
     read_desc(A, LA, doA, diA, bA);
@@ -1577,6 +1782,7 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
     h->use_f32 = (o.precision != TT_PREC_FP64 && o.precision != TT_PREC_DF32);
     h->use_df = (o.precision == TT_PREC_DF32);
     h->fact_f32 = h->use_f32 || o.fast_factor;
+    h->fast_factor = o.fast_factor;
     h->cutoff_user = o.sv_cutoff >= 0;
     h->cutoff = h->cutoff_user ? o.sv_cutoff : default_cutoff(o.precision, h->fact_f32);
     h->conv_tol = o.conv_tol >= 0 ? o.conv_tol : tol;
@@ -1763,6 +1969,7 @@ tt_status tt_fit_sweep(tt_fit* h, int n_sweeps, tt_sweep_report* rep) {
       for (int s = 0; s < n_sweeps && !h->converged; ++s) {
         const int ph = h->phases_done % 2;
         double maxd = 0;
+        h->hp_sweep = use_hp_basis(h);
         const double n2 = h->use_f32  ? run_phase<float>(h, ph, h->phases_done, maxd)
                           : h->use_df ? run_phase<df32>(h, ph, h->phases_done, maxd)
                                       : run_phase<double>(h, ph, h->phases_done, maxd);
@@ -1862,6 +2069,7 @@ tt_status tt_fit_result(const tt_fit* hc, tt_mpo_desc* C, double* lambdas) {
 
 tt_status tt_fit_set_precision(tt_fit* h, int precision, int fast_factor) {
   if (!h || precision < 0 || precision > 5 || precision == TT_PREC_BF16_SPLIT) return TT_ERR_INVALID_ARGUMENT;
+  if (fast_factor < 0 || fast_factor > 3) return TT_ERR_INVALID_ARGUMENT;
   if (h->poisoned) return TT_ERR_STATE;
   if (h->segs.size() > 1 && h->phases_done % 2 != 0) {
     h->last_error = "tt_fit_set_precision: a segment-parallel fit switches between full sets of local sweeps";
@@ -1874,6 +2082,7 @@ tt_status tt_fit_set_precision(tt_fit* h, int precision, int fast_factor) {
     h->use_f32 = f32;
     h->use_df = precision == TT_PREC_DF32;
     h->fact_f32 = f32 || fast_factor;
+    h->fast_factor = fast_factor;
     if (!h->cutoff_user) h->cutoff = default_cutoff(precision, h->fact_f32);
     h->converged = false;
     if (f32) rebuild_chain<float>(h);

@@ -145,8 +145,8 @@ cudaError_t gemm_simt(const GemmArgs<T>& g, T* ws, size_t ws_elems, int sm_count
   // split keeps at least kmin k-steps: a tile's time is bound by its SM's
   // arithmetic rate, which for FP64 is 1/64 of the FP32 rate on this GPU (and
   // a df32 multiply-add takes 15 FP32 instructions), so the small GEMMs of
-  // those types split deeper
-  const int kmin = std::is_same<T, double>::value ? 16 : (std::is_same<T, df32>::value ? 64 : 256);
+  // those types split down to one k-tile per CTA
+  const int kmin = (std::is_same<T, double>::value || std::is_same<T, df32>::value) ? 16 : 256;
   while (tiles * splits < 2 * sm_count && g.K / (splits * 2) >= kmin &&
          (size_t)(splits * 2) * g.M * g.N <= ws_elems)
     splits *= 2;

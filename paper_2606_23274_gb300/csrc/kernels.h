@@ -119,4 +119,15 @@ cudaError_t unscale_pow2(int p, F* s, double* nrm, const int* e, cudaStream_t st
 template <typename T>
 cudaError_t scale_cols_t(int rows, int cols, const double* in, const double* y, T* out, cudaStream_t st);
 
+// Inverse of an FP32 upper-triangular R (p x p, ld ldr) for the FP64-class
+// randomized update (linalg.cu), scaled by 2^-*eexp (eexp may be null):
+// out p x p column-major double-FP32. p <= TRI_INV_MAX.
+constexpr int TRI_INV_MAX = 160;
+cudaError_t tri_inv(int p, const float* R, int ldr, const int* eexp, df32* out, uint32_t* errw, cudaStream_t st);
+// out = in diag(2^-e / s) in double-FP32 (in, out: rows x cols column-major)
+cudaError_t scale_cols_inv(int rows, int cols, const float* in, const float* s, const int* eexp, df32* out,
+                           cudaStream_t st);
+// ERRW_HPFAIL when max |G - I| > tol (G: p x p double-FP32)
+cudaError_t ortho_check(int p, const df32* G, double tol, uint32_t* errw, cudaStream_t st);
+
 }  // namespace ttfit

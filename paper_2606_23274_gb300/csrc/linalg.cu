@@ -620,6 +620,7 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
   cl.sync();  // no CTA reads another's partial W of the last panel any more
   C* Qm = sm + Lay.Qm;
   C* Vmy = sm + Lay.Vmy;
+  if (Qg != nullptr) {  // R-only calls (Qg == nullptr, uniform over the cluster) skip the formation of Q
   for (int i = tid & 63; i < rb; i += 64)
     for (int c = tid >> 6; c < r; c += 4) Qm[(size_t)c * ld + i] = (r0 + i == c) ? C(1) : C(0);
   for (int pn = npan - 1; pn >= 0; --pn) {
@@ -692,6 +693,7 @@ __global__ void __cluster_dims__(JQ, 1, 1) __launch_bounds__(256)
 #pragma unroll 4
     for (int c = tid >> 6; c < r; c += 4)
       Qg[(size_t)c * q + r0 + i] = (S)(qneg(diag[c]) ? -Qm[(size_t)c * ld + i] : Qm[(size_t)c * ld + i]);
+  }
   for (int i = tid & 63; i < nr; i += 64) {
     const int gi = r0 + i;
     if (gi >= r) continue;
@@ -722,6 +724,7 @@ cudaError_t qr_householder(int q, int p, S* X, S* Q, S* R, cudaStream_t st) {
   if (min(q, p) > 1024 || q > 1024) return cudaErrorInvalidValue;
   if constexpr (std::is_same<C, S>::value) {  // rows spread over a cluster when the matrix is large enough
     const size_t bsm = qr_cluster_blocked_smem<C>(q, p);
+    if (Q == nullptr && !(q >= 128 && p >= 16 && bsm <= 220 * 1024)) return cudaErrorInvalidValue;
     if (q >= 128 && p >= 16 && bsm <= 220 * 1024) {
       auto launch = [&](auto kern) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
@@ -746,6 +749,7 @@ cudaError_t qr_householder(int q, int p, S* X, S* Q, S* R, cudaStream_t st) {
       return cudaGetLastError();
     }
   }
+  if (Q == nullptr) return cudaErrorInvalidValue;  // only the cluster kernel has an R-only mode
   ++tl_launches;
   if (q <= 128) qr_house_kernel<C, S, 4><<<1, 1024, 0, st>>>(q, p, X, Q, R);
   else if (q <= 256) qr_house_kernel<C, S, 8><<<1, 1024, 0, st>>>(q, p, X, Q, R);
@@ -1457,6 +1461,8 @@ template cudaError_t copy_map<float, double>(int, int, const float*, IdxMap, Idx
                                              cudaStream_t);
 template cudaError_t copy_map<float, float>(int, int, const float*, IdxMap, IdxMap, float*, IdxMap, IdxMap, double,
                                             cudaStream_t);
+template cudaError_t copy_map<float, df32>(int, int, const float*, IdxMap, IdxMap, df32*, IdxMap, IdxMap, double,
+                                           cudaStream_t);
 template cudaError_t copy_map<double, df32>(int, int, const double*, IdxMap, IdxMap, df32*, IdxMap, IdxMap, double,
                                             cudaStream_t);
 template cudaError_t copy_map<df32, double>(int, int, const df32*, IdxMap, IdxMap, double*, IdxMap, IdxMap, double,
@@ -1484,6 +1490,7 @@ cudaError_t philox_fill(F* out, long long count, uint64_t seed, uint64_t stream,
 }
 template cudaError_t philox_fill<double>(double*, long long, uint64_t, uint64_t, double, cudaStream_t);
 template cudaError_t philox_fill<float>(float*, long long, uint64_t, uint64_t, double, cudaStream_t);
+template cudaError_t philox_fill<df32>(df32*, long long, uint64_t, uint64_t, double, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Sign convention of singular pair j: the entry of largest magnitude of u_j is
@@ -1545,6 +1552,7 @@ cudaError_t fix_signs(int m, int n, int p, F* U, int ld_u, F* V, int ld_v, cudaS
 }
 template cudaError_t fix_signs<double>(int, int, int, double*, int, double*, int, cudaStream_t);
 template cudaError_t fix_signs<float>(int, int, int, float*, int, float*, int, cudaStream_t);
+template cudaError_t fix_signs<df32>(int, int, int, df32*, int, df32*, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Alg. 4 from FP64 isometries U (m x k), V (n x k) (column-major) and the
@@ -1753,4 +1761,164 @@ cudaError_t unscale_pow2(int p, F* s, double* nrm, const int* e, cudaStream_t st
 }
 template cudaError_t unscale_pow2<float>(int, float*, double*, const int*, cudaStream_t);
 template cudaError_t unscale_pow2<double>(int, double*, double*, const int*, cudaStream_t);
+}  // namespace ttfit
+
+namespace ttfit {
+
+// ---------------------------------------------------------------------------
+// Inverse of a small upper-triangular factor in FP32, written in double-FP32,
+// for the basis of the randomized update (see engine.cu, factorize_rsvd_hp):
+// R is the p x p upper-triangular factor of a Householder QR (FP32,
+// column-major, ld ldr); out = 2^-e R^-1 with e = *eexp (0 if null). Any
+// non-singular right factor keeps the column space of the matrix it
+// multiplies, so FP32 accuracy suffices: the range is carried by the
+// double-FP32 product that applies it. For the same reason a pivot below
+// 2^-24 max |r_ii| (a sketch column in the noise of the others) is raised to
+// that floor instead of stopping the factorisation. One CTA; R and X = R^-1
+// live in shared memory (2 p^2 floats). Bottom-up by panels of TI_B rows: the
+// rows of a panel are finished column by column (one thread per column,
+// back substitution inside the panel: x_i = (e_i - acc_i - sum r_il x_l) / r_ii),
+// then every row above takes the panel's rank-TI_B update acc_r += sum_i r_ri x_i.
+// Only a non-finite or all-zero R sets ERRW_HPFAIL.
+// ---------------------------------------------------------------------------
+constexpr int TI_B = 8;
+
+__global__ void __launch_bounds__(1024) tri_inv_kernel(int p, const float* __restrict__ R, int ldr, const int* eexp,
+                                                       df32* __restrict__ out, uint32_t* errw) {
+  extern __shared__ __align__(16) float tis[];
+  float* A = tis;           // R, column-major p x p
+  float* X = tis + p * p;   // accumulators, then rows of R^-1
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < p * p; e += nt) {
+    const int i = e % p, j = e / p;
+    A[e] = i <= j ? R[(size_t)j * ldr + i] : 0.f;
+    X[e] = 0.f;
+  }
+  __syncthreads();
+  float big = 0.f;  // max |r_ii|, the same in every thread
+  bool finite = true;
+  for (int i = 0; i < p; ++i) {
+    const float d = A[i * p + i];
+    finite = finite && isfinite(d);
+    big = fmaxf(big, fabsf(d));
+  }
+  const float floor_ = big * 0x1p-24f;
+  const bool bad = !finite || !(big > 0.f);
+  for (int i0 = ((p - 1) / TI_B) * TI_B; i0 >= 0; i0 -= TI_B) {
+    const int i1 = min(p, i0 + TI_B);  // panel rows i0 .. i1-1
+    for (int c = i0 + tid; c < p; c += nt) {  // finish the panel's rows of column c, bottom-up
+      float xv[TI_B];
+#pragma unroll
+      for (int t = TI_B - 1; t >= 0; --t) {
+        const int i = i0 + t;
+        if (i >= i1 || c < i) {
+          xv[t] = 0.f;
+          continue;
+        }
+        float acc = X[c * p + i];
+#pragma unroll
+        for (int u = t + 1; u < TI_B; ++u)
+          if (i0 + u < i1) acc = fmaf(A[(i0 + u) * p + i], xv[u], acc);
+        float rii = A[i * p + i];
+        if (!(fabsf(rii) >= floor_)) rii = floor_ > 0.f ? floor_ : 1.f;
+        xv[t] = ((c == i ? 1.f : 0.f) - acc) / rii;
+      }
+#pragma unroll
+      for (int t = 0; t < TI_B; ++t)
+        if (i0 + t < i1) X[c * p + i0 + t] = xv[t];
+    }
+    __syncthreads();
+    const long long cnt = (long long)i0 * (p - i0);  // rows r < i0 of columns c >= i0
+    for (long long e = tid; e < cnt; e += nt) {
+      const int r = (int)(e % i0), c = i0 + (int)(e / i0);
+      float acc = X[c * p + r];
+#pragma unroll
+      for (int t = 0; t < TI_B; ++t)
+        if (i0 + t < i1) acc = fmaf(A[(i0 + t) * p + r], X[c * p + i0 + t], acc);
+      X[c * p + r] = acc;
+    }
+    __syncthreads();
+  }
+  const int ex = eexp ? *eexp : 0;
+  for (int e = tid; e < p * p; e += nt) {
+    const int i = e % p, j = e / p;
+    out[e] = df32(i <= j ? scalbnf(X[e], -ex) : 0.f, 0.f);
+  }
+  if (bad && tid == 0 && errw) atomicOr(errw, ERRW_HPFAIL);
+}
+
+cudaError_t tri_inv(int p, const float* R, int ldr, const int* eexp, df32* out, uint32_t* errw, cudaStream_t st) {
+  if (p <= 0) return cudaSuccess;
+  const size_t smem = 2 * (size_t)p * p * sizeof(float);
+  if (p > TRI_INV_MAX || smem > 220 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(tri_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  ++tl_launches;
+  tri_inv_kernel<<<1, 1024, smem, st>>>(p, R, ldr, eexp, out, errw);
+  return cudaGetLastError();
+}
+
+// out (rows x cols, column-major, double-FP32) = in (FP32, column-major, ld rows) with
+// column j scaled by 2^-e / s_j (0 where s_j = 0); e = *eexp.
+__global__ void scale_cols_inv_kernel(int rows, int cols, const float* __restrict__ in, const float* __restrict__ s,
+                                      const int* eexp, df32* __restrict__ out) {
+  const long long tot = (long long)rows * cols;
+  const int ex = eexp ? *eexp : 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e / rows);
+    const float sj = s[j];
+    // 1 / s_j as a double-FP32 reciprocal: r0 = 1/s, r1 = r0 (2 - s r0) rounded split (Newton's method)
+    df32 v(0.f, 0.f);
+    if (sj != 0.f) {
+      const float r0 = 1.f / sj;
+      const float res = __fmaf_rn(-sj, r0, 1.f);  // 1 - s r0, exact by FMA
+      v = renorm(r0, r0 * res) * df32(in[e], 0.f);
+      v = df32(scalbnf(v.hi, -ex), scalbnf(v.lo, -ex));
+    }
+    out[e] = v;
+  }
+}
+
+cudaError_t scale_cols_inv(int rows, int cols, const float* in, const float* s, const int* eexp, df32* out,
+                           cudaStream_t st) {
+  const long long tot = (long long)rows * cols;
+  if (tot <= 0) return cudaSuccess;
+  int blocks = (int)((tot + 255) / 256);
+  if (blocks > 1024) blocks = 1024;
+  ++tl_launches;
+  scale_cols_inv_kernel<<<blocks, 256, 0, st>>>(rows, cols, in, s, eexp, out);
+  return cudaGetLastError();
+}
+
+// max |G - I| of a p x p double-FP32 matrix; sets ERRW_HPFAIL above tol.
+__global__ void ortho_check_kernel(int p, const df32* __restrict__ G, double tol, uint32_t* errw) {
+  float worst = 0.f;
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int i = e % p, j = e / p;
+    const df32 d = G[e] - df32(i == j ? 1.f : 0.f, 0.f);
+    const float a = fabsf(d.hi);
+    worst = (a > worst || !isfinite(a)) ? (isfinite(a) ? a : INFINITY) : worst;
+  }
+  worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, 16));
+  worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, 8));
+  worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, 4));
+  worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, 2));
+  worst = fmaxf(worst, __shfl_xor_sync(0xffffffffu, worst, 1));
+  __shared__ float red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = worst;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float w = 0.f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) w = fmaxf(w, red[i]);
+    if (!(w <= (float)tol) && errw) atomicOr(errw, ERRW_HPFAIL);
+  }
+}
+
+cudaError_t ortho_check(int p, const df32* G, double tol, uint32_t* errw, cudaStream_t st) {
+  if (p <= 0) return cudaSuccess;
+  ++tl_launches;
+  ortho_check_kernel<<<1, 1024, 0, st>>>(p, G, tol, errw);
+  return cudaGetLastError();
+}
+
 }  // namespace ttfit

@@ -169,7 +169,7 @@ def _options(update="svd", oversample=10, seed=0, precision="fp64", init="random
     o.stream = ct.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     o.prepare_inputs = 1 if prepare_inputs else 0
     o.fault_inject = int(fault_inject)
-    o.fast_factor = 1 if fast_factor else 0
+    o.fast_factor = int(fast_factor)
     o.n_segments = int(n_segments)
     o.edge_extra = int(edge_extra)
     return o, dC
@@ -375,7 +375,7 @@ class Fit:
     def set_precision(self, precision, fast_factor=False):
         """Switch the contraction precision for the following sweeps (see include/ttfit.h)."""
         prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
-        _check(load().tt_fit_set_precision(self.h, prec, 1 if fast_factor else 0), self.h, "tt_fit_set_precision")
+        _check(load().tt_fit_set_precision(self.h, prec, int(fast_factor)), self.h, "tt_fit_set_precision")
 
     def stage_times(self) -> dict:
         v = (ct.c_double * 7)()

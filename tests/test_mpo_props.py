@@ -48,3 +48,22 @@ def test_diff_norm_matches_dense_and_oracle():
     dz = np.linalg.norm(to_dense(X) - to_dense(Z))
     assert np.isclose(diff_norm(_t(X), _t(Z)), dz, rtol=1e-5)
     assert diff_norm(_t(X), _t(X)) <= 1e-14 * np.linalg.norm(to_dense(X))
+
+
+def test_bench_rel_frobenius_matches_oracle():
+    """bench.py's accuracy figure ||X - Y||_F / ||Y||_F (torch, QR sweep) against the oracle's
+    stable difference norm and against dense matrices."""
+    import importlib
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    bench = importlib.import_module("bench")
+    from oracle.mpo import mpo_diff_norm, mpo_norm
+    X = gaussian_mpo(6, 2, 3, 21, 0, 0.7)
+    Y = [x.copy() for x in X]
+    Y[2] = Y[2] + 1e-7 * gaussian_mpo(6, 2, 3, 21, 1, 0.7)[2]
+    got = bench.rel_frobenius(_t(X), _t(Y))
+    ref = mpo_diff_norm(X, Y) / mpo_norm(Y)
+    dense = np.linalg.norm(to_dense(X) - to_dense(Y)) / np.linalg.norm(to_dense(Y))
+    assert np.isclose(got, ref, rtol=1e-6) and np.isclose(got, dense, rtol=1e-5)
+    assert bench.rel_frobenius(_t(X), _t(X)) <= 1e-14
