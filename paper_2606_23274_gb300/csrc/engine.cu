@@ -242,7 +242,8 @@ struct tt_fit {
   bool use_df = false;
   bool fact_f32 = false;  // FP32 factorisation + FP64 polish (always for float chains; optional for FP64)
   int fast_factor = 0;    // tt_fit_options.fast_factor of the current precision (1, 3: FP64-class sketch basis)
-  bool hp_sweep = false;  // the current sweep uses the FP64-class sketch basis (factorize_rsvd_hp)
+  bool hp_sweep = false;  // the current sweep uses the FP64-class sketch basis (factorize_hp)
+  int escale = 0;         // the fit runs on 2^-ea A, 2^-eb B; C, its spectra and norm get 2^escale back
   bool use_oz = true;     // DF32 chains: contractions on the tensor cores by the digit split
   std::vector<void*> chain_bufs;  // buffers rebuilt when the chain precision changes
 };
@@ -1828,6 +1829,30 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
       qr_sweep(h, PB, h->B64, D.b, D.du, D.dt);
       finish_prep(h, PA);
       finish_prep(h, PB);
+      // A and B are now left-canonical with their norms in the last cores. The fit is equivariant
+      // in the scale of A and B, so those cores are scaled by powers of two (exact) to norm ~1
+      // and the scale is given back to C on export: long chains of normalised random cores
+      // (||A B|| ~ 0.2^L) then stay inside the range of the FP32 / double-FP32 chains
+      auto unit = [&](std::vector<double*>& X, const std::vector<int>& bd, const std::vector<int>& d1,
+                      const std::vector<int>& d2) {
+        const int j = LA - 1;
+        const long long n = prodll({bd[j], d1[j], d2[j], bd[j + 1]});
+        CK(frob_norm<double>(X[j], n, W(h).dnorm, nullptr, W(h).st));
+        double nrm = 0;
+        CK(cudaMemcpyAsync(&nrm, W(h).dnorm, sizeof(double), cudaMemcpyDeviceToHost, W(h).st));
+        CK(cudaStreamSynchronize(W(h).st));
+        if (!(nrm > 0.0) || !std::isfinite(nrm)) return 0;
+        const int e = (int)std::lround(std::log2(nrm));
+        if (e == 0) return 0;
+        double* y = h->pool.alloc<double>(n);
+        CK(copy_map<double, double>(1, (int)n, X[j], IdxMap::lin(0), IdxMap::lin(1), y, IdxMap::lin(0), IdxMap::lin(1),
+                                    std::ldexp(1.0, -e), W(h).st));
+        CK(cudaStreamSynchronize(W(h).st));
+        h->pool.release(X[j]);
+        X[j] = y;
+        return e;
+      };
+      h->escale = unit(h->A64, D.a, D.ds, D.du) + unit(h->B64, D.b, D.du, D.dt);
     }
     // capacity of C bonds: min(chi_max, prod of local dims to the left / right)
     const int L = LA;
@@ -2008,7 +2033,7 @@ tt_status tt_fit_sweep(tt_fit* h, int n_sweeps, tt_sweep_report* rep) {
     rep->sweeps_done = h->sweeps_done;
     rep->converged = h->converged ? 1 : 0;
     rep->delta = h->delta;
-    rep->norm2_C = h->segs.size() > 1 ? h->cur_n2 : h->last_n2;
+    rep->norm2_C = std::ldexp(h->segs.size() > 1 ? h->cur_n2 : h->last_n2, 2 * h->escale);
     rep->max_discarded = h->max_disc;
     rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
@@ -2033,11 +2058,12 @@ tt_status tt_fit_result(const tt_fit* hc, tt_mpo_desc* C, double* lambdas) {
   }
   for (int l = 0; l <= L; ++l) bond[l] = D.c[l];
   try {
+    const double sc = std::ldexp(1.0, h->escale);  // the scale taken off A and B at create time
     if (lambdas) {
       size_t off = 0;
       for (int l = 1; l < L; ++l) {
         const std::vector<double>& v = h->lam[l];
-        for (int j = 0; j < D.c[l]; ++j) lambdas[off + j] = (j < (int)v.size()) ? v[j] : 0.0;
+        for (int j = 0; j < D.c[l]; ++j) lambdas[off + j] = (j < (int)v.size()) ? sc * v[j] : 0.0;
         off += D.c[l];
       }
     }
@@ -2048,13 +2074,18 @@ tt_status tt_fit_result(const tt_fit* hc, tt_mpo_desc* C, double* lambdas) {
       const int rows = D.c[l] * D.ds[l] * D.dt[l], cols = D.c[l + 1];
       // C_l = Psi_l Y_l for l < L (inverse gauge); Y = 1 in the site gauge
       const bool scale = (h->gauge == TT_GAUGE_INVERSE_CANONICAL) && (l < L - 1);
-      if (C->dtype == TT_DTYPE_F64) {
+      const double f = l == 0 ? sc : 1.0;  // the input scale goes back into the first core
+      if (C->dtype == TT_DTYPE_F64 && f == 1.0) {
         CK(scale_cols(rows, cols, h->C64[l], scale ? h->Y[l + 1] : nullptr, (double*)C->cores[l], W(h).st));
       } else {
         double* tmp = h->pool.alloc<double>((size_t)rows * cols);
         CK(scale_cols(rows, cols, h->C64[l], scale ? h->Y[l + 1] : nullptr, tmp, W(h).st));
-        CK(copy_map<double, float>(1, rows * cols, tmp, IdxMap::lin(0), IdxMap::lin(1), (float*)C->cores[l],
-                                   IdxMap::lin(0), IdxMap::lin(1), 1.0, W(h).st));
+        if (C->dtype == TT_DTYPE_F64)
+          CK(copy_map<double, double>(1, rows * cols, tmp, IdxMap::lin(0), IdxMap::lin(1), (double*)C->cores[l],
+                                      IdxMap::lin(0), IdxMap::lin(1), f, W(h).st));
+        else
+          CK(copy_map<double, float>(1, rows * cols, tmp, IdxMap::lin(0), IdxMap::lin(1), (float*)C->cores[l],
+                                     IdxMap::lin(0), IdxMap::lin(1), f, W(h).st));
         CK(cudaStreamSynchronize(W(h).st));
         h->pool.release(tmp);
       }

@@ -106,6 +106,11 @@ WORKLOADS = {
     "kron_L10_chi16": dict(kind="kron", L=10, K=16, chi_C=16),
     "kron_L12_chi32": dict(kind="kron", L=12, K=32, chi_C=32),
     "uniform_L12_chi12": dict(kind="uniform", L=12, chi=12, alpha=-0.5, chi_C=12),
+    # the paper's random tensor trains (Sec. 5.1): entries uniform in [alpha, 1], cores normalised;
+    # ||A B|| falls like ~0.2^L, far below the FP32 range at these lengths
+    "uniform_L102_chi30": dict(kind="uniform", L=102, chi=30, alpha=-0.33, chi_C=30),
+    "uniform_L102_chi100": dict(kind="uniform", L=102, chi=100, alpha=-0.5, chi_C=100),
+    "uniform_L50_chi128": dict(kind="uniform", L=50, chi=128, alpha=-0.5, chi_C=128),
     # the timed workload's window shapes (chi = 128 at the middle sites) on a short chain, for profiling
     "kron_L10_chi128": dict(kind="kron", L=10, K=128, chi_C=128),
 }
