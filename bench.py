@@ -53,6 +53,8 @@ def parse():
                    help="synthetic workload (default: the timed one); smaller ones serve profiling captures")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-accuracy", action="store_true", help="skip the (untimed) FP64 reference fit")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the measurements of the other configurations (segments, configs 2, 4, 5)")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
 
@@ -385,12 +387,154 @@ def native(args):
         "jacobi_max_sweeps": rep.get("jacobi_max_sweeps"),
         "accuracy": accuracy,
     }
+    if rank == 0 and not args.no_extras and args.workload == WORKLOAD:
+        out["extras"] = extras(ttfit, dev, stream, out["norm2_C"])
     if rank == 0 and not args.no_cpu_baseline and args.workload == WORKLOAD:
         out["cpu_baseline"] = cpu_baseline(sweeps)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# --------------------------------------------------------------------------- other configurations
+def _timed(stream, fn):
+    """fn() bracketed by CUDA events on `stream` (seconds), and its result."""
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    r = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / 1e3, r
+
+
+def _segment_fit(ttfit, A, B, dev, stream, n_seg, edge_extra=0):
+    """The timed workload in the inverse gauge, serial (n_seg = 1) or segment-parallel
+    (Alg. 6): one cheap 3xTF32 pass (a full set of local sweeps when segmented), then
+    DF32 with the FP32 factorisation until delta <= TOL."""
+    def run():
+        f = ttfit.tt_fit_create(A, B, CHI, TOL, "inverse", update="rsvd", oversample=OVERSAMPLE, seed=0,
+                                precision="tf32x3", device=dev, stream=stream, n_segments=n_seg,
+                                edge_extra=edge_extra)
+        per_set = 2 if n_seg > 1 else 1
+        f.sweep(per_set)
+        f.set_precision("df32", fast_factor=1)
+        n, rep = per_set, None
+        while n < MAX_SWEEPS * per_set:
+            rep = f.sweep(1)
+            n += 1
+            if rep["converged"]:
+                break
+        f.destroy()
+        return rep, n
+    run()  # warm-up
+    t, (rep, n) = _timed(stream, run)
+    return t, rep, n
+
+
+def extras(ttfit, dev, stream, norm2_site):
+    """One measured run each (after a warm-up) of: the segment-parallel fit of the timed
+    workload (Sec. 4, Alg. 6); plain FP32 vs mixed precision at equal accuracy (config 2:
+    L=20, chi=64); 32 uneven independent pairs plus an L=64, chi=128 chain in 8 segments
+    (config 4); the adjoint at L=32, chi=96 (config 5)."""
+    import numpy as np
+    import torch
+    from paper_2606_23274_gb300.synth import gaussian_mpo, kron_sum_mpo, mpo_pair
+    out = {}
+    # segment-parallel fit of the timed workload
+    A, B = mpo_pair(WORKLOAD, seed=0)
+    A = [torch.from_numpy(a).to(dev) for a in A]
+    B = [torch.from_numpy(b).to(dev) for b in B]
+    seg = {}
+    for n_seg, ee in ((1, 0), (2, 0), (4, 2), (8, 2)):
+        t, rep, n = _segment_fit(ttfit, A, B, dev, stream, n_seg, ee)
+        seg[str(n_seg)] = {"time_to_tol_s": round(t, 4), "sweeps_or_phases": n, "converged": bool(rep["converged"]),
+                           "delta": rep["delta"], "norm2_rel_to_site_fit": rep["norm2_C"] / norm2_site - 1.0,
+                           "edge_extra": ee}
+    out["segments_inverse_gauge_L30_chi128"] = seg
+
+    # config 2: plain FP32 (FP32 CUDA-core contractions, FP32 SVD) vs mixed (3xTF32, then DF32 with the
+    # FP64 SVD), both the exact two-site update; error = relative Frobenius distance to the converged FP64 fit
+    A2, B2 = mpo_pair("kron_L20_chi64", seed=0)
+    A2 = [torch.from_numpy(a).to(dev) for a in A2]
+    B2 = [torch.from_numpy(b).to(dev) for b in B2]
+    g = ttfit.tt_fit_create(A2, B2, 64, 1e-8, "site", precision="fp64", device=dev, stream=stream, conv_tol=1e-13)
+    g.sweep(14)
+    C_ref = g.result()
+    g.destroy()
+
+    def trace(schedule):
+        lo, hi = (schedule.split(">") + [None])[:2]
+        f = ttfit.tt_fit_create(A2, B2, 64, 1e-8, "site", precision=lo, device=dev, stream=stream, conv_tol=0.0)
+        t_cum, pts = 0.0, []
+        for s in range(12):
+            if hi is not None and s == 1:
+                dt, _ = _timed(stream, lambda: f.set_precision(hi, fast_factor=0))
+                t_cum += dt
+            dt, _ = _timed(stream, lambda: f.sweep(1))
+            t_cum += dt
+            pts.append((t_cum, rel_frobenius(f.result(), C_ref)))
+        f.destroy()
+        return pts
+    trace("fp32")  # warm-up
+    plain = trace("fp32")
+    mixed = trace("tf32x3>df32")
+    best = min(e for _, e in plain)
+    t_plain = next(t for t, e in plain if e <= 1.05 * best)
+    t_mixed = next((t for t, e in mixed if e <= best), None)
+    out["config2_plain_fp32_vs_mixed_L20_chi64"] = {
+        "accuracy_target": float(f"{best:.3e}"), "note": "the plain FP32 fit's best relative Frobenius error "
+        "(to the converged FP64 fit) over 12 sweeps; each fit timed until it first reaches it",
+        "plain_fp32_s": round(t_plain, 4), "mixed_s": round(t_mixed, 4) if t_mixed else None,
+        "speedup": round(t_plain / t_mixed, 2) if t_mixed else None,
+        "mixed_final_error": float(f"{mixed[-1][1]:.3e}"),
+        "plain_errors": [float(f"{e:.2e}") for _, e in plain], "mixed_errors": [float(f"{e:.2e}") for _, e in mixed]}
+
+    # config 4: 32 pairs with uneven L and chi, and one L = 64, chi = 128 chain in 8 segments
+    rng = np.random.default_rng(4)
+    Ls = rng.integers(16, 65, size=32)
+    chis = rng.choice([16, 32, 64, 96, 128], size=32)
+    pairs = [([torch.from_numpy(a).to(dev) for a in kron_sum_mpo(int(L), int(c), 100 + i, 0)],
+              [torch.from_numpy(b).to(dev) for b in kron_sum_mpo(int(L), int(c), 100 + i, 1)])
+             for i, (L, c) in enumerate(zip(Ls, chis))]
+    Ac = [torch.from_numpy(a).to(dev) for a in kron_sum_mpo(64, 128, 99, 0)]
+    Bc = [torch.from_numpy(b).to(dev) for b in kron_sum_mpo(64, 128, 99, 1)]
+    kw = dict(update="rsvd", oversample=OVERSAMPLE, seed=0, precision="tf32x3", device=dev, stream=stream)
+
+    def batch():
+        fits = ttfit.tt_fit_create_batched(pairs, [int(c) for c in chis], 0.0, "inverse", conv_tol=0.0, **kw)
+        fits += ttfit.tt_fit_create_batched([(Ac, Bc)], [128], 0.0, "inverse", n_segments=8, edge_extra=3,
+                                            conv_tol=0.0, **kw)
+        t_s, reps = _timed(stream, lambda: ttfit.tt_fit_sweep_batched(fits, 4))
+        flops = sum(f.stage_times()["contraction_flops"] for f in fits)
+        for f in fits:
+            f.destroy()
+        return t_s, reps, flops
+    batch()  # warm-up (fills the block cache)
+    t_all, (t_s, reps, flops) = _timed(stream, batch)
+    windows = int(sum(int(L) - 1 for L in Ls) * 4 + 63 * 2)
+    out["config4_batched_32_pairs_plus_L64_chi128_8_segments"] = {
+        "pairs": 32, "L": [int(x) for x in Ls], "chi": [int(x) for x in chis], "precision": "tf32x3 (FP32-class)",
+        "gauge": "inverse", "sweeps": "4 per pair; 4 phases (2 full sets) for the segmented chain",
+        "sweep_wall_s": round(t_s, 4), "create_sweep_destroy_s": round(t_all, 4),
+        "windows_per_s": round(windows / t_s, 1),
+        "contraction_tflops_last_call": round(flops / t_s / 1e12, 3),
+        "concurrency": "one host thread and CUDA stream per handle (and per segment); no single persistent launch"}
+
+    # config 5: the adjoint at L = 32, chi_A = chi_B = chi_C = 96, W of chi = 32, FP32
+    A5 = [torch.from_numpy(a).to(dev) for a in kron_sum_mpo(32, 96, 5, 0)]
+    B5 = [torch.from_numpy(b).to(dev) for b in kron_sum_mpo(32, 96, 5, 1)]
+    C5 = [torch.from_numpy(c).to(dev) for c in gaussian_mpo(32, 2, 96, 5, 2)]
+    W5 = [torch.from_numpy(w).to(dev) for w in gaussian_mpo(32, 2, 32, 5, 3)]
+    res5 = {}
+    for target, X in (("residual", C5), ("inner", W5)):
+        ttfit.tt_mpo_grad(A5, B5, X, target, "fp32", 0, stream=stream)  # warm-up
+        t, _ = _timed(stream, lambda: ttfit.tt_mpo_grad(A5, B5, X, target, "fp32", 0, stream=stream))
+        res5[target] = round(t, 4)
+    out["config5_adjoint_L32_chi96_fp32_s"] = res5
+    return out
 
 
 # --------------------------------------------------------------------------- oracle timing

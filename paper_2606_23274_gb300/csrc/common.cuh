@@ -3,8 +3,30 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstddef>
+#include <map>
+#include <mutex>
+#include <utility>
 
 namespace ttfit {
+
+// Raise (never lower) a kernel's dynamic shared-memory limit on the current
+// device. The limit is process-wide per function, and host threads of
+// concurrent handles launch the same kernels with different sizes: setting it
+// to each launch's own size would let one thread lower it between another
+// thread's set and launch (the launch then fails with an invalid argument).
+inline cudaError_t ensure_smem(const void* kern, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> cur;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> g(mu);
+  size_t& have = cur[{dev, kern}];
+  if (have >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) have = bytes;
+  return e;
+}
 
 // Kernel launches issued by the calling host thread; every launch site
 // increments it, and the API entry points attribute the difference to their

@@ -2074,7 +2074,10 @@ tt_status tt_fit_result(const tt_fit* hc, tt_mpo_desc* C, double* lambdas) {
       const int rows = D.c[l] * D.ds[l] * D.dt[l], cols = D.c[l + 1];
       // C_l = Psi_l Y_l for l < L (inverse gauge); Y = 1 in the site gauge
       const bool scale = (h->gauge == TT_GAUGE_INVERSE_CANONICAL) && (l < L - 1);
-      const double f = l == 0 ? sc : 1.0;  // the input scale goes back into the first core
+      // the input scale goes back into the orthogonality centre, so that the other cores keep
+      // their canonical form: in the site gauge the last core after a forward sweep, else the first
+      const int oc = (h->gauge != TT_GAUGE_INVERSE_CANONICAL && !h->forward) ? L - 1 : 0;
+      const double f = l == oc ? sc : 1.0;
       if (C->dtype == TT_DTYPE_F64 && f == 1.0) {
         CK(scale_cols(rows, cols, h->C64[l], scale ? h->Y[l + 1] : nullptr, (double*)C->cores[l], W(h).st));
       } else {

@@ -571,10 +571,8 @@ cudaError_t gemm_tf32(const GemmArgs<float>& g, float* ws, size_t ws_elems, int 
   } else {
     if (!make_map(&tb, g.B, (uint64_t)g.N, (uint64_t)g.K, (uint64_t)ldb, 32, BK)) return cudaErrorNotSupported;
   }
-  cudaError_t ea = split ? cudaFuncSetAttribute(gemm_tf32_kernel<false, true>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<true>::SMEM_BYTES)
-                         : cudaFuncSetAttribute(gemm_tf32_kernel<false, false>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<false>::SMEM_BYTES);
+  cudaError_t ea = split ? ensure_smem((const void*)gemm_tf32_kernel<false, true>, Cfg<true>::SMEM_BYTES)
+                         : ensure_smem((const void*)gemm_tf32_kernel<false, false>, Cfg<false>::SMEM_BYTES);
   if (ea != cudaSuccess) return ea;
   const int gm = (g.M + BM - 1) / BM, gn = (g.N + BN - 1) / BN;
   int splits = 1;
@@ -629,7 +627,7 @@ cudaError_t gemm_oz(const GemmArgs<df32>& g, float* sA, float* sB, size_t slice_
   CUtensorMap ta, tb;
   if (!make_map(&ta, sA, (uint64_t)Kp, (uint64_t)OZ_S * g.M, (uint64_t)Kp, BK, BM)) return cudaErrorNotSupported;
   if (!make_map(&tb, sB, (uint64_t)Kp, (uint64_t)OZ_S * g.N, (uint64_t)Kp, BK, BN)) return cudaErrorNotSupported;
-  if ((e = cudaFuncSetAttribute(gemm_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM)) != cudaSuccess)
+  if ((e = ensure_smem((const void*)gemm_oz_kernel, OZ_SMEM)) != cudaSuccess)
     return e;
   dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, nch);
   ++tl_launches;

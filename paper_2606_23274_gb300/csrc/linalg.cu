@@ -727,7 +727,7 @@ cudaError_t qr_householder(int q, int p, S* X, S* Q, S* R, cudaStream_t st) {
     if (Q == nullptr && !(q >= 128 && p >= 16 && bsm <= 220 * 1024)) return cudaErrorInvalidValue;
     if (q >= 128 && p >= 16 && bsm <= 220 * 1024) {
       auto launch = [&](auto kern) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
+        cudaError_t e = ensure_smem((const void*)kern, bsm);
         if (e != cudaSuccess) return e;
         ++tl_launches;
         kern<<<JQ, 256, bsm, st>>>(q, p, X, Q, R);
@@ -741,7 +741,7 @@ cudaError_t qr_householder(int q, int p, S* X, S* Q, S* R, cudaStream_t st) {
     if (q >= 128 && p >= 16 && csm <= 200 * 1024) {
       if (csm > 48 * 1024) {
         cudaError_t e =
-            cudaFuncSetAttribute(qr_cluster_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
+            ensure_smem((const void*)qr_cluster_kernel<C>, csm);
         if (e != cudaSuccess) return e;
       }
       ++tl_launches;
@@ -765,7 +765,7 @@ cudaError_t qr_householder_df32(int q, int p, double* X, double* Q, double* R, c
   const size_t bsm = qr_cluster_blocked_smem<df32>(q, p);
   if (q < 128 || p < 16 || q > 1024 || bsm > 220 * 1024) return qr_householder<double, double>(q, p, X, Q, R, st);
   auto launch = [&](auto kern) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
+    cudaError_t e = ensure_smem((const void*)kern, bsm);
     if (e != cudaSuccess) return e;
     ++tl_launches;
     kern<<<JQ, 256, bsm, st>>>(q, p, X, Q, R);
@@ -977,7 +977,7 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(int q, int p, S* __restric
 // jacobi_kernel. All CTAs run the same number of barriers (the stop decision is
 // a cluster-wide OR read by all), so no barrier waits on a CTA that has left.
 // ---------------------------------------------------------------------------
-constexpr int JC = 8;  // CTAs per cluster (portable size)
+constexpr int JC = 8;  // CTAs per cluster (portable size); 16 (opt-in) when 8 CTAs' shared memory is too small
 
 template <typename C>
 __device__ __forceinline__ bool jacobi_pair(C* __restrict__ xi, C* __restrict__ xj, int q, int rows, C tol2) {
@@ -1068,13 +1068,13 @@ __device__ __forceinline__ bool jacobi_pair_any(C* __restrict__ xi, C* __restric
   else return jacobi_pair<C>(xi, xj, q, rows, tol2);
 }
 
-template <typename C, int RPL>
-__global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(RPL > 0 ? 640 : 1024)
+template <typename C, int RPL, int NC>
+__global__ void __launch_bounds__(RPL > 0 ? 640 : 1024)
     jacobi_cluster_kernel(int q, int p, int b, const C* __restrict__ Win, int max_sweeps, double tol, uint32_t* errw,
                           C* __restrict__ Uo, C* __restrict__ So, C* __restrict__ Vo) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
-  const int P = 2 * JC;
+  const int P = 2 * NC;
   const bool want_v = Vo != nullptr;
   const int rows = q + (want_v ? p : 0);  // a column: its w part, then its v part
   constexpr int V16 = 16 / (int)sizeof(C);
@@ -1147,7 +1147,7 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(RPL > 0 ? 640 : 102
         for (int sl = 0; sl < 2; ++sl) {
           const int x = sl == 0 ? rank : P - 1 - rank;
           const int src = x == 0 ? 0 : (x == 1 ? P - 1 : x - 1);
-          const int scta = src < JC ? src : P - 1 - src, ssl = src < JC ? 0 : 1;
+          const int scta = src < NC ? src : P - 1 - src, ssl = src < NC ? 0 : 1;
           rsrc[sl] = reinterpret_cast<const uint4*>(cl.map_shared_rank(col(cur, ssl, 0), scta));
           rid[sl] = cl.map_shared_rank(&cid(cur, ssl, 0), scta);
         }
@@ -1205,7 +1205,7 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(RPL > 0 ? 640 : 102
     if (me < 0) continue;
     const C v = nrm[w];
     int rk = 0;
-    for (int c = 0; c < JC; ++c) {
+    for (int c = 0; c < NC; ++c) {
       const C* rn = cl.map_shared_rank(nrm, c);
       const int* ri = cl.map_shared_rank(&cid(cur, 0, 0), c);
       for (int t = lane; t < 2 * b; t += 32) {
@@ -1226,8 +1226,8 @@ __global__ void __cluster_dims__(JC, 1, 1) __launch_bounds__(RPL > 0 ? 640 : 102
 }
 
 template <typename C>
-size_t jacobi_cluster_smem(int q, int p, bool want_v) {
-  const int b = (p + 2 * JC - 1) / (2 * JC);
+size_t jacobi_cluster_smem(int q, int p, bool want_v, int nc) {
+  const int b = (p + 2 * nc - 1) / (2 * nc);
   const size_t V16 = 16 / sizeof(C);
   const size_t rows = (size_t)q + (want_v ? p : 0), ld = (rows + V16 - 1) / V16 * V16;
   return 4 * (size_t)b * ld * sizeof(C) + (4 * (size_t)b + 4) * sizeof(int) + 2 * (size_t)b * sizeof(C) + 16;
@@ -1243,24 +1243,52 @@ cudaError_t jacobi_svd(int q, int p, S* W, S* U, S* Sv, S* V, S* Vwork, int max_
   // would keep rotating on noise
   const double eps = (sizeof(C) == 8) ? DBL_EPSILON : (double)FLT_EPSILON;
   const double tol = 4.0 * eps * sqrt((double)q);
-  // the cluster kernel spreads the columns over JC SMs when there are enough of them
+  // the cluster kernel spreads the columns over JC SMs when there are enough of them (16, an
+  // opt-in cluster size, when a block of columns of 8 CTAs does not fit in shared memory)
   if constexpr (std::is_same<C, S>::value) {
-    const size_t csm = jacobi_cluster_smem<C>(q, p, V != nullptr);
-    const int bc = (p + 2 * JC - 1) / (2 * JC), B = bc + (bc & 1);
-    if (p >= 32 && csm <= 200 * 1024 && 32 * B <= 1024) {
-      auto launch = [&](auto kern) {
-        if (csm > 48 * 1024) {
-          cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm);
-          if (e != cudaSuccess) return e;
+    for (const int nc : {JC, 2 * JC}) {
+      const size_t csm = jacobi_cluster_smem<C>(q, p, V != nullptr, nc);
+      const int bc = (p + 2 * nc - 1) / (2 * nc), B = bc + (bc & 1);
+      if (!(p >= 32 && csm <= 200 * 1024 && 32 * B <= 1024)) continue;
+      auto launch = [&](auto kern) -> cudaError_t {
+        cudaError_t e = ensure_smem((const void*)kern, csm);
+        if (e != cudaSuccess) return e;
+        if (nc > 8 && (e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) !=
+                          cudaSuccess)
+          return e;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(nc);
+        cfg.blockDim = dim3(32 * B);
+        cfg.dynamicSmemBytes = csm;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = nc;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        if (nc > 8) {  // a 16-CTA cluster must fit in one GPC next to nothing else: check it can be placed
+          int nclu = 0;
+          if (cudaOccupancyMaxActiveClusters(&nclu, kern, &cfg) != cudaSuccess || nclu < 1) {
+            cudaGetLastError();
+            return cudaErrorNotSupported;
+          }
         }
         ++tl_launches;
-        kern<<<JC, 32 * B, csm, st>>>(q, p, bc, W, max_sweeps, tol, errw, U, Sv, V);
-        return cudaGetLastError();
+        e = cudaLaunchKernelEx(&cfg, kern, q, p, bc, (const C*)W, max_sweeps, tol, errw, (C*)U, (C*)Sv, (C*)V);
+        return e != cudaSuccess ? e : cudaGetLastError();
       };
       const int rows = q + (V != nullptr ? p : 0);
-      if (rows <= 160 && 32 * B <= 640) return launch(jacobi_cluster_kernel<C, 5>);
-      if (rows <= 288 && 32 * B <= 640) return launch(jacobi_cluster_kernel<C, 9>);
-      return launch(jacobi_cluster_kernel<C, 0>);
+      cudaError_t e;
+      if (nc == JC) {
+        if (rows <= 160 && 32 * B <= 640) e = launch(jacobi_cluster_kernel<C, 5, JC>);
+        else if (rows <= 288 && 32 * B <= 640) e = launch(jacobi_cluster_kernel<C, 9, JC>);
+        else e = launch(jacobi_cluster_kernel<C, 0, JC>);
+      } else {
+        e = launch(jacobi_cluster_kernel<C, 0, 2 * JC>);
+      }
+      if (e != cudaErrorNotSupported) return e;  // otherwise the one-CTA kernel below
     }
   }
   const size_t need = ((size_t)q * p + (V ? (size_t)p * p : 0)) * sizeof(S);
@@ -1269,7 +1297,7 @@ cudaError_t jacobi_svd(int q, int p, S* W, S* U, S* Sv, S* V, S* Vwork, int max_
   const int pairs = (p + (p & 1)) / 2;
   auto launch = [&](auto kern) -> cudaError_t {
     if (in_smem) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap);
+      cudaError_t e = ensure_smem((const void*)kern, cap);
       if (e != cudaSuccess) return e;
     }
     ++tl_launches;
@@ -1851,7 +1879,7 @@ cudaError_t tri_inv(int p, const float* R, int ldr, const int* eexp, df32* out, 
   if (p <= 0) return cudaSuccess;
   const size_t smem = 2 * (size_t)p * p * sizeof(float);
   if (p > TRI_INV_MAX || smem > 220 * 1024) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(tri_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_smem((const void*)tri_inv_kernel, smem);
   if (e != cudaSuccess) return e;
   ++tl_launches;
   tri_inv_kernel<<<1, 1024, smem, st>>>(p, R, ldr, eexp, out, errw);

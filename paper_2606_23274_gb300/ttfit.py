@@ -216,6 +216,11 @@ def tt_fit_sweep_batched(fits: Sequence["Fit"], n_sweeps: int) -> list[dict]:
     reps = (tt_sweep_report * n)()
     hs = (ct.c_void_p * n)(*[f.h.value for f in fits])
     code = load().tt_fit_sweep_batched(n, hs, int(n_sweeps), reps)
+    if code != TT_OK:  # name the first failing handle and its own message
+        for i, f in enumerate(fits):
+            msg = load().tt_fit_last_error(f.h).decode()
+            if msg:
+                raise TTError(code, f"tt_fit_sweep_batched: handle {i}: {msg}")
     _check(code, None, "tt_fit_sweep_batched")
     return [{k: getattr(r, k) for k, _ in tt_sweep_report._fields_} for r in reps]
 

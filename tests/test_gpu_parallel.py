@@ -178,3 +178,33 @@ def test_parallel_df32_matches_oracle():
     assert abs(reps[3]["norm2_C"] - par[1][0]) <= 1e-10 * par[1][0]
     assert _rel(_cpu(f.result()), p.result()) <= 1e-9
     f.destroy()
+
+
+def test_batched_uneven_shapes_match_serial_fits():
+    """Sixteen handles whose windows differ in shape (hence in the shared memory
+    their factorisation kernels request) sweep concurrently, one host thread
+    each, and give the same fits as one at a time. The kernels' shared-memory
+    limits are process-wide, so a launch must never see a limit lowered by
+    another thread (it then fails with an invalid argument)."""
+    rng = np.random.default_rng(7)
+    Ls = rng.integers(8, 15, size=16)
+    chis = rng.choice([6, 8, 12, 16, 24], size=16)
+    pairs = [(kron_sum_mpo(int(L), int(c), 300 + i, 0), kron_sum_mpo(int(L), int(c), 300 + i, 1))
+             for i, (L, c) in enumerate(zip(Ls, chis))]
+    kw = dict(update="rsvd", oversample=6, seed=2, precision="tf32x3", conv_tol=0.0)
+    fits = ttfit.tt_fit_create_batched(pairs, [int(c) for c in chis], 0.0, "inverse", **kw)
+    try:
+        reps = ttfit.tt_fit_sweep_batched(fits, 3)
+        got = [[c.cpu().numpy() for c in f.result()] for f in fits]
+    finally:
+        for f in fits:
+            f.destroy()
+    for (A, B), c, r, C in zip(pairs, chis, reps, got):
+        f = ttfit.tt_fit_create(A, B, int(c), 0.0, "inverse", **kw)
+        try:
+            r1 = f.sweep(3)
+            C1 = [x.cpu().numpy() for x in f.result()]
+        finally:
+            f.destroy()
+        assert abs(r["norm2_C"] - r1["norm2_C"]) <= 1e-6 * r1["norm2_C"]
+        assert mpo_diff_norm(C, C1) <= 1e-5 * mpo_norm(C1)
