@@ -216,12 +216,14 @@ tt_status tt_fit_stage_times(const tt_fit* h, double out[7]);
  * timed ran in this library's kernels. */
 tt_status tt_fit_launch_count(const tt_fit* h, long long* n);
 
-/* Device memory of the handles comes from a process-wide cache of blocks
- * binned by size: tt_fit_destroy (and the release of buffers that a handle no
- * longer needs) returns blocks to it instead of freeing them, and the next
- * handle of the same shapes reuses them without allocating. At most 64 GiB
- * stay cached; when an allocation fails the cache of that device is emptied
- * and the allocation retried. This call frees every cached block of `device`
+/* Device memory of the handles comes from a process-wide cache of blocks:
+ * tt_fit_destroy (and the release of buffers that a handle no longer needs)
+ * returns blocks to it instead of freeing them, and later handles reuse them
+ * without allocating (best fit: the smallest cached block of at least the size
+ * asked for and at most twice it). At most a quarter of a device's memory (and
+ * at most 64 GiB) stays cached; when an allocation fails the cache of that
+ * device is emptied and the allocation retried. Cached memory stays with the
+ * process until this call returns it. This call frees every cached block of `device`
  * (all devices if device < 0) and returns the number of bytes it held. Safe to
  * call at any time: cached blocks are not in use. Host-only otherwise (no
  * stream work). */
@@ -315,8 +317,12 @@ tt_status tt_svd_truncated(const double* M, int m, int n, int chi_max, double ta
  * An m x n input needs 2 q r + 2 r^2 + r + 6 doubles of it (r = min(m, n),
  * q = max(m, n); e.g. up to 512 x 256); larger inputs return
  * TT_ERR_INVALID_ARGUMENT. The first call on a device looks up the array's
- * address on that device (cudaGetSymbolAddress), so make that first call
- * before any stream capture. All calls on a device share the one array and
+ * address on that device (cudaGetSymbolAddress); with lazy module loading (the
+ * CUDA default) that is also when the array is committed. So make that first
+ * call before any stream capture, and before a caching allocator claims the
+ * device's memory (else it can fail with TT_ERR_CUDA). The address is cached per
+ * device: after cudaDeviceReset on a device it is stale, and this entry point
+ * must not be called on that device again in the same process. All calls on a device share the one array and
  * it keeps the last call's contents: calls that overlap on the GPU (other
  * streams, other host threads) race and must be serialised by the caller.
  * Synchronises `stream` before returning. */

@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include <exception>
+#include <map>
 #include <memory>
 #include <mutex>
 #include <thread>
@@ -45,37 +46,59 @@ struct TTError : std::runtime_error {
                     std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_));                                \
   } while (0)
 
-// Process-wide cache of device blocks, binned by device and size (rounded up
-// to 512 bytes). A handle takes a cached block of the size it asks for, or
-// allocates a new one; on allocation failure every cached block of the device
-// is freed and the allocation retried. Released blocks return to the cache
-// (cudaFree would also synchronise the whole device); above a cap on the
-// cached bytes a released block is freed instead. A block is released only
-// after the streams that used it have been synchronised (the preparation
-// streams, the handle's lanes), so a block handed out again is idle.
+// Process-wide cache of device blocks, by device and size (rounded up to 512
+// bytes). A handle takes the smallest cached block of at least the size it asks
+// for and at most twice that (best fit, so that fits of uneven shapes reuse each
+// other's blocks), or allocates a new one; on allocation failure every cached
+// block of the device is freed and the allocation retried. Released blocks return
+// to the cache (cudaFree would also synchronise the whole device) while the cache
+// holds at most a quarter of the device's memory (and at most 64 GiB); beyond
+// that a released block is freed. tt_device_cache_release frees the cache. A
+// block is released only after the streams that used it have been synchronised
+// (the preparation streams, the handle's lanes), so a block handed out again is idle.
 struct BlockCache {
-  static constexpr size_t kCap = size_t(64) << 30;
+  static constexpr size_t kCapMax = size_t(64) << 30;
   std::mutex mu;
   std::vector<std::pair<std::pair<int, size_t>, void*>> free_blocks;
-  size_t cached = 0;
-  void* take(int dev, size_t bytes) {
+  std::map<int, size_t> cached;  // bytes held per device
+  std::map<int, size_t> cap;     // per device: min(kCapMax, total memory / 4)
+  void* take(int dev, size_t bytes, size_t* got) {
     std::lock_guard<std::mutex> g(mu);
-    for (size_t i = 0; i < free_blocks.size(); ++i)
-      if (free_blocks[i].first == std::make_pair(dev, bytes)) {
-        void* p = free_blocks[i].second;
-        free_blocks[i] = free_blocks.back();
-        free_blocks.pop_back();
-        cached -= bytes;
-        return p;
-      }
-    return nullptr;
+    size_t best = 0;
+    for (size_t i = 0; i < free_blocks.size(); ++i) {
+      const auto& fb = free_blocks[i].first;
+      if (fb.first == dev && fb.second >= bytes && fb.second <= 2 * bytes &&
+          (best == 0 || fb.second < free_blocks[best - 1].first.second))
+        best = i + 1;
+    }
+    if (!best) return nullptr;
+    const size_t i = best - 1;
+    void* p = free_blocks[i].second;
+    *got = free_blocks[i].first.second;
+    free_blocks[i] = free_blocks.back();
+    free_blocks.pop_back();
+    cached[dev] -= *got;
+    return p;
   }
   void give(int dev, size_t bytes, void* p) {
     {
       std::lock_guard<std::mutex> g(mu);
-      if (cached + bytes <= kCap) {
+      auto it = cap.find(dev);
+      if (it == cap.end()) {
+        size_t fr = 0, tot = 0;
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(dev);
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+          cudaGetLastError();
+          tot = 0;
+        }
+        cudaSetDevice(cur);
+        it = cap.emplace(dev, std::min(kCapMax, tot / 4)).first;
+      }
+      if (cached[dev] + bytes <= it->second) {
         free_blocks.push_back({{dev, bytes}, p});
-        cached += bytes;
+        cached[dev] += bytes;
         return;
       }
     }
@@ -88,7 +111,7 @@ struct BlockCache {
       for (size_t i = 0; i < free_blocks.size();)
         if (dev < 0 || free_blocks[i].first.first == dev) {
           drop.push_back(free_blocks[i]);
-          cached -= free_blocks[i].first.second;
+          cached[free_blocks[i].first.first] -= free_blocks[i].first.second;
           free_blocks[i] = free_blocks.back();
           free_blocks.pop_back();
         } else {
@@ -130,7 +153,8 @@ struct DevPool {
     const size_t bytes = (n * sizeof(T) + 511) & ~(size_t)511;
     int dev = 0;
     cudaGetDevice(&dev);
-    void* p = block_cache().take(dev, bytes);
+    size_t got = bytes;
+    void* p = block_cache().take(dev, bytes, &got);
     if (!p) {
       cudaError_t e = cudaMalloc(&p, bytes);
       if (e != cudaSuccess) {
@@ -143,7 +167,7 @@ struct DevPool {
         throw TTError(TT_ERR_OUT_OF_MEMORY, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
       }
     }
-    blks.push_back({p, bytes, dev});
+    blks.push_back({p, p ? got : bytes, dev});
     return (T*)p;
   }
   void release(void* p) {

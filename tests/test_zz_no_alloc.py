@@ -48,6 +48,34 @@ def test_noalloc_matches_allocating_entry_point_twice():
         assert np.linalg.norm(U * S[None, :] @ Vt - M) <= 1e-12 * np.linalg.norm(M)
 
 
+def test_noalloc_call_allocates_no_device_memory():
+    """After a first call (which commits the library's fixed scratch on this
+    device), a call leaves the device's free memory unchanged: nothing is
+    allocated for it, by the library or by anything it calls."""
+    lib = ttfit.load()
+    fn = lib.tt_svd_truncated_noalloc
+    fn.argtypes = [ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.c_double, ct.c_void_p, ct.c_void_p, ct.c_void_p,
+                   ct.POINTER(ct.c_int), ct.c_void_p]
+    fn.restype = ct.c_int
+    rng = np.random.default_rng(5)
+    m, n = 128, 64
+    M = torch.as_tensor(rng.standard_normal((m, n)) * (0.8 ** np.arange(n))[None, :], device="cuda")
+    U = torch.empty((m, n), dtype=torch.float64, device="cuda")
+    S = torch.empty((n,), dtype=torch.float64, device="cuda")
+    Vt = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    k = ct.c_int(-1)
+    st = ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+    args = (M.data_ptr(), m, n, 16, 0.0, U.data_ptr(), S.data_ptr(), Vt.data_ptr(), ct.byref(k), st)
+    assert fn(*args) == ttfit.TT_OK                      # warm-up: commits the scratch
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        assert fn(*args) == ttfit.TT_OK
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert k.value == 16
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     M = np.ones((600, 600))
     code, *_ = _noalloc(M, 10)
