@@ -1,0 +1,103 @@
+"""Plain FP64 zip-up contraction of two MPOs (Sec. 2.2, Alg. 2), used as the
+fit's initial guess (Sec. 2.3.5).
+
+ORACLE: test infrastructure only. Imported by tests/ (and through them nothing
+else); never by the product path. It shares no code with the CUDA path; only
+the seeded inputs of paper_2606_23274_gb300.synth are common.
+
+Alg. 2 runs left to right on right-canonical inputs. Its mirror runs right to
+left on left-canonical inputs (the paper notes that it applies to TTs brought
+into left-canonical form) and leaves C right-canonical with the orthogonality
+centre on site 1, which is the form the fit starts from; the GPU builds that
+one. Readings taken here:
+
+* Each step factorises the reshaped remainder with the truncation rule of the
+  fit (Sec. 2.3.4: keep min(chi_max, smallest k with sqrt(sum_{j>k} s_j^2) <=
+  (tau / L) ||M||_F) values, then drop s_j <= sv_cutoff s_1, k >= 1).
+* With update="rsvd" the factorisation is the randomized SVD of Sec. 3.1 (the
+  paper: "can be reduced ... using randomized SVDs"), applied to the side whose
+  singular vectors become the new core, with k_s = chi_max + oversample and the
+  Philox Gaussian of stream zipup_stream(site); when k_s is not narrower than
+  the matrix the exact SVD is used.
+* The sign convention of the fit (largest-magnitude entry of each kept vector
+  positive) is applied to the kept singular vectors.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import philox
+from .fit import fix_signs, keep_rank
+from .mpo import left_orthogonalize, right_orthogonalize
+
+
+def zipup_stream(site: int) -> int:
+    """Philox stream of the zip-up sketch at a site (1-based): distinct from the
+    fit's sweep sketches and initial guess."""
+    return (3 << 40) | int(site)
+
+
+def _factor(M, chi_max, tau, L, sv_cutoff, update, oversample, seed, site):
+    """Truncated factorisation M ~ U S V^T by the fit's rule; returns U (signed), S, Vt."""
+    m, n = M.shape
+    norm_M = float(np.linalg.norm(M))
+    ks = chi_max + oversample
+    if update == "rsvd" and ks < min(m, n):
+        Om = philox.normals(seed, zipup_stream(site), n * ks).reshape(n, ks)
+        Q, _ = np.linalg.qr(M @ Om)
+        Ub, S, Vt = np.linalg.svd(Q.T @ M, full_matrices=False)
+        U = Q @ Ub
+    else:
+        U, S, Vt = np.linalg.svd(M, full_matrices=False)
+    k = keep_rank(S, norm_M, tau, L, chi_max, sv_cutoff)
+    U, Vt = fix_signs(U[:, :k], Vt[:k, :])
+    return U, S[:k], Vt
+
+
+def zipup_left_to_right(A, B, chi_max, tau=0.0, sv_cutoff=1e-13, update="svd", oversample=10, seed=0):
+    """Alg. 2 as printed: inputs right-canonicalised; R_0 = [[[1]]]; at site l,
+    R'' = R_{l-1} A_l B_l reshaped (chi d d') x (chi_A chi_B); C_l = U, R_l = S V^T;
+    the last remainder is absorbed into C_L."""
+    A = right_orthogonalize([np.asarray(x, np.float64) for x in A])
+    B = right_orthogonalize([np.asarray(x, np.float64) for x in B])
+    L = len(A)
+    R = np.ones((1, 1, 1))                                     # [c, a, b]
+    C = []
+    for l in range(L):
+        T = np.einsum("cab,asux->cbsux", R, A[l])
+        T = np.einsum("cbsux,buty->cstxy", T, B[l])            # [c, s, t, a', b']
+        c, s, t, x, y = T.shape
+        if l == L - 1:                                         # x = y = 1: the remainder is the last core
+            C.append(T.reshape(c, s, t, 1))
+            break
+        U, S, Vt = _factor(T.reshape(c * s * t, x * y), chi_max, tau, L, sv_cutoff, update, oversample, seed,
+                           l + 1)
+        k = S.shape[0]
+        C.append(U.reshape(c, s, t, k))
+        R = (S[:, None] * Vt).reshape(k, x, y)
+    return C
+
+
+def zipup_right_to_left(A, B, chi_max, tau=0.0, sv_cutoff=1e-13, update="svd", oversample=10, seed=0):
+    """The mirror of Alg. 2: inputs left-canonicalised; R_{L+1} = [[[1]]]; at site l,
+    M = A_l B_l R_{l+1} reshaped (chi_A chi_B) x (d d' chi); C_l = V^T (right-orthonormal),
+    R_l = U S; the last remainder is C_1."""
+    A = left_orthogonalize([np.asarray(x, np.float64) for x in A])
+    B = left_orthogonalize([np.asarray(x, np.float64) for x in B])
+    L = len(A)
+    R = np.ones((1, 1, 1))                                     # [a, b, c]
+    C = [None] * L
+    for l in range(L - 1, -1, -1):
+        T = np.einsum("asux,xyc->asuyc", A[l], R)
+        T = np.einsum("asuyc,buty->abstc", T, B[l])            # [a0, b0, s, t, c]
+        a, b, s, t, c = T.shape
+        if l == 0:                                             # a = b = 1: the remainder is the first core
+            C[0] = T.reshape(1, s, t, c)
+            break
+        # the new core spans the right singular vectors: factorise M^T = V S U^T
+        V, S, Ut = _factor(T.reshape(a * b, s * t * c).T, chi_max, tau, L, sv_cutoff, update, oversample, seed,
+                           l + 1)
+        k = S.shape[0]
+        C[l] = V.T.reshape(k, s, t, c)
+        R = (Ut.T * S[None, :]).reshape(a, b, k)
+    return C
