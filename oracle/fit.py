@@ -19,6 +19,9 @@ Readings of the paper taken here, where it is silent or ambiguous:
   core l >= 2 the orthonormal-row factor of a Gaussian matrix. A given guess
   (or a copy of B) is trimmed by a QR sweep and then right-orthogonalized by
   an RQ sweep; neither changes the operator.
+  The zip-up guess (Sec. 2.3.5) is the right-to-left zip-up of the prepared
+  A, B (oracle/zipup.py) with the fit's chi_max, tau, cut-off, update and
+  seed: right-canonical with the orthogonality centre at site 1 as it comes.
   In the inverse gauge Psi_l = C0_l and Y_l = 1.
 * Truncation (Sec. 2.3.4): keep k = min(chi_max, min{k : sqrt(sum_{j>k} s_j^2)
   <= (tau/L) ||M||_F}), then drop s_j <= sv_cutoff * s_1 (Sec. 2.3.1 allows
@@ -190,6 +193,10 @@ class FitOracle:
             C0 = random_right_canonical(dout, din, self.chi_max, self.seed)
         elif init == "copy_b":                   # QR sweep (trims bonds), then RQ sweep
             C0 = right_orthogonalize(left_orthogonalize(B))
+        elif init == "zipup":                    # Sec. 2.3.5: the zip-up contraction as the guess
+            from .zipup import zipup_right_to_left   # right to left on the left-canonical A, B
+            C0 = zipup_right_to_left(A, B, self.chi_max, self.tau, self.sv_cutoff, update, self.oversample,
+                                     self.seed)
         elif init == "given":
             C0 = right_orthogonalize(left_orthogonalize([np.asarray(x, np.float64) for x in init_C]))
         else:

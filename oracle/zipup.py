@@ -39,19 +39,8 @@ def zipup_stream(site: int) -> int:
 
 def _factor(M, chi_max, tau, L, sv_cutoff, update, oversample, seed, site):
     """Truncated factorisation M ~ U S V^T by the fit's rule; returns U (signed), S, Vt."""
-    m, n = M.shape
-    norm_M = float(np.linalg.norm(M))
-    ks = chi_max + oversample
-    if update == "rsvd" and ks < min(m, n):
-        Om = philox.normals(seed, zipup_stream(site), n * ks).reshape(n, ks)
-        Q, _ = np.linalg.qr(M @ Om)
-        Ub, S, Vt = np.linalg.svd(Q.T @ M, full_matrices=False)
-        U = Q @ Ub
-    else:
-        U, S, Vt = np.linalg.svd(M, full_matrices=False)
-    k = keep_rank(S, norm_M, tau, L, chi_max, sv_cutoff)
-    U, Vt = fix_signs(U[:, :k], Vt[:k, :])
-    return U, S[:k], Vt
+    U, S, Vt, _ = _factor_full(M, chi_max, tau, L, sv_cutoff, update, oversample, seed, site)
+    return U, S, Vt
 
 
 def zipup_left_to_right(A, B, chi_max, tau=0.0, sv_cutoff=1e-13, update="svd", oversample=10, seed=0):
@@ -101,3 +90,49 @@ def zipup_right_to_left(A, B, chi_max, tau=0.0, sv_cutoff=1e-13, update="svd", o
         C[l] = V.T.reshape(k, s, t, c)
         R = (Ut.T * S[None, :]).reshape(a, b, k)
     return C
+
+
+def compress(X, chi_max, tau=0.0, sv_cutoff=1e-13, update="svd", oversample=10, seed=0, return_discarded=False):
+    """compress() of Alg. 1 (Sec. 2.1): the standard SVD compression, which the
+    paper names without spelling out. Reading: X is left-orthogonalized, then swept
+    right to left; at site l the core absorbs the remainder, M = X_l R_{l+1}
+    reshaped chi_{l-1} x (d d' chi), and the truncated factorisation of M^T (the
+    rule and sketch streams of the zip-up) gives C_l = V^T (right-orthonormal) and
+    R_l = U S. With return_discarded, also the discarded weight
+    sqrt(sum_{j>k} s_j^2) of every factorisation (of the kept spectrum of the
+    sketch under update="rsvd")."""
+    X = left_orthogonalize([np.asarray(x, np.float64) for x in X])
+    L = len(X)
+    R = np.ones((1, 1))                                        # [a, c]
+    C = [None] * L
+    disc = []
+    for l in range(L - 1, -1, -1):
+        T = np.einsum("astx,xc->astc", X[l], R)
+        a, s, t, c = T.shape
+        if l == 0:
+            C[0] = T
+            break
+        M = T.reshape(a, s * t * c)
+        V, S, Ut, full = _factor_full(M.T, chi_max, tau, L, sv_cutoff, update, oversample, seed, l + 1)
+        k = S.shape[0]
+        disc.append(float(np.sqrt(np.sum(full[k:] ** 2))))
+        C[l] = V.T.reshape(k, s, t, c)
+        R = Ut.T * S[None, :]
+    return (C, disc[::-1]) if return_discarded else C
+
+
+def _factor_full(M, chi_max, tau, L, sv_cutoff, update, oversample, seed, site):
+    """_factor, also returning every singular value it computed."""
+    m, n = M.shape
+    norm_M = float(np.linalg.norm(M))
+    ks = chi_max + oversample
+    if update == "rsvd" and ks < min(m, n):
+        Om = philox.normals(seed, zipup_stream(site), n * ks).reshape(n, ks)
+        Q, _ = np.linalg.qr(M @ Om)
+        Ub, S, Vt = np.linalg.svd(Q.T @ M, full_matrices=False)
+        U = Q @ Ub
+    else:
+        U, S, Vt = np.linalg.svd(M, full_matrices=False)
+    k = keep_rank(S, norm_M, tau, L, chi_max, sv_cutoff)
+    Uk, Vtk = fix_signs(U[:, :k], Vt[:k, :])
+    return Uk, S[:k], Vtk, S
