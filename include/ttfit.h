@@ -78,8 +78,12 @@ typedef enum {
  * Gaussian stream (core 1 Gaussian, core l>=2 the orthonormal-row factor of a
  * Gaussian matrix), bonds min(chi_max, prod d d' left, prod d d' right).
  * COPY_B: B itself. GIVEN: options.init_C. The guess is brought to
- * right-canonical form (orthogonality centre at site 1) before the sweeps. */
-typedef enum { TT_INIT_RANDOM = 0, TT_INIT_COPY_B = 1, TT_INIT_GIVEN = 2 } tt_init;
+ * right-canonical form (orthogonality centre at site 1) before the sweeps.
+ * ZIPUP: the zip-up contraction of the prepared A and B (tt_mpo_zipup, with
+ * the fit's chi_max, tol, sv_cutoff, update, oversample and seed), which comes
+ * out right-canonical; FP64 arithmetic for the FP64 and DF32 precisions, FP32
+ * for the others (3xTF32 tensor-core contractions for the TF32 ones). */
+typedef enum { TT_INIT_RANDOM = 0, TT_INIT_COPY_B = 1, TT_INIT_GIVEN = 2, TT_INIT_ZIPUP = 3 } tt_init;
 
 typedef enum { TT_DTYPE_F64 = 0, TT_DTYPE_F32 = 1 } tt_dtype;
 
@@ -328,6 +332,55 @@ tt_status tt_svd_truncated(const double* M, int m, int n, int chi_max, double ta
  * Synchronises `stream` before returning. */
 tt_status tt_svd_truncated_noalloc(const double* M, int m, int n, int chi_max, double tau_rel, double* U, double* S,
                                    double* Vt, int* k_out, void* stream);
+
+/* Exact per-site product of two MPOs, the contraction step of the naive
+ * algorithm (Sec. 2.1, Alg. 1, without its final compression):
+ * C_l[(i_a i_b), s, t, (j_a j_b)] = sum_u A_l[i_a, s, u, j_a] B_l[i_b, u, t, j_b],
+ * the combined bond index i_a * chi_B + i_b, so that C has bonds chi_A chi_B.
+ * A, B: device MPOs of equal L with A.d_in == B.d_out, both FP64 or both FP32.
+ * C: caller descriptor whose cores are device buffers of the same dtype with
+ * bond[l] = A.bond[l] * B.bond[l], d_out = A.d_out, d_in = B.d_in; every
+ * core is overwritten. One kernel launch per site on `stream` (cudaStream_t,
+ * NULL = legacy default stream); returns without synchronising. Errors:
+ * TT_ERR_INVALID_ARGUMENT (missing fields, mixed dtypes), TT_ERR_SHAPE_MISMATCH,
+ * TT_ERR_CUDA. */
+tt_status tt_mpo_naive_product(const tt_mpo_desc* A, const tt_mpo_desc* B, const tt_mpo_desc* C, void* stream);
+
+/* Zip-up contraction C ~ A B (Sec. 2.2, Alg. 2) in one pass, right to left:
+ * A and B are prepared as for the fit (RQ sweep, then the QR sweep: left-
+ * canonical, the mirror of the right-canonical inputs the paper's
+ * left-to-right pass takes); from site L down to 2 the remainder R_{l+1} is
+ * contracted with A_l and B_l into the (chi_A chi_B) x (d d' chi) matrix M_l,
+ * whose truncated factorisation (the fit's rule, Sec. 2.3.4, with tol as tau
+ * and chi_max) keeps the right singular vectors as C_l and R_l = M_l V; site 1
+ * takes the last remainder. The result is right-canonical (orthogonality
+ * centre at site 1). opt (NULL = defaults) supplies update (randomized SVD of
+ * Sec. 3.1 with k_s = chi_max + oversample columns and the Philox stream
+ * (3 << 40) | l of seed, where k_s < min of M's sizes), oversample, seed,
+ * precision (FP64 and DF32: FP64 arithmetic; FP32, TF32, TF32_SPLIT: FP32, with
+ * 3xTF32 tensor-core contractions for the TF32 ones), sv_cutoff, stream and
+ * prepare_inputs; the other fields are ignored. M_l with more than 1024 rows is
+ * factorised through its (sketch's) Gram matrix, which resolves singular
+ * values only down to about sqrt(eps) s_1. Needs d d' chi_max <= 1024 and
+ * input cores with d d' chi <= 1024 (the QR of the preparation).
+ * C: caller descriptor (L, d_out = A.d_out, d_in = B.d_in, dtype FP64 or
+ * FP32) whose cores are device buffers with room for bond[l] * d * d' *
+ * bond[l+1] values; bond[l] >= min(chi_max, A.bond[l] B.bond[l],
+ * prod_{j>=l} d_j d'_j) always suffices. Core l is written packed in the kept
+ * bonds, (bond_out[l], d, d', bond_out[l+1]) row-major, and bond_out (host,
+ * L+1 ints) receives the kept bonds. Synchronises the stream. Errors:
+ * TT_ERR_INVALID_ARGUMENT, TT_ERR_SHAPE_MISMATCH (also when a kept bond
+ * exceeds C.bond), TT_ERR_OUT_OF_MEMORY, TT_ERR_NUMERICAL, TT_ERR_CUDA. */
+tt_status tt_mpo_zipup(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max, double tol,
+                       const tt_fit_options* opt, const tt_mpo_desc* C, int* bond_out);
+
+/* compress(X, tol, chi_max) of Alg. 1 (Sec. 2.1): X is left-orthogonalised and
+ * swept right to left; at each site the core absorbs the remainder and its
+ * truncated factorisation keeps the right singular vectors. This is the
+ * zip-up of X with the identity MPO (d_out = d_in = X.d_in, bond 1), so
+ * options, output and errors are those of tt_mpo_zipup (C.d_in = X.d_in). */
+tt_status tt_mpo_compress(const tt_mpo_desc* X, int chi_max, double tol, const tt_fit_options* opt,
+                          const tt_mpo_desc* C, int* bond_out);
 
 #ifdef __cplusplus
 }

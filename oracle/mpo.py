@@ -76,11 +76,29 @@ def right_orthogonalize(X):
     return X
 
 
+def trim_right(X):
+    """RQ steps from the right end (Sec. 2.3.1), each as right_orthogonalize
+    takes it, only while they trim: the sweep ends at the first site whose
+    left bond is already within its bound d d' chi_right. The operator is
+    unchanged."""
+    X = [x.copy() for x in X]
+    for l in range(len(X) - 1, 0, -1):
+        a0, d, dp, a1 = X[l].shape
+        if a0 <= d * dp * a1:
+            break
+        Q, R = qr_pos(X[l].reshape(a0, d * dp * a1).T)
+        k = Q.shape[1]
+        X[l] = Q.T.reshape(k, d, dp, a1)
+        X[l - 1] = np.einsum("axyb,kb->axyk", X[l - 1], R)
+    return X
+
+
 def canonicalize_input(X):
-    """Input preparation of Alg. 5 (left_orthogonalize): an RQ sweep first (it
-    trims every bond to its exact rank bound from the right), then the QR sweep
-    the algorithm names. The operator is unchanged."""
-    return left_orthogonalize(right_orthogonalize(X))
+    """Input preparation of Alg. 5 (left_orthogonalize): bonds first trimmed to
+    their rank bound from the right (trim_right), then the QR sweep the
+    algorithm names. The operator is unchanged; the left gauge it leaves is the
+    one a Gaussian sketch over the input bonds (the randomized zip-up) sees."""
+    return left_orthogonalize(trim_right(X))
 
 
 def is_left_orthogonal(Xl, tol=1e-12) -> bool:

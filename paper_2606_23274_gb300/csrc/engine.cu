@@ -1663,6 +1663,322 @@ double run_phase(tt_fit* h, int ph, int sweep_index, double& maxd) {
   return n2;
 }
 
+// ---------------------------------------------------------------------------
+// Input preparation (Alg. 5 left_orthogonalize), shared by the fit and the
+// zip-up entry points: an RQ sweep that trims every bond to its rank bound,
+// then the QR sweep, for A and B concurrently. The fit is equivariant in the
+// scale of A and B, so their last cores (which carry the norms) are then
+// scaled by powers of two (exact) to norm ~1 and h->escale records what C
+// gets back on export: long chains of normalised random cores (||A B|| ~
+// 0.2^L) then stay inside the range of the FP32 / double-FP32 chains.
+// mc: largest core of A and B (scratch of the sweeps).
+// ---------------------------------------------------------------------------
+void prepare_ab(tt_fit* h, long long mc) {
+  Dims& D = h->D;
+  const int L = D.L;
+  Prep PA = make_prep(h, mc), PB = make_prep(h, mc);
+  rq_sweep(h, PA, h->A64, D.a, D.ds, D.du, 1, true);
+  rq_sweep(h, PB, h->B64, D.b, D.du, D.dt, 1, true);
+  qr_sweep(h, PA, h->A64, D.a, D.ds, D.du);
+  qr_sweep(h, PB, h->B64, D.b, D.du, D.dt);
+  finish_prep(h, PA);
+  finish_prep(h, PB);
+  auto unit = [&](std::vector<double*>& X, const std::vector<int>& bd, const std::vector<int>& d1,
+                  const std::vector<int>& d2) {
+    const int j = L - 1;
+    const long long n = prodll({bd[j], d1[j], d2[j], bd[j + 1]});
+    CK(frob_norm<double>(X[j], n, W(h).dnorm, nullptr, W(h).st));
+    double nrm = 0;
+    CK(cudaMemcpyAsync(&nrm, W(h).dnorm, sizeof(double), cudaMemcpyDeviceToHost, W(h).st));
+    CK(cudaStreamSynchronize(W(h).st));
+    if (!(nrm > 0.0) || !std::isfinite(nrm)) return 0;
+    const int e = (int)std::lround(std::log2(nrm));
+    if (e == 0) return 0;
+    double* y = h->pool.alloc<double>(n);
+    CK(copy_map<double, double>(1, (int)n, X[j], IdxMap::lin(0), IdxMap::lin(1), y, IdxMap::lin(0), IdxMap::lin(1),
+                                std::ldexp(1.0, -e), W(h).st));
+    CK(cudaStreamSynchronize(W(h).st));
+    h->pool.release(X[j]);
+    X[j] = y;
+    return e;
+  };
+  h->escale = unit(h->A64, D.a, D.ds, D.du) + unit(h->B64, D.b, D.du, D.dt);
+}
+
+// ---------------------------------------------------------------------------
+// Zip-up contraction (Sec. 2.2, Alg. 2), run right to left on the prepared,
+// left-canonical A and B: the mirror of the printed left-to-right pass, which
+// the paper gives for left-canonical inputs. From site L down to 2, A_l, B_l
+// and the remainder R_{l+1} (chi_A x chi x chi_B) contract into M_l, an
+// (chi_A chi_B) x (d d' chi) matrix; its truncated factorisation (the fit's
+// rule, Sec. 2.3.4) keeps the right singular vectors as C_l (orthonormal rows)
+// and R_l = M_l V as the next remainder; site 1 takes the last remainder. C
+// comes out right-canonical with the orthogonality centre at site 1, the form
+// the fit starts from (Sec. 2.3.5).
+// Factorisation of M (m x n):
+// * randomized (Sec. 3.1) when k_s = chi_max + oversample < min(m, n): the
+//   sketch Y = M^T Omega (Omega m x k_s row-major, Philox stream
+//   (3 << 40) | l), its orthonormal basis Q (n x k_s) and Z = M Q (m x k_s);
+//   otherwise exact, with Q = I and Z = M;
+// * Z by one-sided Jacobi when m <= 1024; a taller Z through its Gram matrix
+//   Z^T Z (Jacobi eigenvectors W, s_j = sqrt(eigenvalue)), whose squared
+//   condition resolves s_j only down to ~sqrt(eps) s_1: enough for a guess
+//   that the sweeps refine;
+// * V = Q W, signs fixed as in the fit (largest-magnitude entry positive).
+// T: arithmetic of the contractions and the factorisation (double, or float
+// for the FP32-class precisions, with 3xTF32 tensor-core contractions for the
+// TF32 ones). On return C[l] holds core l (FP64, row-major, bonds cb) and
+// cb[1..L-1] the kept bonds.
+// ---------------------------------------------------------------------------
+inline uint64_t zipup_stream(int site1) { return (3ull << 40) | (uint64_t)site1; }
+
+template <typename T>
+void zgemm(tt_fit* h, const GemmArgs<T>& g, T* ws, size_t wse, bool tc) {
+  if constexpr (sizeof(T) == 4) {
+    if (tc && (long long)g.M * g.N * g.K >= (1ll << 18)) {
+      cudaError_t e = gemm_tf32(g, ws, wse, h->sm_count, W(h).errw, W(h).st, true);
+      if (e == cudaSuccess) {
+        h->tc_launches += 1;
+        return;
+      }
+      if (e != cudaErrorNotSupported) CK(e);
+    }
+  }
+  CK(gemm_simt<T>(g, ws, wse, h->sm_count, W(h).st));
+}
+
+template <typename T>
+void zipup_rl(tt_fit* h, std::vector<double*>& C, std::vector<int>& cb) {
+  const Dims& D = h->D;
+  const int L = D.L;
+  Work& w = W(h);
+  cudaStream_t st = w.st;
+  const bool tc = sizeof(T) == 4 && (h->precision == TT_PREC_TF32 || h->precision == TT_PREC_TF32_SPLIT);
+  const int ks = h->chi_max + h->oversample;
+  const bool rsvd_on = h->update == TT_UPDATE_2SITE_RSVD;
+  C.assign(L, nullptr);
+  cb.assign(L + 1, 1);
+  // scratch for the largest site (chi of the remainder <= min(chi_max, chi_A chi_B of the next site))
+  size_t sz_mn = 1, sz_t2 = 1, sz_om = 1, sz_nk = 1, sz_z = 1, sz_zc = 1, sz_u = 1, sz_pp = 1, sz_p = 1, sz_r = 1,
+         sz_ab = 1;
+  for (int l = 0; l < L; ++l) {
+    const long long c = l == L - 1 ? 1 : std::min<long long>(h->chi_max, (long long)D.a[l + 1] * D.b[l + 1]);
+    const long long m = (long long)D.a[l] * D.b[l], n = (long long)D.ds[l] * D.dt[l] * c;
+    if (n > 1024) throw TTError(TT_ERR_INVALID_ARGUMENT, "zip-up: d d' chi above 1024 at a site");
+    const bool rs = rsvd_on && ks < std::min(m, n);
+    const long long p = rs ? ks : n;
+    sz_mn = std::max<size_t>(sz_mn, m * n);
+    sz_t2 = std::max<size_t>(sz_t2, (size_t)D.b[l] * D.dt[l] * c * D.du[l] * D.a[l + 1]);
+    sz_ab = std::max<size_t>(sz_ab, std::max(prodll({D.a[l], D.ds[l], D.du[l], D.a[l + 1]}),
+                                             prodll({D.b[l], D.du[l], D.dt[l], D.b[l + 1]})));
+    if (rs) {
+      sz_om = std::max<size_t>(sz_om, m * ks);
+      sz_nk = std::max<size_t>(sz_nk, n * ks);
+      sz_z = std::max<size_t>(sz_z, m * ks);
+    }
+    if (!rs && m < n) {
+      sz_zc = std::max<size_t>(sz_zc, m * n);
+      sz_u = std::max<size_t>(sz_u, m * n);
+      sz_pp = std::max<size_t>(sz_pp, m * m);
+    } else if (m <= 1024) {
+      sz_zc = std::max<size_t>(sz_zc, m * p);
+      sz_u = std::max<size_t>(sz_u, m * p);
+    } else {
+      sz_zc = std::max<size_t>(sz_zc, p * p);
+      sz_u = std::max<size_t>(sz_u, p * p);
+    }
+    sz_pp = std::max<size_t>(sz_pp, p * p);
+    sz_p = std::max<size_t>(sz_p, std::max(p, m));
+    sz_r = std::max<size_t>(sz_r, m * std::min<long long>(h->chi_max, std::min(m, n)));
+  }
+  const size_t wse = (size_t)1 << 22;
+  std::vector<void*> bufs;
+  auto take = [&](size_t n) {
+    T* p = h->pool.alloc<T>(n);
+    bufs.push_back(p);
+    return p;
+  };
+  T *Mr = take(sz_mn), *Mt = take(sz_mn), *T2 = take(sz_t2), *Om = take(sz_om), *Omt = take(sz_om);
+  T *Y = take(sz_nk), *Q = take(sz_nk), *Rq = take((size_t)ks * ks), *Z = take(sz_z), *Zc = take(sz_zc);
+  T *Ux = take(sz_u), *Sv = take(sz_p), *Vx = take(sz_pp), *Vw = take(sz_pp), *Vn = take(std::max(sz_nk, sz_mn));
+  T *Rc = take(sz_r), *Rn = take(sz_r), *ws = take(wse);
+  T *Al = nullptr, *Bl = nullptr;
+  if (!std::is_same<T, double>::value) Al = take(sz_ab), Bl = take(sz_ab);
+  {  // R_{L+1} = [[[1]]]
+    const T one = T(1);
+    CK(cudaMemcpyAsync(Rc, &one, sizeof(T), cudaMemcpyHostToDevice, st));
+  }
+  for (int l = L - 1; l >= 0; --l) {
+    const int a0 = D.a[l], a1 = D.a[l + 1], b0 = D.b[l], b1 = D.b[l + 1];
+    const int s = D.ds[l], u = D.du[l], t = D.dt[l], c = cb[l + 1];
+    const long long m = (long long)a0 * b0, n = (long long)s * t * c;
+    const T *Ap, *Bp;
+    if constexpr (std::is_same<T, double>::value) {
+      Ap = h->A64[l];
+      Bp = h->B64[l];
+    } else {
+      const long long na = prodll({a0, s, u, a1}), nb = prodll({b0, u, t, b1});
+      copymap<double, T>(h, 1, (int)na, h->A64[l], IdxMap::lin(0), IdxMap::lin(1), Al, IdxMap::lin(0), IdxMap::lin(1));
+      copymap<double, T>(h, 1, (int)nb, h->B64[l], IdxMap::lin(0), IdxMap::lin(1), Bl, IdxMap::lin(0), IdxMap::lin(1));
+      Ap = Al;
+      Bp = Bl;
+    }
+    {  // T2[(b0 t c), (u a1)] = sum_{b1} B_l[(b0 u t), b1] R[(a1 c), b1]
+      GemmArgs<T> g;
+      g.M = b0 * u * t;
+      g.N = a1 * c;
+      g.K = b1;
+      g.A = Bp;
+      g.am = IdxMap::lin(b1);
+      g.ak = IdxMap::lin(1);
+      g.B = Rc;
+      g.bn = IdxMap::lin(b1);
+      g.bk = IdxMap::lin(1);
+      g.C = T2;
+      g.cm = IdxMap::three(u, t, (long long)t * c * u * a1, a1, (long long)c * u * a1);
+      g.cn = IdxMap::two(c, 1, (long long)u * a1);
+      zgemm<T>(h, g, ws, wse, tc);
+    }
+    {  // M[(a0 b0), (s t c)] = sum_{(u a1)} A_l[(a0 s), (u a1)] T2[(b0 t c), (u a1)], also as M^T
+      GemmArgs<T> g;
+      g.M = a0 * s;
+      g.N = b0 * t * c;
+      g.K = u * a1;
+      g.A = Ap;
+      g.am = IdxMap::lin((long long)u * a1);
+      g.ak = IdxMap::lin(1);
+      g.B = T2;
+      g.bn = IdxMap::lin((long long)u * a1);
+      g.bk = IdxMap::lin(1);
+      g.C = Mr;
+      g.cm = IdxMap::two(s, (long long)b0 * n, (long long)t * c);
+      g.cn = IdxMap::three(t, c, n, c, 1);
+      g.C2 = Mt;
+      g.cm2 = IdxMap::two(s, b0, (long long)t * c * m);
+      g.cn2 = IdxMap::three(t, c, 1, (long long)c * m, m);
+      zgemm<T>(h, g, ws, wse, tc);
+    }
+    if (l == 0) {  // a0 = b0 = 1: the remainder is the first core
+      C[0] = h->pool.alloc<double>(n);
+      copymap<T, double>(h, 1, (int)n, Mr, IdxMap::lin(0), IdxMap::lin(1), C[0], IdxMap::lin(0), IdxMap::lin(1));
+      break;
+    }
+    CK(frob_norm<T>(Mr, m * n, w.dnorm, w.errw, st));
+    const bool rs = rsvd_on && ks < std::min(m, n);
+    int p = (int)n;
+    const T* Zp = Mt;  // Z column-major m x p
+    if (rs) {
+      p = ks;
+      CK(philox_fill<T>(Om, m * ks, h->seed, zipup_stream(l + 1), 1.0, st));
+      copymap<T, T>(h, (int)m, ks, Om, IdxMap::lin(ks), IdxMap::lin(1), Omt, IdxMap::lin(1), IdxMap::lin(m));
+      GemmArgs<T> g;  // Y (n x k_s, column-major) = M^T Omega
+      g.M = (int)n;
+      g.N = ks;
+      g.K = (int)m;
+      g.A = Mt;
+      g.am = IdxMap::lin(m);
+      g.ak = IdxMap::lin(1);
+      g.B = Omt;
+      g.bn = IdxMap::lin(m);
+      g.bk = IdxMap::lin(1);
+      g.C = Y;
+      g.cm = IdxMap::lin(1);
+      g.cn = IdxMap::lin(n);
+      zgemm<T>(h, g, ws, wse, tc);
+      CK(qr_householder<T, T>((int)n, ks, Y, Q, Rq, st));
+      GemmArgs<T> z;  // Z (m x k_s, column-major) = M Q
+      z.M = (int)m;
+      z.N = ks;
+      z.K = (int)n;
+      z.A = Mr;
+      z.am = IdxMap::lin(n);
+      z.ak = IdxMap::lin(1);
+      z.B = Q;
+      z.bn = IdxMap::lin(n);
+      z.bk = IdxMap::lin(1);
+      z.C = Z;
+      z.cm = IdxMap::lin(1);
+      z.cn = IdxMap::lin(m);
+      zgemm<T>(h, z, ws, wse, tc);
+      Zp = Z;
+    }
+    int pv = p;        // singular values in Sv, V = Vn (n x pv column-major)
+    T* W_ = nullptr;   // V = Q W when randomized
+    if (!rs && m < n) {  // M^T (n x m, column-major = M row-major) is the tall side: M^T = Ux S Vx^T
+      CK(cudaMemcpyAsync(Zc, Mr, sizeof(T) * m * n, cudaMemcpyDeviceToDevice, st));
+      CK(jacobi_svd<T, T>((int)n, (int)m, Zc, Vn, Sv, Vx, Vw, 60, w.errw, st));
+      pv = (int)m;
+    } else if (m <= 1024) {  // Z = Ux S W^T
+      CK(cudaMemcpyAsync(Zc, Zp, sizeof(T) * m * p, cudaMemcpyDeviceToDevice, st));
+      CK(jacobi_svd<T, T>((int)m, p, Zc, Ux, Sv, rs ? Vx : Vn, Vw, 60, w.errw, st));
+      W_ = rs ? Vx : nullptr;
+    } else {  // Gram matrix Z^T Z = W S^2 W^T
+      GemmArgs<T> g;
+      g.M = p;
+      g.N = p;
+      g.K = (int)m;
+      g.A = Zp;
+      g.am = IdxMap::lin(m);
+      g.ak = IdxMap::lin(1);
+      g.B = Zp;
+      g.bn = IdxMap::lin(m);
+      g.bk = IdxMap::lin(1);
+      g.C = Zc;
+      g.cm = IdxMap::lin(1);
+      g.cn = IdxMap::lin(p);
+      zgemm<T>(h, g, ws, wse, tc);
+      CK(jacobi_svd<T, T>(p, p, Zc, Ux, Sv, rs ? Vx : Vn, Vw, 60, w.errw, st));
+      CK(sqrt_clamp<T>(p, Sv, st));
+      W_ = rs ? Vx : nullptr;
+    }
+    if (W_) {  // V = Q W (n x k_s)
+      GemmArgs<T> g;
+      g.M = (int)n;
+      g.N = p;
+      g.K = p;
+      g.A = Q;
+      g.am = IdxMap::lin(1);
+      g.ak = IdxMap::lin(n);
+      g.a_kfast = false;
+      g.B = W_;
+      g.bn = IdxMap::lin(p);
+      g.bk = IdxMap::lin(1);
+      g.C = Vn;
+      g.cm = IdxMap::lin(1);
+      g.cn = IdxMap::lin(n);
+      zgemm<T>(h, g, ws, wse, false);
+    }
+    CK(fix_signs<T>((int)n, 0, pv, Vn, (int)n, nullptr, 0, st));
+    CK(truncate_rule<T>(Sv, pv, w.dnorm, h->tol / L, h->chi_max, h->cutoff, w.dk, w.ddinfo, st));
+    CK(cudaMemcpyAsync(w.hk, w.dk, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(w.herrw, w.errw, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    check_errw(h, ("zip-up site " + std::to_string(l + 1)).c_str());
+    const int k = *w.hk;
+    if (k < 1 || k > pv) throw TTError(TT_ERR_NUMERICAL, "zip-up: invalid kept rank");
+    cb[l] = k;
+    C[l] = h->pool.alloc<double>((size_t)k * n);  // C_l = V^T (k x (s t c)): V column-major is V^T row-major
+    copymap<T, double>(h, 1, (int)(k * n), Vn, IdxMap::lin(0), IdxMap::lin(1), C[l], IdxMap::lin(0), IdxMap::lin(1));
+    GemmArgs<T> g;  // R_l[a0, k, b0] = (M V)[(a0 b0), k]
+    g.M = (int)m;
+    g.N = k;
+    g.K = (int)n;
+    g.A = Mr;
+    g.am = IdxMap::lin(n);
+    g.ak = IdxMap::lin(1);
+    g.B = Vn;
+    g.bn = IdxMap::lin(n);
+    g.bk = IdxMap::lin(1);
+    g.C = Rn;
+    g.cm = IdxMap::two(b0, (long long)k * b0, 1);
+    g.cn = IdxMap::lin(b0);
+    zgemm<T>(h, g, ws, wse, tc);
+    std::swap(Rc, Rn);
+  }
+  CK(cudaStreamSynchronize(st));
+  for (void* b : bufs) h->pool.release(b);
+}
+
 void setup(tt_fit* h, const std::vector<double*>& C0) {
   Dims& D = h->D;
   const int L = D.L;
@@ -1752,6 +2068,146 @@ struct LaunchTally {
   }
 };
 
+}  // extern "C"
+
+namespace {
+
+// Shared body of tt_mpo_zipup and tt_mpo_compress (B == nullptr: the identity
+// MPO on X's input legs). A handle without a fit holds the prepared inputs,
+// the lane (stream, flags) and the scratch; it is freed before returning.
+tt_status zipup_entry(const char* what, const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max, double tol,
+                      const tt_fit_options* opt, const tt_mpo_desc* Cd, int* bond_out) {
+  g_create_error.clear();
+  if (!Cd || !bond_out || chi_max < 1 || !(tol >= 0.0)) return TT_ERR_INVALID_ARGUMENT;
+  tt_fit_options o{};
+  o.struct_size = sizeof(o);
+  o.update = TT_UPDATE_2SITE_SVD;
+  o.oversample = 10;
+  o.precision = TT_PREC_FP64;
+  o.sv_cutoff = -1;
+  o.prepare_inputs = 1;
+  if (opt) {
+    if (opt->struct_size != sizeof(tt_fit_options)) return TT_ERR_INVALID_ARGUMENT;
+    o = *opt;
+  }
+  if (o.update != 0 && o.update != 1) return TT_ERR_INVALID_ARGUMENT;
+  if (o.precision < 0 || o.precision > 5 || o.precision == TT_PREC_BF16_SPLIT || o.oversample < 0)
+    return TT_ERR_INVALID_ARGUMENT;
+  std::unique_ptr<tt_fit> hold(new tt_fit());
+  tt_fit* h = hold.get();
+  bool lane = false;
+  try {
+    int LA, LB, LC;
+    std::vector<int> doA, diA, bA, doB, diB, bB, doC, diC, bC;
+    read_desc(A, LA, doA, diA, bA);
+    if (B) {
+      read_desc(B, LB, doB, diB, bB);
+    } else {  // identity: d_out = d_in = A.d_in, bond 1
+      LB = LA;
+      doB = diA;
+      diB = diA;
+      bB.assign(LA + 1, 1);
+    }
+    read_desc(Cd, LC, doC, diC, bC);
+    if (LA != LB || LC != LA) return TT_ERR_SHAPE_MISMATCH;
+    for (int l = 0; l < LA; ++l)
+      if (diA[l] != doB[l] || doC[l] != doA[l] || diC[l] != diB[l]) return TT_ERR_SHAPE_MISMATCH;
+    LaunchTally tally(h);
+    h->L = LA;
+    h->chi_max = chi_max;
+    h->tol = tol;
+    h->update = o.update;
+    h->oversample = o.oversample;
+    h->precision = o.precision;
+    h->seed = o.seed;
+    h->use_f32 = (o.precision != TT_PREC_FP64 && o.precision != TT_PREC_DF32);
+    h->cutoff = o.sv_cutoff >= 0 ? o.sv_cutoff : default_cutoff(o.precision, h->use_f32);
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, dev));
+    h->device = dev;
+    init_lane(h, h->w0, (cudaStream_t)o.stream, false);
+    lane = true;
+    Dims& D = h->D;
+    D.L = LA;
+    D.ds = doA;
+    D.du = diA;
+    D.dt = diB;
+    D.a = bA;
+    D.b = bB;
+    upload(h, A, doA, diA, bA, h->A64);
+    if (B) {
+      upload(h, B, doB, diB, bB, h->B64);
+    } else {
+      h->B64.resize(LA);
+      for (int l = 0; l < LA; ++l) {
+        const int d = diA[l];
+        std::vector<double> eye((size_t)d * d, 0.0);
+        for (int i = 0; i < d; ++i) eye[(size_t)i * d + i] = 1.0;
+        h->B64[l] = h->pool.alloc<double>((size_t)d * d);
+        CK(cudaMemcpyAsync(h->B64[l], eye.data(), sizeof(double) * d * d, cudaMemcpyHostToDevice, W(h).st));
+        CK(cudaStreamSynchronize(W(h).st));
+      }
+    }
+    CK(cudaStreamSynchronize(W(h).st));
+    long long mc = 1;
+    for (int l = 0; l < LA; ++l) {
+      mc = std::max(mc, prodll({bA[l], doA[l], diA[l], bA[l + 1]}));
+      mc = std::max(mc, prodll({bB[l], doB[l], diB[l], bB[l + 1]}));
+    }
+    if (o.prepare_inputs) prepare_ab(h, mc);
+    std::vector<double*> Cc;
+    std::vector<int> cb;
+    if (h->use_f32) zipup_rl<float>(h, Cc, cb);
+    else zipup_rl<double>(h, Cc, cb);
+    for (int l = 0; l <= LA; ++l)
+      if (cb[l] > bC[l]) throw TTError(TT_ERR_SHAPE_MISMATCH, "a kept bond exceeds C.bond");
+    for (int l = 0; l < LA; ++l) {
+      const long long n = prodll({cb[l], doA[l], diB[l], cb[l + 1]});
+      const double sc = l == 0 ? std::ldexp(1.0, h->escale) : 1.0;
+      if (Cd->dtype == TT_DTYPE_F64)
+        CK(copy_map<double, double>(1, (int)n, Cc[l], IdxMap::lin(0), IdxMap::lin(1), (double*)Cd->cores[l],
+                                    IdxMap::lin(0), IdxMap::lin(1), sc, W(h).st));
+      else
+        CK(copy_map<double, float>(1, (int)n, Cc[l], IdxMap::lin(0), IdxMap::lin(1), (float*)Cd->cores[l],
+                                   IdxMap::lin(0), IdxMap::lin(1), sc, W(h).st));
+    }
+    CK(cudaStreamSynchronize(W(h).st));
+    for (int l = 0; l <= LA; ++l) bond_out[l] = cb[l];
+    free_lanes(h);
+    return TT_OK;
+  } catch (const TTError& e) {
+    g_create_error = std::string(what) + ": " + e.what();
+    cudaGetLastError();
+    cudaDeviceSynchronize();
+    if (lane) free_lanes(h);
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    cudaDeviceSynchronize();
+    if (lane) free_lanes(h);
+    return TT_ERR_OUT_OF_MEMORY;
+  } catch (...) {
+    cudaDeviceSynchronize();
+    if (lane) free_lanes(h);
+    return TT_ERR_CUDA;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+tt_status tt_mpo_zipup(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max, double tol,
+                       const tt_fit_options* opt, const tt_mpo_desc* C, int* bond_out) {
+  if (!B) return TT_ERR_INVALID_ARGUMENT;
+  return zipup_entry("tt_mpo_zipup", A, B, chi_max, tol, opt, C, bond_out);
+}
+
+tt_status tt_mpo_compress(const tt_mpo_desc* X, int chi_max, double tol, const tt_fit_options* opt,
+                          const tt_mpo_desc* C, int* bond_out) {
+  return zipup_entry("tt_mpo_compress", X, nullptr, chi_max, tol, opt, C, bond_out);
+}
+
 tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max, double tol, int gauge,
                         const tt_fit_options* opt, tt_fit** out) {
   if (!out) return TT_ERR_INVALID_ARGUMENT;
@@ -1775,7 +2231,7 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
     }
     if (o.update != 0 && o.update != 1) return TT_ERR_INVALID_ARGUMENT;
     if (o.precision < 0 || o.precision > 5 || o.oversample < 0) return TT_ERR_INVALID_ARGUMENT;
-    if (o.init < 0 || o.init > 2 || (o.init == TT_INIT_GIVEN && !o.init_C)) return TT_ERR_INVALID_ARGUMENT;
+    if (o.init < 0 || o.init > 3 || (o.init == TT_INIT_GIVEN && !o.init_C)) return TT_ERR_INVALID_ARGUMENT;
     if (o.precision == TT_PREC_BF16_SPLIT) return TT_ERR_INVALID_ARGUMENT;  // reserved, not implemented
     if (o.n_segments > 1 && gauge != TT_GAUGE_INVERSE_CANONICAL) return TT_ERR_INVALID_ARGUMENT;
     if (o.edge_extra < 0) return TT_ERR_INVALID_ARGUMENT;
@@ -1845,39 +2301,7 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
       if (g->L == LA && g->bond && g->d_out && g->d_in)
         for (int l = 0; l < LA; ++l) mc = std::max(mc, prodll({g->bond[l], g->d_out[l], g->d_in[l], g->bond[l + 1]}));
     }
-    if (o.prepare_inputs) {  // Alg. 5: left_orthogonalize(A), left_orthogonalize(B), concurrently
-      Prep PA = make_prep(h, mc), PB = make_prep(h, mc);
-      rq_sweep(h, PA, h->A64, D.a, D.ds, D.du, 1, true);
-      rq_sweep(h, PB, h->B64, D.b, D.du, D.dt, 1, true);
-      qr_sweep(h, PA, h->A64, D.a, D.ds, D.du);
-      qr_sweep(h, PB, h->B64, D.b, D.du, D.dt);
-      finish_prep(h, PA);
-      finish_prep(h, PB);
-      // A and B are now left-canonical with their norms in the last cores. The fit is equivariant
-      // in the scale of A and B, so those cores are scaled by powers of two (exact) to norm ~1
-      // and the scale is given back to C on export: long chains of normalised random cores
-      // (||A B|| ~ 0.2^L) then stay inside the range of the FP32 / double-FP32 chains
-      auto unit = [&](std::vector<double*>& X, const std::vector<int>& bd, const std::vector<int>& d1,
-                      const std::vector<int>& d2) {
-        const int j = LA - 1;
-        const long long n = prodll({bd[j], d1[j], d2[j], bd[j + 1]});
-        CK(frob_norm<double>(X[j], n, W(h).dnorm, nullptr, W(h).st));
-        double nrm = 0;
-        CK(cudaMemcpyAsync(&nrm, W(h).dnorm, sizeof(double), cudaMemcpyDeviceToHost, W(h).st));
-        CK(cudaStreamSynchronize(W(h).st));
-        if (!(nrm > 0.0) || !std::isfinite(nrm)) return 0;
-        const int e = (int)std::lround(std::log2(nrm));
-        if (e == 0) return 0;
-        double* y = h->pool.alloc<double>(n);
-        CK(copy_map<double, double>(1, (int)n, X[j], IdxMap::lin(0), IdxMap::lin(1), y, IdxMap::lin(0), IdxMap::lin(1),
-                                    std::ldexp(1.0, -e), W(h).st));
-        CK(cudaStreamSynchronize(W(h).st));
-        h->pool.release(X[j]);
-        X[j] = y;
-        return e;
-      };
-      h->escale = unit(h->A64, D.a, D.ds, D.du) + unit(h->B64, D.b, D.du, D.dt);
-    }
+    if (o.prepare_inputs) prepare_ab(h, mc);  // Alg. 5: left_orthogonalize(A), left_orthogonalize(B)
     // capacity of C bonds: min(chi_max, prod of local dims to the left / right)
     const int L = LA;
     D.cb.assign(L + 1, 1);
@@ -1920,6 +2344,10 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
         cudaStreamDestroy(x);
       }
       for (void* d : dead) h->pool.release(d);
+    } else if (o.init == TT_INIT_ZIPUP) {  // Sec. 2.3.5: the zip-up contraction of A and B
+      if (h->use_f32) zipup_rl<float>(h, C0, cbond);
+      else zipup_rl<double>(h, C0, cbond);
+      for (int l = 1; l < L; ++l) D.cb[l] = std::max(D.cb[l], cbond[l]);
     } else {
       std::vector<int> dz, bz;
       const tt_mpo_desc* src = (o.init == TT_INIT_COPY_B) ? nullptr : o.init_C;

@@ -82,6 +82,10 @@ template <typename F>
 cudaError_t truncate_rule(const F* S, int p, const double* normM, double tau_over_L, int chi_max,
                           double cutoff, int* info, double* dinfo, cudaStream_t st);
 
+// x_j = sqrt(max(x_j, 0)) (singular values from Gram eigenvalues)
+template <typename F>
+cudaError_t sqrt_clamp(int n, F* x, cudaStream_t st);
+
 // Gauge update after the factorisation of the m x n two-site matrix
 // (U: m x ld_u col-major, S, V: n x ld_v col-major; k from *kdev):
 // mode 0 = site forward (C_l = U, C_{l+1} = S V^T), 1 = site backward

@@ -1412,6 +1412,24 @@ template cudaError_t truncate_rule<double>(const double*, int, const double*, do
 template cudaError_t truncate_rule<float>(const float*, int, const double*, double, int, double, int*, double*,
                                           cudaStream_t);
 
+// s_j = sqrt(max(lambda_j, 0)): singular values from the eigenvalues of a Gram matrix
+template <typename F>
+__global__ void sqrt_clamp_kernel(int n, F* x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const F v = x[i];
+    x[i] = v > F(0) ? sqrt(v) : F(0);
+  }
+}
+template <typename F>
+cudaError_t sqrt_clamp(int n, F* x, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  ++tl_launches;
+  sqrt_clamp_kernel<F><<<(n + 255) / 256, 256, 0, st>>>(n, x);
+  return cudaGetLastError();
+}
+template cudaError_t sqrt_clamp<double>(int, double*, cudaStream_t);
+template cudaError_t sqrt_clamp<float>(int, float*, cudaStream_t);
+
 // ---------------------------------------------------------------------------
 template <typename T, typename F>
 __global__ void gauge_update_kernel(int mode, int m, int n, const F* __restrict__ U, int ld_u,

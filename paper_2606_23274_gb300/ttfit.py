@@ -22,7 +22,7 @@ TT_ERR_CUDA, TT_ERR_NUMERICAL, TT_ERR_TIMEOUT, TT_ERR_STATE = 4, 5, 6, 7
 GAUGE = {"site": 0, "inverse": 1}
 UPDATE = {"svd": 0, "rsvd": 1}
 PRECISION = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16_split": 3, "tf32x3": 4, "df32": 5}
-INIT = {"random": 0, "copy_b": 1, "given": 2}
+INIT = {"random": 0, "copy_b": 1, "given": 2, "zipup": 3}
 TT_FAULT_ALLOC_FAIL, TT_FAULT_NAN_INPUT, TT_FAULT_SVD_NOCONV = 0x1, 0x2, 0x4
 DTYPE_F64, DTYPE_F32 = 0, 1
 
@@ -96,6 +96,17 @@ def load():
         lib.tt_mpo_grad.restype = ct.c_int
         lib.tt_fit_jacobi_sweeps.argtypes = [ct.c_void_p, ct.POINTER(ct.c_int)]
         lib.tt_fit_jacobi_sweeps.restype = ct.c_int
+        lib.tt_mpo_naive_product.argtypes = [ct.POINTER(tt_mpo_desc), ct.POINTER(tt_mpo_desc),
+                                             ct.POINTER(tt_mpo_desc), ct.c_void_p]
+        lib.tt_mpo_naive_product.restype = ct.c_int
+        for name in ("tt_mpo_zipup",):
+            getattr(lib, name).argtypes = [ct.POINTER(tt_mpo_desc), ct.POINTER(tt_mpo_desc), ct.c_int, ct.c_double,
+                                           ct.POINTER(tt_fit_options), ct.POINTER(tt_mpo_desc),
+                                           ct.POINTER(ct.c_int)]
+            getattr(lib, name).restype = ct.c_int
+        lib.tt_mpo_compress.argtypes = [ct.POINTER(tt_mpo_desc), ct.c_int, ct.c_double, ct.POINTER(tt_fit_options),
+                                        ct.POINTER(tt_mpo_desc), ct.POINTER(ct.c_int)]
+        lib.tt_mpo_compress.restype = ct.c_int
         lib.tt_device_cache_release.argtypes = [ct.c_int]
         lib.tt_device_cache_release.restype = ct.c_size_t
         _lib = lib
@@ -303,6 +314,71 @@ def tt_svd_truncated(M, chi_max: int, tau_rel: float = 0.0, stream=None):
                                 Vt.data_ptr(), ct.byref(k), ct.c_void_p(stream.cuda_stream))
     _check(code, None, "tt_svd_truncated")
     return U, S, Vt, k.value
+
+
+def tt_mpo_naive_product(A, B, stream=None, device="cuda"):
+    """Exact per-site product C_l = A_l x B_l (Alg. 1's contraction step,
+    tt_mpo_naive_product); returns the cores of C (bond chi_A chi_B) as device
+    tensors of the inputs' dtype."""
+    import torch
+    lib = load()
+    Ad, Bd = _as_device(A, device), _as_device(B, device)
+    dA, dB = _Desc(Ad), _Desc(Bd)
+    C = [torch.empty((a.shape[0] * b.shape[0], a.shape[1], b.shape[2], a.shape[3] * b.shape[3]), dtype=a.dtype,
+                     device=a.device) for a, b in zip(dA.tensors, dB.tensors)]
+    dC = _Desc(C)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    code = lib.tt_mpo_naive_product(ct.byref(dA.desc), ct.byref(dB.desc), ct.byref(dC.desc),
+                                    ct.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)))
+    _check(code, None, "tt_mpo_naive_product")
+    return C
+
+
+def _zipup_call(name, X, Y, chi_max, tol, dtype, device, kw):
+    import torch
+    lib = load()
+    Xd = _as_device(X, device)
+    dX = _Desc(Xd)
+    dY = _Desc(_as_device(Y, device)) if Y is not None else None
+    L = len(Xd)
+    dout = [x.shape[1] for x in Xd]
+    din = [y.shape[2] for y in (dY.tensors if dY else Xd)]
+    if len(din) != L:  # the library reports the mismatch
+        din = dout
+    cap = [1] * (L + 1)
+    right = 1
+    for l in range(L - 1, 0, -1):
+        right *= dout[l] * din[l]
+        ab = Xd[l].shape[0] * (dY.tensors[l].shape[0] if dY and l < len(dY.tensors) else 1)
+        cap[l] = int(min(chi_max, ab, right))
+    dt = dtype or Xd[0].dtype
+    C = [torch.empty((cap[l], dout[l], din[l], cap[l + 1]), dtype=dt, device=Xd[0].device) for l in range(L)]
+    dC = _Desc(C)
+    o, _keep = _options(device=device, **kw)
+    bonds = (ct.c_int * (L + 1))()
+    if dY is not None:
+        code = lib.tt_mpo_zipup(ct.byref(dX.desc), ct.byref(dY.desc), int(chi_max), float(tol), ct.byref(o),
+                                ct.byref(dC.desc), bonds)
+    else:
+        code = lib.tt_mpo_compress(ct.byref(dX.desc), int(chi_max), float(tol), ct.byref(o), ct.byref(dC.desc), bonds)
+    _check(code, None, name)
+    b = list(bonds)
+    return [C[l].reshape(-1)[: b[l] * dout[l] * din[l] * b[l + 1]].reshape(b[l], dout[l], din[l], b[l + 1])
+            for l in range(L)]
+
+
+def tt_mpo_zipup(A, B, chi_max: int, tol: float = 0.0, *, dtype=None, device="cuda", **kw):
+    """Zip-up contraction C ~ A B (Alg. 2, tt_mpo_zipup). Keywords as for
+    tt_fit_create (update, oversample, seed, precision, sv_cutoff, stream,
+    prepare_inputs); returns the cores of C as device tensors (dtype: that of A
+    unless given)."""
+    return _zipup_call("tt_mpo_zipup", A, B, chi_max, tol, dtype, device, kw)
+
+
+def tt_mpo_compress(X, chi_max: int, tol: float = 0.0, *, dtype=None, device="cuda", **kw):
+    """compress() of Alg. 1 (tt_mpo_compress): truncated SVD sweep of X."""
+    return _zipup_call("tt_mpo_compress", X, None, chi_max, tol, dtype, device, kw)
 
 
 def tt_device_cache_release(device: int = -1) -> int:
