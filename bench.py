@@ -37,6 +37,7 @@ METRIC = "MPO-MPO fit time-to-tol (s) & local-update TFLOP/s vs peak, L=30 χ=12
 WORKLOAD = "kron_L30_chi128"
 L_SITES, CHI, OVERSAMPLE, TOL, MAX_SWEEPS = 30, 128, 10, 1e-8, 14
 LO_SWEEPS = 1  # default: cheap sweeps before the FP64-class ones
+SCHEDULE = "tf32x3>df32"  # default precision schedule of the timed fit
 
 
 def parse():
@@ -45,7 +46,7 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="native", choices=["native", "reference"])
-    p.add_argument("--precision", default=os.environ.get("TTFIT_BENCH_PRECISION", "tf32x3>df32"),
+    p.add_argument("--precision", default=os.environ.get("TTFIT_BENCH_PRECISION", SCHEDULE),
                    help='a precision ("fp64", "df32", "fp32", "tf32x3", ...) or a schedule "lo>hi"')
     p.add_argument("--lo-sweeps", type=int, default=LO_SWEEPS,
                    help="sweeps (>= 1) in the cheap precision of a 'lo>hi' schedule before the switch")
@@ -150,7 +151,7 @@ FMA_LANES = {"f64": 2, "f32": 128}
 DF32_INSTR = 15  # FP32 instructions of one double-FP32 multiply-add (csrc/common.cuh, madd)
 
 
-def run_fit(ttfit, Ain, Bin, schedule, seed, dev, stream, chi=CHI, lo_sweeps=LO_SWEEPS):
+def run_fit(ttfit, Ain, Bin, schedule, seed, dev, stream, chi=CHI, lo_sweeps=LO_SWEEPS, init="random"):
     """One complete fit. ``schedule`` is a precision name ("fp64", "df32", "tf32x3", ...) for a
     single-precision fit, or "lo>hi", e.g. "tf32x3>df32": sweeps in ``lo`` (FP32-factorised
     randomized update) for ``lo_sweeps`` sweeps, then FP64-class contractions in ``hi`` with the
@@ -160,7 +161,7 @@ def run_fit(ttfit, Ain, Bin, schedule, seed, dev, stream, chi=CHI, lo_sweeps=LO_
     ev = {k: torch.cuda.Event(enable_timing=True) for k in ("c0", "c1", "s0", "s1", "r0", "r1")}
     ev["c0"].record(stream)
     f = ttfit.tt_fit_create(Ain, Bin, chi, TOL, "site", update="rsvd", oversample=OVERSAMPLE, seed=seed,
-                            precision=lo, device=dev, stream=stream)
+                            precision=lo, device=dev, stream=stream, init=init)
     ev["c1"].record(stream)
     switched = False
     phases = {lo: {k: 0.0 for k in STAGES}}
@@ -534,7 +535,40 @@ def extras(ttfit, dev, stream, norm2_site):
         t, _ = _timed(stream, lambda: ttfit.tt_mpo_grad(A5, B5, X, target, "fp32", 0, stream=stream))
         res5[target] = round(t, 4)
     out["config5_adjoint_L32_chi96_fp32_s"] = res5
+
+    # the zip-up contraction (Alg. 2) of the timed workload, alone and as the fit's initial guess
+    # (Sec. 2.3.5), against the random guess of the timed fit
+    zu = {}
+    for prec in ("tf32x3", "fp64"):
+        kwz = dict(update="rsvd", oversample=OVERSAMPLE, seed=0, precision=prec, stream=stream, device=dev)
+        ttfit.tt_mpo_zipup(A, B, CHI, TOL, **kwz)  # warm-up
+        t, Cz = _timed(stream, lambda: ttfit.tt_mpo_zipup(A, B, CHI, TOL, **kwz))
+        zu[f"zipup_{prec}_s"] = round(t, 4)
+        zu[f"zipup_{prec}_norm2_rel_to_site_fit"] = float(f"{sum_sq(Cz) / norm2_site - 1.0:.3e}")
+    for init in ("zipup", "random"):
+        run_fit(ttfit, A, B, SCHEDULE, 0, dev, stream, init=init)  # warm-up
+        t, (rep, sweeps, _, _, _, _) = _timed(stream, lambda: run_fit(ttfit, A, B, SCHEDULE, 0, dev, stream,
+                                                                       init=init))
+        zu[f"fit_from_{init}"] = {"time_to_tol_s": round(t, 4), "sweeps": sweeps, "converged": bool(rep["converged"]),
+                                  "norm2_rel_to_site_fit": float(f"{rep['norm2_C'] / norm2_site - 1.0:.3e}"),
+                                  "delta_history": [float(f"{d:.3e}") if d != float("inf") else None
+                                                    for d in rep["history"]]}
+    out["zipup_L30_chi128"] = zu
     return out
+
+
+def sum_sq(C) -> float:
+    """||C||_F^2 of an MPO on the device (FP64 left-orthogonalisation, QR per site)."""
+    import torch
+    M = None
+    for c in C:
+        c = c.double()
+        a0, d, dp, a1 = c.shape
+        X = c.reshape(a0, -1) if M is None else M @ c.reshape(a0, -1)
+        X = X.reshape(-1, a1)
+        _, R = torch.linalg.qr(X)
+        M = R
+    return float(torch.sum(M * M))
 
 
 # --------------------------------------------------------------------------- oracle timing
