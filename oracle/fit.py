@@ -23,6 +23,11 @@ Readings of the paper taken here, where it is silent or ambiguous:
   A, B (oracle/zipup.py) with the fit's chi_max, tau, cut-off, update and
   seed: right-canonical with the orthogonality centre at site 1 as it comes.
   In the inverse gauge Psi_l = C0_l and Y_l = 1.
+* Randomized bond projection (Sec. 3.2, option ab_rank = k): the projectors
+  depend only on A and B, which the fit never changes, so they are drawn once:
+  A and B are replaced by their projected chains (oracle/zipup.py
+  project_bonds, streams (4 << 40) | l for A and (5 << 40) | l for B), brought
+  back to left-canonical form, and the fit runs on them in either gauge.
 * Truncation (Sec. 2.3.4): keep k = min(chi_max, min{k : sqrt(sum_{j>k} s_j^2)
   <= (tau/L) ||M||_F}), then drop s_j <= sv_cutoff * s_1 (Sec. 2.3.1 allows
   dropping very small values before inversion; applied in both gauges), k >= 1.
@@ -173,7 +178,7 @@ class FitState:
 class FitOracle:
     def __init__(self, A, B, chi_max, tol, gauge="site", update="svd", oversample=10,
                  seed=0, sv_cutoff=1e-13, conv_tol=None, init="random", init_C=None,
-                 prepare_inputs=True):
+                 prepare_inputs=True, ab_rank=0):
         assert gauge in ("site", "inverse") and update in ("svd", "rsvd")
         L = len(A)
         assert len(B) == L and L >= 2
@@ -187,6 +192,10 @@ class FitOracle:
         B = [np.asarray(x, np.float64) for x in B]
         if prepare_inputs:                       # Alg. 5: left_orthogonalize(A), (B)
             A, B = canonicalize_input(A), canonicalize_input(B)
+        if ab_rank > 0:                          # Sec. 3.2: rank-k projectors on the A and B bonds
+            from .zipup import project_bonds
+            A = left_orthogonalize(project_bonds(A, ab_rank, seed, 0))
+            B = left_orthogonalize(project_bonds(B, ab_rank, seed, 1))
         dout = [a.shape[1] for a in A]
         din = [b.shape[2] for b in B]
         if init == "random":

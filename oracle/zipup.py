@@ -136,3 +136,38 @@ def _factor_full(M, chi_max, tau, L, sv_cutoff, update, oversample, seed, site):
     k = keep_rank(S, norm_M, tau, L, chi_max, sv_cutoff)
     Uk, Vtk = fix_signs(U[:, :k], Vt[:k, :])
     return Uk, S[:k], Vtk, S
+
+
+def project_stream(which: int, site: int) -> int:
+    """Philox stream of the bond projector of A (which = 0) or B (which = 1) at a site (1-based)."""
+    return ((4 + int(which)) << 40) | int(site)
+
+
+def project_bonds(X, k, seed=0, which=0):
+    """Randomized bond projection of one MPO chain (Sec. 3.2): a projector Q Q^T of
+    rank k on every bond. Reading: X (left-orthogonalized, so that everything left of
+    a bond is an isometry) is swept right to left; at site l the core with the
+    remainder absorbed, M = X_l R_{l+1} reshaped chi_{l-1} x (d d' k), gets the
+    range finder of Sec. 3: Y = M^T Omega (Omega chi_{l-1} x k Gaussian, stream
+    project_stream(which, l)), Q = the orthonormal factor of Y (d d' k x k);
+    X_l <- Q^T and R_l = M Q. Where k >= min of M's sizes the bond is kept whole
+    (Q = the orthonormal factor of M^T). The result is right-canonical."""
+    X = left_orthogonalize([np.asarray(x, np.float64) for x in X])
+    L = len(X)
+    R = np.ones((1, 1))
+    out = [None] * L
+    for l in range(L - 1, -1, -1):
+        T = np.einsum("astx,xc->astc", X[l], R)
+        a, s, t, c = T.shape
+        if l == 0:
+            out[0] = T
+            break
+        M = T.reshape(a, s * t * c)
+        if k < min(M.shape):
+            Om = philox.normals(seed, project_stream(which, l + 1), a * k).reshape(a, k)
+            Q, _ = np.linalg.qr(M.T @ Om)
+        else:
+            Q, _ = np.linalg.qr(M.T)
+        out[l] = Q.T.reshape(Q.shape[1], s, t, c)
+        R = M @ Q
+    return out

@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 
 from oracle.mpo import mpo_diff_norm, mpo_norm, naive_product, to_dense
-from oracle.zipup import compress, zipup_left_to_right, zipup_right_to_left
+from oracle.zipup import compress, project_bonds, zipup_left_to_right, zipup_right_to_left
 from paper_2606_23274_gb300.synth import gaussian_mpo, kron_sum_mpo
 
 
@@ -131,3 +131,68 @@ def test_fit_from_the_zipup_guess():
         f.sweep(10, stop_on_converge=False)
         n2.append(f.st.history[-1].norm2)
     assert abs(n2[0] - n2[1]) <= 1e-8 * n2[1]
+
+
+def _pad_bonds(X, width, seed):
+    """The same operator with every inner bond widened to `width` by random isometries
+    (bond rank unchanged)."""
+    rng = np.random.default_rng(seed)
+    X = [x.copy() for x in X]
+    for l in range(len(X) - 1):
+        r = X[l].shape[3]
+        V, _ = np.linalg.qr(rng.standard_normal((width, r)))      # width x r, orthonormal columns
+        X[l] = np.einsum("asty,zy->astz", X[l], V)
+        X[l + 1] = np.einsum("zy,yuvb->zuvb", V, X[l + 1])
+    return X
+
+
+def test_bond_projection_is_exact_when_k_covers_the_bond_rank():
+    """Sec. 3.2's range finder: a chi x (d d' chi) matrix of rank r <= k is captured
+    exactly by k Gaussian test vectors; here the bonds are 12 wide but of rank 4,
+    so rank-6 projectors keep the operator (and shrink the bonds to 6)."""
+    X = _pad_bonds(kron_sum_mpo(7, 4, 3, 0), 12, 1)
+    assert max(x.shape[3] for x in X) == 12
+    P = project_bonds(X, 6, seed=2)
+    assert mpo_diff_norm(X, P) <= 1e-12 * mpo_norm(X)
+    assert max(p.shape[3] for p in P) == 6
+    for c in P[1:]:
+        M = c.reshape(c.shape[0], -1)
+        assert np.allclose(M @ M.T, np.eye(c.shape[0]), atol=1e-12)
+
+
+def test_bond_projection_error_of_two_sites():
+    """L = 2: the projected operator is M Q Q^T across the bond, whose error is at
+    least the Eckart-Young tail and equals || M (I - Q Q^T) || computed densely."""
+    X = gaussian_mpo(2, 2, 8, 4, 0, 0.5)
+    D = to_dense(X).reshape(2, 2, 2, 2).transpose(0, 2, 1, 3).reshape(4, 4)
+    s = np.linalg.svd(D, compute_uv=False)
+    for k in (1, 2, 3):
+        P = project_bonds(X, k, seed=9)
+        E = to_dense(P).reshape(2, 2, 2, 2).transpose(0, 2, 1, 3).reshape(4, 4)
+        err = np.linalg.norm(D - E)
+        assert err >= np.sqrt(np.sum(s[k:] ** 2)) * (1 - 1e-12)
+        Q = P[1].reshape(P[1].shape[0], -1).T                      # (s t) x k, orthonormal
+        assert abs(err - np.linalg.norm(D - D @ Q @ Q.T)) <= 1e-12 * s[0]
+
+
+def test_fit_with_projected_inputs():
+    """ab_rank above every bond of A and B leaves the fit as it was; a smaller rank fits
+    the product of the projected chains."""
+    from oracle.fit import FitOracle
+    A = kron_sum_mpo(8, 6, 5, 0)
+    B = kron_sum_mpo(8, 6, 5, 1)
+    f0 = FitOracle(A, B, 12, 0.0, conv_tol=0.0)
+    f1 = FitOracle(A, B, 12, 0.0, conv_tol=0.0, ab_rank=16)
+    f0.sweep(3, stop_on_converge=False)
+    f1.sweep(3, stop_on_converge=False)
+    assert abs(f0.st.history[-1].norm2 - f1.st.history[-1].norm2) <= 1e-12 * f0.st.history[-1].norm2
+    # a smaller rank fits the product of the projected chains
+    from oracle.mpo import canonicalize_input, left_orthogonalize
+    f2 = FitOracle(A, B, 12, 0.0, conv_tol=0.0, ab_rank=3, seed=4)
+    f2.sweep(3, stop_on_converge=False)
+    Ap = left_orthogonalize(project_bonds(canonicalize_input(A), 3, 4, 0))
+    Bp = left_orthogonalize(project_bonds(canonicalize_input(B), 3, 4, 1))
+    assert max(x.shape[3] for x in Ap) == 3
+    f3 = FitOracle(Ap, Bp, 12, 0.0, conv_tol=0.0, seed=4, prepare_inputs=False)
+    f3.sweep(3, stop_on_converge=False)
+    assert mpo_diff_norm(f2.result(), f3.result()) <= 1e-12 * mpo_norm(f3.result())
