@@ -151,7 +151,7 @@ FMA_LANES = {"f64": 2, "f32": 128}
 DF32_INSTR = 15  # FP32 instructions of one double-FP32 multiply-add (csrc/common.cuh, madd)
 
 
-def run_fit(ttfit, Ain, Bin, schedule, seed, dev, stream, chi=CHI, lo_sweeps=LO_SWEEPS, init="random"):
+def run_fit(ttfit, Ain, Bin, schedule, seed, dev, stream, chi=CHI, lo_sweeps=LO_SWEEPS, init="random", ab_rank=0):
     """One complete fit. ``schedule`` is a precision name ("fp64", "df32", "tf32x3", ...) for a
     single-precision fit, or "lo>hi", e.g. "tf32x3>df32": sweeps in ``lo`` (FP32-factorised
     randomized update) for ``lo_sweeps`` sweeps, then FP64-class contractions in ``hi`` with the
@@ -161,7 +161,7 @@ def run_fit(ttfit, Ain, Bin, schedule, seed, dev, stream, chi=CHI, lo_sweeps=LO_
     ev = {k: torch.cuda.Event(enable_timing=True) for k in ("c0", "c1", "s0", "s1", "r0", "r1")}
     ev["c0"].record(stream)
     f = ttfit.tt_fit_create(Ain, Bin, chi, TOL, "site", update="rsvd", oversample=OVERSAMPLE, seed=seed,
-                            precision=lo, device=dev, stream=stream, init=init)
+                            precision=lo, device=dev, stream=stream, init=init, ab_rank=ab_rank)
     ev["c1"].record(stream)
     switched = False
     phases = {lo: {k: 0.0 for k in STAGES}}
@@ -554,6 +554,20 @@ def extras(ttfit, dev, stream, norm2_site):
                                   "delta_history": [float(f"{d:.3e}") if d != float("inf") else None
                                                     for d in rep["history"]]}
     out["zipup_L30_chi128"] = zu
+
+    # randomized bond projection of A and B (Sec. 3.2) to rank k, the default schedule; error relative
+    # to the unprojected fit of the same schedule
+    _, _, _, _, C_full, _ = run_fit(ttfit, A, B, SCHEDULE, 0, dev, stream)
+    pr = {}
+    for k in (32, 64, 96):
+        run_fit(ttfit, A, B, SCHEDULE, 0, dev, stream, ab_rank=k)  # warm-up
+        t, (rep, sweeps, _, phases, C_k, _) = _timed(stream, lambda: run_fit(ttfit, A, B, SCHEDULE, 0, dev, stream,
+                                                                             ab_rank=k))
+        chain_ms = sum(ph["halves_ms"] + ph["join_ms"] + ph["env_finish_ms"] for ph in phases.values())
+        pr[str(k)] = {"time_to_tol_s": round(t, 4), "sweeps": sweeps, "converged": bool(rep["converged"]),
+                      "chain_ms": round(chain_ms, 2),
+                      "rel_frobenius_vs_unprojected": float(f"{rel_frobenius(C_k, C_full):.3e}")}
+    out["bond_projection_L30_chi128"] = pr
     return out
 
 

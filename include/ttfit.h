@@ -130,6 +130,14 @@ typedef struct {
                        /* merge, not built); see tt_fit_sweep for what a sweep is then.     */
   int edge_extra;      /* sites moved from the inner segments to each edge segment (load   */
                        /* balance of Sec. 4.1: edge segments have one neighbour), default 0 */
+  int ab_rank;         /* randomized bond projection of the A and B chains (Sec. 3.2): k > 0 */
+                       /* puts a rank-k projector Q Q^T on every bond of A and of B, Q the    */
+                       /* orthonormal range of a k-column Philox Gaussian sketch of the bond  */
+                       /* (streams (4 << 40) | l for A, (5 << 40) | l for B, site l 1-based), */
+                       /* drawn once at creation on the prepared chains (right to left, then */
+                       /* the QR sweep again); the fit then contracts bonds of at most k. The */
+                       /* fit approximates the product of the projected chains, so this needs */
+                       /* A and B with decaying bond spectra. Needs prepare_inputs. 0 = off.  */
 } tt_fit_options;
 
 /* Host-side fault injection (tests only; nothing here touches the device). */

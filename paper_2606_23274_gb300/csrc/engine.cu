@@ -1732,6 +1732,51 @@ void prepare_ab(tt_fit* h, long long mc) {
 // ---------------------------------------------------------------------------
 inline uint64_t zipup_stream(int site1) { return (3ull << 40) | (uint64_t)site1; }
 
+// Inputs of one zip-up: the two chains (FP64 device cores, row-major) with
+// their bonds a, b and legs ds (X out), du (X in = Y out), dt (Y in), and the
+// truncation and sketch parameters. The sketch of site l (1-based) draws the
+// Philox stream stream_base | l.
+struct ZipArgs {
+  std::vector<double*> X, Y;
+  std::vector<int> a, b, ds, du, dt;
+  int chi_max = 1, oversample = 0;
+  double tol = 0.0, cutoff = 0.0;
+  bool rsvd = false;
+  uint64_t stream_base = 3ull << 40;
+};
+
+// The zip-up of the fit's prepared A and B with its own parameters.
+ZipArgs zip_of_fit(tt_fit* h) {
+  ZipArgs z;
+  z.X = h->A64;
+  z.Y = h->B64;
+  z.a = h->D.a;
+  z.b = h->D.b;
+  z.ds = h->D.ds;
+  z.du = h->D.du;
+  z.dt = h->D.dt;
+  z.chi_max = h->chi_max;
+  z.oversample = h->oversample;
+  z.tol = h->tol;
+  z.cutoff = h->cutoff;
+  z.rsvd = h->update == TT_UPDATE_2SITE_RSVD;
+  z.stream_base = 3ull << 40;
+  return z;
+}
+
+// Identity MPO cores (1, d_l, d_l, 1) on the device.
+std::vector<double*> identity_chain(tt_fit* h, const std::vector<int>& d) {
+  std::vector<double*> I(d.size());
+  for (size_t l = 0; l < d.size(); ++l) {
+    std::vector<double> eye((size_t)d[l] * d[l], 0.0);
+    for (int i = 0; i < d[l]; ++i) eye[(size_t)i * d[l] + i] = 1.0;
+    I[l] = h->pool.alloc<double>(eye.size());
+    CK(cudaMemcpyAsync(I[l], eye.data(), sizeof(double) * eye.size(), cudaMemcpyHostToDevice, W(h).st));
+    CK(cudaStreamSynchronize(W(h).st));
+  }
+  return I;
+}
+
 template <typename T>
 void zgemm(tt_fit* h, const GemmArgs<T>& g, T* ws, size_t wse, bool tc) {
   if constexpr (sizeof(T) == 4) {
@@ -1748,21 +1793,21 @@ void zgemm(tt_fit* h, const GemmArgs<T>& g, T* ws, size_t wse, bool tc) {
 }
 
 template <typename T>
-void zipup_rl(tt_fit* h, std::vector<double*>& C, std::vector<int>& cb) {
-  const Dims& D = h->D;
-  const int L = D.L;
+void zipup_rl(tt_fit* h, const ZipArgs& z, std::vector<double*>& C, std::vector<int>& cb) {
+  const ZipArgs& D = z;
+  const int L = (int)z.X.size();
   Work& w = W(h);
   cudaStream_t st = w.st;
   const bool tc = sizeof(T) == 4 && (h->precision == TT_PREC_TF32 || h->precision == TT_PREC_TF32_SPLIT);
-  const int ks = h->chi_max + h->oversample;
-  const bool rsvd_on = h->update == TT_UPDATE_2SITE_RSVD;
+  const int ks = z.chi_max + z.oversample;
+  const bool rsvd_on = z.rsvd;
   C.assign(L, nullptr);
   cb.assign(L + 1, 1);
   // scratch for the largest site (chi of the remainder <= min(chi_max, chi_A chi_B of the next site))
   size_t sz_mn = 1, sz_t2 = 1, sz_om = 1, sz_nk = 1, sz_z = 1, sz_zc = 1, sz_u = 1, sz_pp = 1, sz_p = 1, sz_r = 1,
          sz_ab = 1;
   for (int l = 0; l < L; ++l) {
-    const long long c = l == L - 1 ? 1 : std::min<long long>(h->chi_max, (long long)D.a[l + 1] * D.b[l + 1]);
+    const long long c = l == L - 1 ? 1 : std::min<long long>(z.chi_max, (long long)D.a[l + 1] * D.b[l + 1]);
     const long long m = (long long)D.a[l] * D.b[l], n = (long long)D.ds[l] * D.dt[l] * c;
     if (n > 1024) throw TTError(TT_ERR_INVALID_ARGUMENT, "zip-up: d d' chi above 1024 at a site");
     const bool rs = rsvd_on && ks < std::min(m, n);
@@ -1789,7 +1834,7 @@ void zipup_rl(tt_fit* h, std::vector<double*>& C, std::vector<int>& cb) {
     }
     sz_pp = std::max<size_t>(sz_pp, p * p);
     sz_p = std::max<size_t>(sz_p, std::max(p, m));
-    sz_r = std::max<size_t>(sz_r, m * std::min<long long>(h->chi_max, std::min(m, n)));
+    sz_r = std::max<size_t>(sz_r, m * std::min<long long>(z.chi_max, std::min(m, n)));
   }
   const size_t wse = (size_t)1 << 22;
   std::vector<void*> bufs;
@@ -1814,12 +1859,12 @@ void zipup_rl(tt_fit* h, std::vector<double*>& C, std::vector<int>& cb) {
     const long long m = (long long)a0 * b0, n = (long long)s * t * c;
     const T *Ap, *Bp;
     if constexpr (std::is_same<T, double>::value) {
-      Ap = h->A64[l];
-      Bp = h->B64[l];
+      Ap = z.X[l];
+      Bp = z.Y[l];
     } else {
       const long long na = prodll({a0, s, u, a1}), nb = prodll({b0, u, t, b1});
-      copymap<double, T>(h, 1, (int)na, h->A64[l], IdxMap::lin(0), IdxMap::lin(1), Al, IdxMap::lin(0), IdxMap::lin(1));
-      copymap<double, T>(h, 1, (int)nb, h->B64[l], IdxMap::lin(0), IdxMap::lin(1), Bl, IdxMap::lin(0), IdxMap::lin(1));
+      copymap<double, T>(h, 1, (int)na, z.X[l], IdxMap::lin(0), IdxMap::lin(1), Al, IdxMap::lin(0), IdxMap::lin(1));
+      copymap<double, T>(h, 1, (int)nb, z.Y[l], IdxMap::lin(0), IdxMap::lin(1), Bl, IdxMap::lin(0), IdxMap::lin(1));
       Ap = Al;
       Bp = Bl;
     }
@@ -1869,7 +1914,7 @@ void zipup_rl(tt_fit* h, std::vector<double*>& C, std::vector<int>& cb) {
     const T* Zp = Mt;  // Z column-major m x p
     if (rs) {
       p = ks;
-      CK(philox_fill<T>(Om, m * ks, h->seed, zipup_stream(l + 1), 1.0, st));
+      CK(philox_fill<T>(Om, m * ks, h->seed, z.stream_base | (uint64_t)(l + 1), 1.0, st));
       copymap<T, T>(h, (int)m, ks, Om, IdxMap::lin(ks), IdxMap::lin(1), Omt, IdxMap::lin(1), IdxMap::lin(m));
       GemmArgs<T> g;  // Y (n x k_s, column-major) = M^T Omega
       g.M = (int)n;
@@ -1949,7 +1994,7 @@ void zipup_rl(tt_fit* h, std::vector<double*>& C, std::vector<int>& cb) {
       zgemm<T>(h, g, ws, wse, false);
     }
     CK(fix_signs<T>((int)n, 0, pv, Vn, (int)n, nullptr, 0, st));
-    CK(truncate_rule<T>(Sv, pv, w.dnorm, h->tol / L, h->chi_max, h->cutoff, w.dk, w.ddinfo, st));
+    CK(truncate_rule<T>(Sv, pv, w.dnorm, z.tol / L, z.chi_max, z.cutoff, w.dk, w.ddinfo, st));
     CK(cudaMemcpyAsync(w.hk, w.dk, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(w.herrw, w.errw, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -1977,6 +2022,48 @@ void zipup_rl(tt_fit* h, std::vector<double*>& C, std::vector<int>& cb) {
   }
   CK(cudaStreamSynchronize(st));
   for (void* b : bufs) h->pool.release(b);
+}
+
+// Randomized bond projection of the A and B chains (Sec. 3.2): a rank-k
+// projector on every bond, drawn once, since the fit never changes A or B.
+// Each prepared (left-canonical) chain is swept right to left as its zip-up
+// with the identity MPO, keeping the k-column Gaussian range of every bond
+// (streams (4 << 40) | l for A, (5 << 40) | l for B; bonds narrower than k stay
+// whole), in FP64 arithmetic, and is then brought back to left-canonical form by
+// the QR sweep.
+// The contractions of the fit then run on bonds of at most k.
+void project_ab(tt_fit* h, int k, long long mc) {
+  Dims& D = h->D;
+  for (int which = 0; which < 2; ++which) {
+    std::vector<double*>& X = which ? h->B64 : h->A64;
+    std::vector<int>& bx = which ? D.b : D.a;
+    const std::vector<int>& dout = which ? D.du : D.ds;
+    const std::vector<int>& din = which ? D.dt : D.du;
+    ZipArgs z;
+    z.X = X;
+    z.Y = identity_chain(h, din);
+    z.a = bx;
+    z.b.assign(D.L + 1, 1);
+    z.ds = dout;
+    z.du = din;
+    z.dt = din;
+    z.chi_max = k;
+    z.oversample = 0;
+    z.tol = 0.0;
+    z.cutoff = 0.0;
+    z.rsvd = true;
+    z.stream_base = (uint64_t)(4 + which) << 40;
+    std::vector<double*> P;
+    std::vector<int> pb;
+    zipup_rl<double>(h, z, P, pb);  // FP64 in every precision: a one-off O(L chi^3) pass
+    for (double* p : z.Y) h->pool.release(p);
+    for (double* p : X) h->pool.release(p);
+    X = P;
+    bx = pb;
+    Prep PX = make_prep(h, mc);
+    qr_sweep(h, PX, X, bx, dout, din);
+    finish_prep(h, PX);
+  }
 }
 
 void setup(tt_fit* h, const std::vector<double*>& C0) {
@@ -2139,15 +2226,7 @@ tt_status zipup_entry(const char* what, const tt_mpo_desc* A, const tt_mpo_desc*
     if (B) {
       upload(h, B, doB, diB, bB, h->B64);
     } else {
-      h->B64.resize(LA);
-      for (int l = 0; l < LA; ++l) {
-        const int d = diA[l];
-        std::vector<double> eye((size_t)d * d, 0.0);
-        for (int i = 0; i < d; ++i) eye[(size_t)i * d + i] = 1.0;
-        h->B64[l] = h->pool.alloc<double>((size_t)d * d);
-        CK(cudaMemcpyAsync(h->B64[l], eye.data(), sizeof(double) * d * d, cudaMemcpyHostToDevice, W(h).st));
-        CK(cudaStreamSynchronize(W(h).st));
-      }
+      h->B64 = identity_chain(h, diA);
     }
     CK(cudaStreamSynchronize(W(h).st));
     long long mc = 1;
@@ -2158,8 +2237,9 @@ tt_status zipup_entry(const char* what, const tt_mpo_desc* A, const tt_mpo_desc*
     if (o.prepare_inputs) prepare_ab(h, mc);
     std::vector<double*> Cc;
     std::vector<int> cb;
-    if (h->use_f32) zipup_rl<float>(h, Cc, cb);
-    else zipup_rl<double>(h, Cc, cb);
+    const ZipArgs z = zip_of_fit(h);
+    if (h->use_f32) zipup_rl<float>(h, z, Cc, cb);
+    else zipup_rl<double>(h, z, Cc, cb);
     for (int l = 0; l <= LA; ++l)
       if (cb[l] > bC[l]) throw TTError(TT_ERR_SHAPE_MISMATCH, "a kept bond exceeds C.bond");
     for (int l = 0; l < LA; ++l) {
@@ -2236,6 +2316,7 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
     if (o.n_segments > 1 && gauge != TT_GAUGE_INVERSE_CANONICAL) return TT_ERR_INVALID_ARGUMENT;
     if (o.edge_extra < 0) return TT_ERR_INVALID_ARGUMENT;
     if (o.fast_factor < 0 || o.fast_factor > 3) return TT_ERR_INVALID_ARGUMENT;
+    if (o.ab_rank < 0 || (o.ab_rank > 0 && !o.prepare_inputs)) return TT_ERR_INVALID_ARGUMENT;
     int LA, LB;
     std::vector<int> doA, diA, bA, doB, diB, bB;
     read_desc(A, LA, doA, diA, bA);
@@ -2302,6 +2383,7 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
         for (int l = 0; l < LA; ++l) mc = std::max(mc, prodll({g->bond[l], g->d_out[l], g->d_in[l], g->bond[l + 1]}));
     }
     if (o.prepare_inputs) prepare_ab(h, mc);  // Alg. 5: left_orthogonalize(A), left_orthogonalize(B)
+    if (o.ab_rank > 0) project_ab(h, o.ab_rank, mc);
     // capacity of C bonds: min(chi_max, prod of local dims to the left / right)
     const int L = LA;
     D.cb.assign(L + 1, 1);
@@ -2345,8 +2427,9 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
       }
       for (void* d : dead) h->pool.release(d);
     } else if (o.init == TT_INIT_ZIPUP) {  // Sec. 2.3.5: the zip-up contraction of A and B
-      if (h->use_f32) zipup_rl<float>(h, C0, cbond);
-      else zipup_rl<double>(h, C0, cbond);
+      const ZipArgs z = zip_of_fit(h);
+      if (h->use_f32) zipup_rl<float>(h, z, C0, cbond);
+      else zipup_rl<double>(h, z, C0, cbond);
       for (int l = 1; l < L; ++l) D.cb[l] = std::max(D.cb[l], cbond[l]);
     } else {
       std::vector<int> dz, bz;

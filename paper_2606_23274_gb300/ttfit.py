@@ -37,7 +37,8 @@ class tt_fit_options(ct.Structure):
                 ("seed", ct.c_uint64), ("precision", ct.c_int), ("init", ct.c_int),
                 ("init_C", ct.POINTER(tt_mpo_desc)), ("sv_cutoff", ct.c_double), ("conv_tol", ct.c_double),
                 ("stream", ct.c_void_p), ("prepare_inputs", ct.c_int), ("fault_inject", ct.c_uint32),
-                ("fast_factor", ct.c_int), ("n_segments", ct.c_int), ("edge_extra", ct.c_int)]
+                ("fast_factor", ct.c_int), ("n_segments", ct.c_int), ("edge_extra", ct.c_int),
+                ("ab_rank", ct.c_int)]
 
 
 class tt_sweep_report(ct.Structure):
@@ -159,7 +160,7 @@ def _check(code, h=None, what=""):
 
 def _options(update="svd", oversample=10, seed=0, precision="fp64", init="random", init_C=None, sv_cutoff=-1.0,
              conv_tol=-1.0, stream=None, prepare_inputs=True, fault_inject=0, fast_factor=False, n_segments=1,
-             edge_extra=0, device="cuda"):
+             edge_extra=0, ab_rank=0, device="cuda"):
     """tt_fit_options from keyword arguments; returns (options, keep-alive objects)."""
     import torch
     o = tt_fit_options()
@@ -183,6 +184,7 @@ def _options(update="svd", oversample=10, seed=0, precision="fp64", init="random
     o.fast_factor = int(fast_factor)
     o.n_segments = int(n_segments)
     o.edge_extra = int(edge_extra)
+    o.ab_rank = int(ab_rank)
     return o, dC
 
 
@@ -190,7 +192,7 @@ def tt_fit_create(A: Sequence, B: Sequence, chi_max: int, tol: float, gauge="sit
     """Create a fit handle (see tt_fit_create in include/ttfit.h). A, B: lists of
     (chi_l, d, d', chi_r) tensors (torch CUDA tensors, or host arrays that are copied).
     Keywords: update, oversample, seed, precision, init, init_C, sv_cutoff, conv_tol,
-    stream, prepare_inputs, fault_inject, fast_factor, n_segments, edge_extra."""
+    stream, prepare_inputs, fault_inject, fast_factor, n_segments, edge_extra, ab_rank."""
     lib = load()
     dA = _Desc(_as_device(A, device))
     dB = _Desc(_as_device(B, device))
