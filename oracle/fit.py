@@ -250,6 +250,7 @@ class FitOracle:
         U, Vt = fix_signs(U[:, :k], Vt[:k, :])
         S = S[:k]
         st.S[l] = S.copy()
+        self.last_factors = (U, S, Vt)
         if self.gauge == "site":
             if forward:                           # C_l, C_{l+1} <- U, S V^T
                 left, right = U, S[:, None] * Vt

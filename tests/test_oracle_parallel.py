@@ -56,3 +56,62 @@ def test_single_segment_equals_serial_inverse_fit():
     p.full_sweep_set()                                       # one set = forward + backward
     Cs, _ = fit(A, B, 8, 0.0, 2, gauge="inverse", init="given", init_C=C_init, stop_on_converge=False)
     assert mpo_diff_norm(p.result(), Cs) <= 1e-10 * mpo_norm(Cs)
+
+
+# --------------------------------------------------------------------------- site-canonical scheme + merge
+from oracle.parallel import SiteParallelFitOracle  # noqa: E402
+from paper_2606_23274_gb300.synth import gaussian_mpo, kron_sum_mpo  # noqa: E402
+
+
+@pytest.mark.parametrize("n_seg", [2, 3, 4])
+def test_site_parallel_fit_and_merge_reproduce_exact_product(n_seg):
+    # (a merge that moved the units' centres from the segment ends instead of from where the
+    # units keep them lost ~1e-2 of the weight at 3 and 4 segments: this pins where they are)
+    """chi_max above the rank of A B: after local sweeps and the merge the fit is A B."""
+    A, B = mpo_pair("gauss_L8_chi8", seed=3)
+    f = SiteParallelFitOracle(A, B, 64, 1e-12, n_seg)
+    for _ in range(2):
+        f.full_sweep_set()
+    f.merge()
+    D = to_dense(A) @ to_dense(B)
+    assert np.linalg.norm(to_dense(f.result()) - D) <= 1e-9 * np.linalg.norm(D)
+
+
+@pytest.mark.parametrize("n_seg", [2, 3, 4, 5])
+@pytest.mark.parametrize("half", [False, True])
+def test_site_merge_leaves_one_canonical_mpo(n_seg, half):
+    """After the merge every core left of its last window is left-orthonormal and every
+    core right of it right-orthonormal, so ||C||^2 is the kept weight of the last update;
+    before it, the units carry their own centres and the cores' product is not the
+    fitted operator. `half` ends the sweeps after an odd|even phase."""
+    A = gaussian_mpo(14, 2, 4, 5, 0)
+    B = gaussian_mpo(14, 2, 4, 5, 1)
+    f = SiteParallelFitOracle(A, B, 8, 0.0, n_seg, conv_tol=0.0)
+    f.full_sweep_set()
+    n2_set = f.half_set() if half else f.par_history[-1]
+    if n_seg > 2 or not half:
+        assert abs(mpo_norm(f.result()) ** 2 - n2_set) > 1e-6 * n2_set
+    n2 = f.merge()
+    C = f.result()
+    l = f.final_boundary
+    for j in range(1, l):
+        assert is_left_orthogonal(C[j - 1], 1e-10)
+    for j in range(l + 2, len(C) + 1):
+        assert is_right_orthogonal(C[j - 1], 1e-10)
+    assert abs(mpo_norm(C) ** 2 - n2) <= 1e-10 * n2
+
+
+@pytest.mark.parametrize("n_seg", [3, 4])
+def test_site_parallel_fit_reaches_the_serial_optimum(n_seg):
+    """Kronecker sums with distinct weight decays (a unique, quickly reached optimum):
+    eight sets plus the merge give the serial fit's ||C||^2 and operator."""
+    A = kron_sum_mpo(12, 5, 6, 0, decay=0.7)
+    B = kron_sum_mpo(12, 5, 6, 1, decay=0.5)
+    C_ser, ser = fit(A, B, 10, 0.0, 12, gauge="site", conv_tol=0.0, stop_on_converge=False)
+    f = SiteParallelFitOracle(A, B, 10, 0.0, n_seg, conv_tol=0.0)
+    for _ in range(8):
+        f.full_sweep_set()
+    n2 = f.merge()
+    C = f.result()
+    assert abs(n2 - ser.st.history[-1].norm2) <= 1e-10 * n2
+    assert mpo_diff_norm(C, C_ser) <= 1e-8 * mpo_norm(C_ser)
