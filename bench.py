@@ -411,23 +411,30 @@ def _timed(stream, fn):
     return e0.elapsed_time(e1) / 1e3, r
 
 
-def _segment_fit(ttfit, A, B, dev, stream, n_seg, edge_extra=0):
-    """The timed workload in the inverse gauge, serial (n_seg = 1) or segment-parallel
-    (Alg. 6): one cheap 3xTF32 pass (a full set of local sweeps when segmented), then
-    DF32 with the FP32 factorisation until delta <= TOL."""
+def _segment_fit(ttfit, A, B, dev, stream, n_seg, edge_extra=0, gauge="inverse"):
+    """The timed workload, serial (n_seg = 1) or segment-parallel (Alg. 6): one cheap 3xTF32
+    pass (a full set of local sweeps when segmented), then DF32 until delta <= TOL, with
+    the FP32 factorisation in the inverse gauge and the FP64 one in the site gauge (whose
+    segments are merged before the switch and at the end, Sec. 4.5)."""
+    site = gauge == "site" and n_seg > 1
+
     def run():
-        f = ttfit.tt_fit_create(A, B, CHI, TOL, "inverse", update="rsvd", oversample=OVERSAMPLE, seed=0,
+        f = ttfit.tt_fit_create(A, B, CHI, TOL, gauge, update="rsvd", oversample=OVERSAMPLE, seed=0,
                                 precision="tf32x3", device=dev, stream=stream, n_segments=n_seg,
                                 edge_extra=edge_extra)
         per_set = 2 if n_seg > 1 else 1
         f.sweep(per_set)
-        f.set_precision("df32", fast_factor=1)
+        if site:
+            f.merge()
+        f.set_precision("df32", fast_factor=0 if site else 1)
         n, rep = per_set, None
         while n < MAX_SWEEPS * per_set:
             rep = f.sweep(1)
             n += 1
             if rep["converged"]:
                 break
+        if site:
+            rep = f.merge()
         f.destroy()
         return rep, n
     run()  # warm-up
@@ -455,6 +462,13 @@ def extras(ttfit, dev, stream, norm2_site):
                            "delta": rep["delta"], "norm2_rel_to_site_fit": rep["norm2_C"] / norm2_site - 1.0,
                            "edge_extra": ee}
     out["segments_inverse_gauge_L30_chi128"] = seg
+    seg = {}
+    for n_seg, ee in ((2, 0), (4, 2), (8, 2)):
+        t, rep, n = _segment_fit(ttfit, A, B, dev, stream, n_seg, ee, gauge="site")
+        seg[str(n_seg)] = {"time_to_tol_s": round(t, 4), "phases": n, "converged": bool(rep["converged"]),
+                           "delta": rep["delta"], "norm2_rel_to_site_fit": rep["norm2_C"] / norm2_site - 1.0,
+                           "edge_extra": ee, "merges": 2}
+    out["segments_site_gauge_L30_chi128"] = seg
 
     # config 2: plain FP32 (FP32 CUDA-core contractions, FP32 SVD) vs mixed (3xTF32, then DF32 with the
     # FP64 SVD), both the exact two-site update; error = relative Frobenius distance to the converged FP64 fit

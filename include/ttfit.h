@@ -126,8 +126,8 @@ typedef struct {
                        /* that the converged C is FP64-class.                                  */
   int n_segments;      /* segment-parallel fit (Sec. 4, Alg. 6): number of contiguous       */
                        /* segments N_p, each >= 2 sites; <= 1 (default) = serial Alg. 5.    */
-                       /* N_p > 1 needs the inverse canonical gauge (the site gauge needs a  */
-                       /* merge, not built); see tt_fit_sweep for what a sweep is then.     */
+                       /* Either gauge: the inverse one (scheme I) or the site one (scheme */
+                       /* II, merged by tt_fit_merge); see tt_fit_sweep for what a sweep is. */
   int edge_extra;      /* sites moved from the inner segments to each edge segment (load   */
                        /* balance of Sec. 4.1: edge segments have one neighbour), default 0 */
   int ab_rank;         /* randomized bond projection of the A and B chains (Sec. 3.2): k > 0 */
@@ -183,15 +183,37 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
  * that of its last update (every Psi is an orthogonality centre in the
  * inverse gauge), and delta compares consecutive full sets, so convergence
  * is tested after every second phase. The sketch of a window in phase p of
- * set s uses sweep index 2 s + p. */
+ * set s uses sweep index 2 s + p.
+ * Site gauge (scheme II): the same phases with the site-gauge update (Alg.
+ * 3); segments are prepared (Sec. 4.2) with odd segments' orthogonality
+ * centres on their first site and even segments' on their last. Every segment
+ * then carries its own centre, so C is not exported until tt_fit_merge has
+ * joined the segments. */
 tt_status tt_fit_sweep(tt_fit* h, int n_sweeps, tt_sweep_report* rep);
+
+/* Binary merge of a site-gauge segment-parallel fit (Sec. 4.5). After the last
+ * phase the chain is a row of consistent units: the segments joined by that
+ * phase's boundary updates, and the segments without one. Neighbouring units
+ * are joined pairwise in rounds (O(log N_p) of them): the left unit's
+ * orthogonality centre moves to its last site l by QR steps and the right
+ * unit's to its first site l+1 by RQ steps, each step finishing the
+ * environment it passes (O(L) in all), then window (l, l+1) is updated forward
+ * with the sketches of phase index P + r - 1 in round r (P = phases run).
+ * The joins of a round run concurrently on their segments' streams. Afterwards
+ * C is one site-canonical MPO with its centre at the last window's right
+ * site, and tt_fit_result may export it; further sweeps continue the local
+ * phases from it. A no-op for any other handle or when already merged.
+ * rep (nullable): norm2_C = ||C||^2 after the merge, other fields as after
+ * the last sweep. Errors: TT_ERR_STATE (poisoned handle), and as tt_fit_sweep. */
+tt_status tt_fit_merge(tt_fit* h, tt_sweep_report* rep);
 
 /* Change the contraction precision for the following sweeps (the paper's
  * "cheap sweeps first, exact sweeps last", Sec. 5.3): the chain buffers are
  * rebuilt in the new arithmetic, and the environments the next sweep reads are
  * recomputed from the current C: R_L..R_3 before a forward sweep, L_1..L_{L-2}
  * before a backward one. A segment-parallel fit switches only between full sets
- * of local sweeps (else TT_ERR_STATE; the handle stays usable). fast_factor as
+ * of local sweeps (else TT_ERR_STATE; the handle stays usable), in the site
+ * gauge only once merged, after which the segments are prepared again. fast_factor as
  * in tt_fit_options; a default cut-off follows the new precision. Resets the
  * converged flag; delta keeps comparing consecutive sweeps. */
 tt_status tt_fit_set_precision(tt_fit* h, int precision, int fast_factor);
@@ -201,7 +223,8 @@ tt_status tt_fit_set_precision(tt_fit* h, int precision, int fast_factor);
  * (L+1 ints); then call again with cores pointing to caller device buffers of
  * the reported sizes in C->dtype. lambdas (nullable, host) receives, for each
  * inner bond l = 1..L-1 in order, the bond[l] singular values of the last
- * update of that bond. In the inverse gauge C_l = Psi_l Y_l (l < L). */
+ * update of that bond. In the inverse gauge C_l = Psi_l Y_l (l < L).
+ * TT_ERR_STATE for a site-gauge segment-parallel fit that is not merged. */
 tt_status tt_fit_result(const tt_fit* h, tt_mpo_desc* C, double* lambdas);
 
 /* Free every buffer of the handle (NULL is a no-op). */

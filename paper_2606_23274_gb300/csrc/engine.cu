@@ -10,6 +10,7 @@
 // diagrams, shared with the two-site tensor) and "finish" (third diagram).
 #include <cuda_runtime.h>
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -270,6 +271,11 @@ struct tt_fit {
   int escale = 0;         // the fit runs on 2^-ea A, 2^-eb B; C, its spectra and norm get 2^escale back
   bool use_oz = true;     // DF32 chains: contractions on the tensor cores by the digit split
   std::vector<void*> chain_bufs;  // buffers rebuilt when the chain precision changes
+  // site-gauge segment-parallel fit: whether the sub-TTs have been merged since the last phase,
+  // which phase ran last, and the orthogonality centre the merge left (-1: none)
+  bool merged = true;
+  int last_phase = 1;
+  int oc_site = -1;
 };
 
 namespace {
@@ -431,11 +437,12 @@ void rq_sweep(tt_fit* h, Prep& P, std::vector<double*>& X, std::vector<int>& bon
   }
 }
 
-// Left-to-right QR sweep (Alg. 5 left_orthogonalize), bonds trimmed.
+// Left-to-right QR sweep (Alg. 5 left_orthogonalize), bonds trimmed; QR steps at
+// sites j0 .. j1 - 1 only when j1 >= 0.
 void qr_sweep(tt_fit* h, Prep& P, std::vector<double*>& X, std::vector<int>& bond, const std::vector<int>& dA,
-              const std::vector<int>& dB) {
+              const std::vector<int>& dB, int j0 = 0, int j1 = -1) {
   const int L = (int)X.size();
-  for (int j = 0; j < L - 1; ++j) {
+  for (int j = j0; j < (j1 >= 0 ? j1 : L - 1); ++j) {
     const int bl = bond[j], br = bond[j + 1], dd = dA[j] * dB[j];
     const int q = bl * dd, p = br, r = std::min(q, p);
     CK(copy_map<double, double>(q, p, X[j], IdxMap::lin(p), IdxMap::lin(1), P.X, IdxMap::lin(1), IdxMap::lin(q), 1.0,
@@ -1008,7 +1015,7 @@ void ns_orthonormalize(tt_fit* h, const Fin* Xin, int rows, int k, double* X64) 
 }
 
 template <typename T, typename F>
-void polish_update(tt_fit* h, int mode, int m, int n, int k, int l) {
+void polish_update(tt_fit* h, int mode, int m, int n, int k, int l, bool both = false) {
   const T* Th = (const T*)W(h).Th;
   T* Ut = (T*)h->Ut[l];
   T* Vt = (T*)h->Vt[l + 1];
@@ -1019,7 +1026,7 @@ void polish_update(tt_fit* h, int mode, int m, int n, int k, int l) {
     // Ut (k x m row-major) = U^T : same memory order as U column-major
     copymap<double, T>(h, 1, m * k, W(h).pU, IdxMap::lin(0), IdxMap::lin(1), Ut, IdxMap::lin(0), IdxMap::lin(1));
   }
-  if (mode != 0) {  // right isometry V (n x k)
+  if (mode != 0 || both) {  // right isometry V (n x k)
     ns_orthonormalize<F>(h, (const F*)W(h).fVM, n, k, W(h).pV);
     copymap<double, T>(h, 1, n * k, W(h).pV, IdxMap::lin(0), IdxMap::lin(1), Vt, IdxMap::lin(0), IdxMap::lin(1));
   }
@@ -1099,16 +1106,21 @@ struct Sweeper {
   //   ENV_NONE    first window of a local sweep of Alg. 6: the stored boundary environment is used;
   //   ENV_CONNECT connection update of Alg. 6: both environments are finished first, both halves are
   //               fresh, and L_{l+1}, R_{l+1} across the new bond are finished afterwards.
-  enum { ENV_SERIAL = 0, ENV_NONE = 1, ENV_CONNECT = 2 };
+  //   ENV_MERGE   merge update of the site-gauge scheme: both environments are already finished,
+  //               both halves are fresh, and the environments across the new bond follow.
+  enum { ENV_SERIAL = 0, ENV_NONE = 1, ENV_CONNECT = 2, ENV_MERGE = 3 };
 
   // one window update; returns kept sum of s^2 and the discarded fraction
   void window(int l, bool fwd, int sweep, double& n2, double& disc, int env = ENV_SERIAL) {
     Dims& D = h->D;
     const int L = D.L;
     CK(cudaEventRecord(W(h).ev[0], W(h).st));
-    if (env == ENV_CONNECT) {
-      if (l >= 1) ch.finish_left(l - 1);
-      if (l + 2 <= L - 1) ch.finish_right(l + 2);
+    const bool boundary = env == ENV_CONNECT || env == ENV_MERGE;
+    if (boundary) {
+      if (env == ENV_CONNECT) {
+        if (l >= 1) ch.finish_left(l - 1);
+        if (l + 2 <= L - 1) ch.finish_right(l + 2);
+      }
       CK(cudaEventRecord(W(h).ev[1], W(h).st));
       ch.half_left(l);
       ch.half_right(l + 1);
@@ -1127,8 +1139,9 @@ struct Sweeper {
     CK(cudaEventRecord(W(h).ev[3], W(h).st));
     int p;
     if (h->fact_f32) {
-      // a forward step of the site gauge keeps only U (C_l = U, C_{l+1} = U^T Theta)
-      const bool left_only = h->gauge != TT_GAUGE_INVERSE_CANONICAL && fwd;
+      // a forward step of the site gauge keeps only U (C_l = U, C_{l+1} = U^T Theta); a boundary
+      // update also needs V, the basis of the right neighbour's environment
+      const bool left_only = h->gauge != TT_GAUGE_INVERSE_CANONICAL && fwd && !boundary;
       p = factorize<T, float>(h, m, n, sweep, l + 1, left_only ? 1 : 3);
       CK(truncate_rule<float>((const float*)W(h).fS, p, W(h).dnorm, h->tol / L, h->chi_max, h->cutoff, W(h).dk, W(h).ddinfo,
                               W(h).st));
@@ -1147,7 +1160,7 @@ struct Sweeper {
       // flag and factorise this window again with the all-FP32 randomized update
       CK(cudaMemsetAsync(W(h).errw, 0, sizeof(uint32_t), W(h).st));
       W(h).hp_off = true;
-      const bool left_only = h->gauge != TT_GAUGE_INVERSE_CANONICAL && fwd;
+      const bool left_only = h->gauge != TT_GAUGE_INVERSE_CANONICAL && fwd && !boundary;
       try {
         p = factorize<T, float>(h, m, n, sweep, l + 1, left_only ? 1 : 3);
       } catch (...) {
@@ -1193,12 +1206,15 @@ struct Sweeper {
       CK(gauge_update<T, FX>(mode, m, n, (const FX*)W(h).fUM, m, (const FX*)W(h).fS, (const FX*)W(h).fVM, n, W(h).dk, h->C64[l],
                             h->C64[l + 1], h->Y[l + 1], (T*)h->Ut[l], (T*)h->Vt[l + 1], W(h).st));
     } else {
-      if (W(h).hp) polish_update<T, df32>(h, mode, m, n, k, l);
-      else polish_update<T, float>(h, mode, m, n, k, l);
+      // a forward boundary update of the site gauge also returns V, the basis of the right
+      // neighbour's environment
+      const bool both = boundary && mode == 0;
+      if (W(h).hp) polish_update<T, df32>(h, mode, m, n, k, l, both);
+      else polish_update<T, float>(h, mode, m, n, k, l, both);
     }
     CK(cudaEventRecord(W(h).ev[6], W(h).st));
     W(h).gauge_pending = true;
-    if (env == ENV_CONNECT) {  // environments across the updated bond, for both neighbours
+    if (boundary) {  // environments across the updated bond, for both neighbours
       CK(cudaEventRecord(W(h).ev[8], W(h).st));
       ch.finish_left(l);
       ch.finish_right(l + 1);
@@ -1510,6 +1526,162 @@ void run_threads(tt_fit* h, int n, Fn fn) {
   if (first) std::rethrow_exception(first);
 }
 
+// ---------------------------------------------------------------------------
+// Site-canonical segment-parallel fit (Sec. 4, the paper's scheme II) and its
+// binary merge (Sec. 4.5).
+// ---------------------------------------------------------------------------
+
+// QR step of the site gauge at site j (0-based): C_j = Q (left-orthonormal),
+// C_{j+1} <- R C_{j+1}, then L_j from the new C_j. FP64 arithmetic on the FP64
+// cores, in the lane's factorisation scratch.
+template <typename T>
+void site_qr_step(tt_fit* h, int j) {
+  Dims& D = h->D;
+  Work& w = W(h);
+  const int q = D.c[j] * D.ds[j] * D.dt[j], p = D.c[j + 1], r = std::min(q, p);
+  const int rest = D.ds[j + 1] * D.dt[j + 1] * D.c[j + 2];
+  to_colmajor(h, q, p, h->C64[j], w.fX);
+  qr(h, q, p, w.fX, w.fQ, w.fR);
+  copymap<double, double>(h, q, r, w.fQ, IdxMap::lin(1), IdxMap::lin(q), h->C64[j], IdxMap::lin(r), IdxMap::lin(1));
+  copymap<double, T>(h, 1, q * r, w.fQ, IdxMap::lin(0), IdxMap::lin(1), (T*)h->Ut[j], IdxMap::lin(0), IdxMap::lin(1));
+  GemmArgs<double> g;  // C_{j+1} <- R C_{j+1} (r x rest)
+  g.M = r; g.N = rest; g.K = p;
+  g.A = w.fR; g.am = IdxMap::lin(1); g.ak = IdxMap::lin(r); g.a_kfast = false;
+  g.B = h->C64[j + 1]; g.bn = IdxMap::lin(1); g.bk = IdxMap::lin(rest); g.b_kfast = false;
+  g.C = w.fY; g.cm = IdxMap::lin(rest); g.cn = IdxMap::lin(1);
+  gemm<double>(h, g);
+  CK(cudaMemcpyAsync(h->C64[j + 1], w.fY, sizeof(double) * (size_t)r * rest, cudaMemcpyDeviceToDevice, w.st));
+  D.c[j + 1] = r;
+  Chain<T> ch(h);
+  ch.half_left(j);
+  ch.finish_left(j);
+}
+
+// RQ step at site j: C_j = Q^T (right-orthonormal), C_{j-1} <- C_{j-1} R^T, then
+// R_j from the new C_j.
+template <typename T>
+void site_rq_step(tt_fit* h, int j) {
+  Dims& D = h->D;
+  Work& w = W(h);
+  const int q = D.ds[j] * D.dt[j] * D.c[j + 1], p = D.c[j], r = std::min(q, p);
+  const int rows = D.c[j - 1] * D.ds[j - 1] * D.dt[j - 1];
+  // C_j row-major (p x q) is C_j^T column-major (q x p)
+  CK(cudaMemcpyAsync(w.fX, h->C64[j], sizeof(double) * (size_t)q * p, cudaMemcpyDeviceToDevice, w.st));
+  qr(h, q, p, w.fX, w.fQ, w.fR);
+  // C_j = Q^T (r x q row-major) = Q column-major; the right operand is the same
+  CK(cudaMemcpyAsync(h->C64[j], w.fQ, sizeof(double) * (size_t)q * r, cudaMemcpyDeviceToDevice, w.st));
+  copymap<double, T>(h, 1, q * r, w.fQ, IdxMap::lin(0), IdxMap::lin(1), (T*)h->Vt[j], IdxMap::lin(0), IdxMap::lin(1));
+  GemmArgs<double> g;  // C_{j-1} <- C_{j-1} R^T (rows x r)
+  g.M = rows; g.N = r; g.K = p;
+  g.A = h->C64[j - 1]; g.am = IdxMap::lin(p); g.ak = IdxMap::lin(1);
+  g.B = w.fR; g.bn = IdxMap::lin(1); g.bk = IdxMap::lin(r); g.b_kfast = false;
+  g.C = w.fY; g.cm = IdxMap::lin(r); g.cn = IdxMap::lin(1);
+  gemm<double>(h, g);
+  CK(cudaMemcpyAsync(h->C64[j - 1], w.fY, sizeof(double) * (size_t)rows * r, cudaMemcpyDeviceToDevice, w.st));
+  D.c[j] = r;
+  Chain<T> ch(h);
+  ch.half_right(j);
+  ch.finish_right(j);
+}
+
+// The consistent sub-TTs after the last phase, as (first site, last site, centre):
+// segments joined by that phase's connection updates form one unit each, with
+// the centre on the right site of the connection; any other segment is a unit
+// with its centre where its local sweep left it.
+std::vector<std::array<int, 3>> site_units(const tt_fit* h) {
+  const auto& segs = h->segs;
+  const int ns = (int)segs.size();
+  const int start = h->last_phase == 0 ? 0 : 1;  // first connected boundary (0-based segment)
+  std::vector<std::array<int, 3>> units;
+  for (int i = 0; i < ns;) {
+    if (i >= start && (i - start) % 2 == 0 && i + 1 < ns) {
+      units.push_back({segs[i].first, segs[i + 1].second, segs[i + 1].first});
+      i += 2;
+    } else {
+      const bool forward = ((i % 2) == 0) == (h->last_phase == 0);
+      units.push_back({segs[i].first, segs[i].second, forward ? segs[i].second : segs[i].first});
+      i += 1;
+    }
+  }
+  return units;
+}
+
+// Binary merge (Sec. 4.5): neighbouring units are joined pairwise, in rounds;
+// the left unit's centre moves to its last site l by QR steps and the right
+// unit's to its first site l + 1 by RQ steps, each step finishing the
+// environment it passes; then window (l, l+1) is updated forward with both
+// environments, drawing the sketches of phase index phases_done + r - 1 in
+// round r. The joins of a round touch disjoint sites and run concurrently, each
+// on the lane of its left unit's first segment. Returns ||C||^2 of the last
+// update (kept sum of s^2, or the FP64-polished projection's).
+template <typename T>
+double site_merge(tt_fit* h) {
+  auto units = site_units(h);
+  double n2 = h->cur_n2;
+  int lw = -1;
+  auto lane_of = [&](int site) {
+    for (size_t i = 0; i < h->segs.size(); ++i)
+      if (site >= h->segs[i].first && site <= h->segs[i].second) return (int)i;
+    return 0;
+  };
+  CK(cudaEventRecord(h->w0.ev[7], h->w0.st));
+  for (auto& w : h->wseg) CK(cudaStreamWaitEvent(w->st, h->w0.ev[7], 0));
+  for (int r = 1; units.size() > 1; ++r) {
+    const int pairs = (int)units.size() / 2;
+    std::vector<double> pn2(pairs, 0.0);
+    run_threads(h, pairs, [&](int u) {
+      const auto a = units[2 * u], b = units[2 * u + 1];
+      tl_work = h->wseg[lane_of(a[0])].get();
+      const int l = a[1];
+      for (int j = a[2]; j < l; ++j) site_qr_step<T>(h, j);
+      for (int j = b[2]; j > l + 1; --j) site_rq_step<T>(h, j);
+      Sweeper<T> sw(h);
+      double disc = 0;
+      sw.window(l, true, h->phases_done + r - 1, pn2[u], disc, Sweeper<T>::ENV_MERGE);
+      CK(cudaStreamSynchronize(W(h).st));
+      sw.resolve_gauge();
+    });
+    std::vector<std::array<int, 3>> next;
+    for (int u = 0; u < pairs; ++u) {
+      next.push_back({units[2 * u][0], units[2 * u + 1][1], units[2 * u][1] + 1});
+      n2 = pn2[u];
+      lw = units[2 * u][1];
+    }
+    if (units.size() % 2) next.push_back(units.back());
+    units = next;
+  }
+  for (auto& w : h->wseg) {
+    CK(cudaEventRecord(w->ev[7], w->st));
+    CK(cudaStreamWaitEvent(h->w0.st, w->ev[7], 0));
+  }
+  if (lw >= 0 && h->fact_f32) {
+    double nr = 0;
+    CK(cudaMemcpyAsync(&nr, h->dn2 + lw, sizeof(double), cudaMemcpyDeviceToHost, h->w0.st));
+    CK(cudaStreamSynchronize(h->w0.st));
+    n2 = nr * nr;
+  }
+  h->oc_site = units[0][2];
+  h->merged = true;
+  return n2;
+}
+
+// Initialisation of the site-gauge scheme (Sec. 4.2): C right-canonical with
+// its centre at site 1 (RQ steps from the right end), which leaves every odd
+// segment's centre on its first site; every even segment (1-based) then moves
+// its centre to its last site by QR steps; every environment follows from
+// these cores. A merged fit is re-partitioned the same way.
+template <typename T>
+void site_segment_init(tt_fit* h) {
+  const int L = h->D.L;
+  for (int j = L - 1; j >= 1; --j) site_rq_step<T>(h, j);
+  for (size_t i = 1; i < h->segs.size(); i += 2)
+    for (int j = h->segs[i].first; j < h->segs[i].second; ++j) site_qr_step<T>(h, j);
+  CK(cudaStreamSynchronize(W(h).st));
+  h->merged = true;
+  h->last_phase = 1;
+  h->oc_site = -1;
+}
+
 // Initial guess -> inverse canonical (Vidal) form by a left-to-right SVD sweep
 // of the right-canonical guess (Sec. 4.2): core j = U S s.t. it is split as
 // Psi_j = U S, Y_{j+1} = 1/S, and S V^T is carried into core j+1. Values
@@ -1742,6 +1914,7 @@ struct ZipArgs {
   int chi_max = 1, oversample = 0;
   double tol = 0.0, cutoff = 0.0;
   bool rsvd = false;
+  bool project = false;  // range finder only: keep the sketch's range (or M's whole row range), no SVD
   uint64_t stream_base = 3ull << 40;
 };
 
@@ -1821,7 +1994,10 @@ void zipup_rl(tt_fit* h, const ZipArgs& z, std::vector<double*>& C, std::vector<
       sz_nk = std::max<size_t>(sz_nk, n * ks);
       sz_z = std::max<size_t>(sz_z, m * ks);
     }
-    if (!rs && m < n) {
+    if (z.project && !rs) {  // QR of M^T: its copy and the R factor
+      sz_zc = std::max<size_t>(sz_zc, m * n);
+      sz_u = std::max<size_t>(sz_u, m * n);
+    } else if (!rs && m < n) {
       sz_zc = std::max<size_t>(sz_zc, m * n);
       sz_u = std::max<size_t>(sz_u, m * n);
       sz_pp = std::max<size_t>(sz_pp, m * m);
@@ -1947,6 +2123,39 @@ void zipup_rl(tt_fit* h, const ZipArgs& z, std::vector<double*>& C, std::vector<
       zgemm<T>(h, z, ws, wse, tc);
       Zp = Z;
     }
+    // C_l = V^T (k x (s t c)): V column-major is V^T row-major; R_l[a0, k, b0] = (M V)[(a0 b0), k]
+    auto emit = [&](int k) {
+      cb[l] = k;
+      C[l] = h->pool.alloc<double>((size_t)k * n);
+      copymap<T, double>(h, 1, (int)(k * n), Vn, IdxMap::lin(0), IdxMap::lin(1), C[l], IdxMap::lin(0),
+                         IdxMap::lin(1));
+      GemmArgs<T> g;
+      g.M = (int)m;
+      g.N = k;
+      g.K = (int)n;
+      g.A = Mr;
+      g.am = IdxMap::lin(n);
+      g.ak = IdxMap::lin(1);
+      g.B = Vn;
+      g.bn = IdxMap::lin(n);
+      g.bk = IdxMap::lin(1);
+      g.C = Rn;
+      g.cm = IdxMap::two(b0, (long long)k * b0, 1);
+      g.cn = IdxMap::lin(b0);
+      zgemm<T>(h, g, ws, wse, tc);
+      std::swap(Rc, Rn);
+    };
+    if (z.project) {  // range finder only (Sec. 3): V = Q, or M's whole row range where k_s >= min(m, n)
+      if (rs) {
+        CK(cudaMemcpyAsync(Vn, Q, sizeof(T) * n * ks, cudaMemcpyDeviceToDevice, st));
+        emit(ks);
+      } else {
+        CK(cudaMemcpyAsync(Zc, Mr, sizeof(T) * m * n, cudaMemcpyDeviceToDevice, st));  // M^T, column-major
+        CK(qr_householder<T, T>((int)n, (int)m, Zc, Vn, Ux, st));
+        emit((int)std::min(m, n));
+      }
+      continue;
+    }
     int pv = p;        // singular values in Sv, V = Vn (n x pv column-major)
     T* W_ = nullptr;   // V = Q W when randomized
     if (!rs && m < n) {  // M^T (n x m, column-major = M row-major) is the tall side: M^T = Ux S Vx^T
@@ -2001,26 +2210,11 @@ void zipup_rl(tt_fit* h, const ZipArgs& z, std::vector<double*>& C, std::vector<
     check_errw(h, ("zip-up site " + std::to_string(l + 1)).c_str());
     const int k = *w.hk;
     if (k < 1 || k > pv) throw TTError(TT_ERR_NUMERICAL, "zip-up: invalid kept rank");
-    cb[l] = k;
-    C[l] = h->pool.alloc<double>((size_t)k * n);  // C_l = V^T (k x (s t c)): V column-major is V^T row-major
-    copymap<T, double>(h, 1, (int)(k * n), Vn, IdxMap::lin(0), IdxMap::lin(1), C[l], IdxMap::lin(0), IdxMap::lin(1));
-    GemmArgs<T> g;  // R_l[a0, k, b0] = (M V)[(a0 b0), k]
-    g.M = (int)m;
-    g.N = k;
-    g.K = (int)n;
-    g.A = Mr;
-    g.am = IdxMap::lin(n);
-    g.ak = IdxMap::lin(1);
-    g.B = Vn;
-    g.bn = IdxMap::lin(n);
-    g.bk = IdxMap::lin(1);
-    g.C = Rn;
-    g.cm = IdxMap::two(b0, (long long)k * b0, 1);
-    g.cn = IdxMap::lin(b0);
-    zgemm<T>(h, g, ws, wse, tc);
-    std::swap(Rc, Rn);
+    emit(k);
   }
+  CK(cudaMemcpyAsync(w.herrw, w.errw, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  check_errw(h, "the zip-up");
   for (void* b : bufs) h->pool.release(b);
 }
 
@@ -2052,6 +2246,7 @@ void project_ab(tt_fit* h, int k, long long mc) {
     z.tol = 0.0;
     z.cutoff = 0.0;
     z.rsvd = true;
+    z.project = true;
     z.stream_base = (uint64_t)(4 + which) << 40;
     std::vector<double*> P;
     std::vector<int> pb;
@@ -2313,7 +2508,6 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
     if (o.precision < 0 || o.precision > 5 || o.oversample < 0) return TT_ERR_INVALID_ARGUMENT;
     if (o.init < 0 || o.init > 3 || (o.init == TT_INIT_GIVEN && !o.init_C)) return TT_ERR_INVALID_ARGUMENT;
     if (o.precision == TT_PREC_BF16_SPLIT) return TT_ERR_INVALID_ARGUMENT;  // reserved, not implemented
-    if (o.n_segments > 1 && gauge != TT_GAUGE_INVERSE_CANONICAL) return TT_ERR_INVALID_ARGUMENT;
     if (o.edge_extra < 0) return TT_ERR_INVALID_ARGUMENT;
     if (o.fast_factor < 0 || o.fast_factor > 3) return TT_ERR_INVALID_ARGUMENT;
     if (o.ab_rank < 0 || (o.ab_rank > 0 && !o.prepare_inputs)) return TT_ERR_INVALID_ARGUMENT;
@@ -2464,7 +2658,18 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
     }
     D.c = cbond;
     setup(h, C0);
-    if (h->segs.size() > 1) {  // inverse canonical form and every environment (Sec. 4.2)
+    if (h->segs.size() > 1 && gauge == TT_GAUGE_SITE_CANONICAL) {  // scheme II (Sec. 4.2)
+      if (h->use_f32) {
+        site_segment_init<float>(h);
+        all_envs<float>(h);
+      } else if (h->use_df) {
+        site_segment_init<df32>(h);
+        all_envs<df32>(h);
+      } else {
+        site_segment_init<double>(h);
+        all_envs<double>(h);
+      }
+    } else if (h->segs.size() > 1) {  // inverse canonical form and every environment (Sec. 4.2)
       if (h->use_f32) {
         vidal_init<float, float>(h);
         all_envs<float>(h);
@@ -2536,6 +2741,11 @@ tt_status tt_fit_sweep(tt_fit* h, int n_sweeps, tt_sweep_report* rep) {
         h->phases_done++;
         h->sweeps_done++;
         h->cur_n2 = n2;
+        if (h->gauge == TT_GAUGE_SITE_CANONICAL) {  // the units carry their own centres until merged
+          h->merged = false;
+          h->last_phase = ph;
+          h->oc_site = -1;
+        }
         h->max_disc = maxd;
         if (ph == 1) {  // a full set of local sweeps is complete
           h->delta = (h->last_n2 >= 0 && n2 > 0) ? std::fabs(n2 - h->last_n2) / n2 : INFINITY;
@@ -2575,11 +2785,42 @@ tt_status tt_fit_sweep(tt_fit* h, int n_sweeps, tt_sweep_report* rep) {
   return TT_OK;
 }
 
+tt_status tt_fit_merge(tt_fit* h, tt_sweep_report* rep) {
+  if (!h) return TT_ERR_INVALID_ARGUMENT;
+  if (h->poisoned) return TT_ERR_STATE;
+  auto t0 = std::chrono::steady_clock::now();
+  LaunchTally tally(h);
+  try {
+    if (!h->merged) {
+      h->cur_n2 = h->use_f32  ? site_merge<float>(h)
+                  : h->use_df ? site_merge<df32>(h)
+                              : site_merge<double>(h);
+      CK(cudaStreamSynchronize(h->w0.st));
+    }
+  } catch (const TTError& e) {
+    poison(h, e);
+    return e.code;
+  }
+  if (rep) {
+    rep->sweeps_done = h->sweeps_done;
+    rep->converged = h->converged ? 1 : 0;
+    rep->delta = h->delta;
+    rep->norm2_C = std::ldexp(h->segs.size() > 1 ? h->cur_n2 : h->last_n2, 2 * h->escale);
+    rep->max_discarded = h->max_disc;
+    rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return TT_OK;
+}
+
 tt_status tt_fit_result(const tt_fit* hc, tt_mpo_desc* C, double* lambdas) {
   tt_fit* h = const_cast<tt_fit*>(hc);
   if (!h || !C) return TT_ERR_INVALID_ARGUMENT;
   LaunchTally tally(h);
   if (h->poisoned) return TT_ERR_STATE;
+  if (!h->merged) {
+    h->last_error = "tt_fit_result: the site-gauge segments are not merged (tt_fit_merge)";
+    return TT_ERR_STATE;
+  }
   const Dims& D = h->D;
   const int L = D.L;
   C->L = L;
@@ -2611,7 +2852,8 @@ tt_status tt_fit_result(const tt_fit* hc, tt_mpo_desc* C, double* lambdas) {
       const bool scale = (h->gauge == TT_GAUGE_INVERSE_CANONICAL) && (l < L - 1);
       // the input scale goes back into the orthogonality centre, so that the other cores keep
       // their canonical form: in the site gauge the last core after a forward sweep, else the first
-      const int oc = (h->gauge != TT_GAUGE_INVERSE_CANONICAL && !h->forward) ? L - 1 : 0;
+      const int oc = h->oc_site >= 0 ? h->oc_site
+                     : (h->gauge != TT_GAUGE_INVERSE_CANONICAL && !h->forward && h->segs.size() <= 1) ? L - 1 : 0;
       const double f = l == oc ? sc : 1.0;
       if (C->dtype == TT_DTYPE_F64 && f == 1.0) {
         CK(scale_cols(rows, cols, h->C64[l], scale ? h->Y[l + 1] : nullptr, (double*)C->cores[l], W(h).st));
@@ -2644,6 +2886,10 @@ tt_status tt_fit_set_precision(tt_fit* h, int precision, int fast_factor) {
     h->last_error = "tt_fit_set_precision: a segment-parallel fit switches between full sets of local sweeps";
     return TT_ERR_STATE;
   }
+  if (h->segs.size() > 1 && h->gauge == TT_GAUGE_SITE_CANONICAL && !h->merged) {
+    h->last_error = "tt_fit_set_precision: merge the site-gauge segments first (tt_fit_merge)";
+    return TT_ERR_STATE;
+  }
   LaunchTally tally(h);
   try {
     const bool f32 = precision != TT_PREC_FP64 && precision != TT_PREC_DF32;
@@ -2657,7 +2903,12 @@ tt_status tt_fit_set_precision(tt_fit* h, int precision, int fast_factor) {
     if (f32) rebuild_chain<float>(h);
     else if (h->use_df) rebuild_chain<df32>(h);
     else rebuild_chain<double>(h);
-    if (h->segs.size() > 1) {  // the parallel fit needs every environment and half
+    if (h->segs.size() > 1 && h->gauge == TT_GAUGE_SITE_CANONICAL) {
+      // merged C, back to the scheme's initial gauge, every environment in the new type
+      if (f32) site_segment_init<float>(h), all_envs<float>(h);
+      else if (h->use_df) site_segment_init<df32>(h), all_envs<df32>(h);
+      else site_segment_init<double>(h), all_envs<double>(h);
+    } else if (h->segs.size() > 1) {  // the parallel fit needs every environment and half
       if (f32) all_envs<float>(h);
       else if (h->use_df) all_envs<df32>(h);
       else all_envs<double>(h);

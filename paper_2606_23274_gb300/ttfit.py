@@ -66,6 +66,8 @@ def load():
                                       ct.c_int, ct.POINTER(tt_fit_options), ct.POINTER(ct.c_void_p)]
         lib.tt_fit_create.restype = ct.c_int
         lib.tt_fit_sweep.argtypes = [ct.c_void_p, ct.c_int, ct.POINTER(tt_sweep_report)]
+        lib.tt_fit_merge.argtypes = [ct.c_void_p, ct.POINTER(tt_sweep_report)]
+        lib.tt_fit_merge.restype = ct.c_int
         lib.tt_fit_sweep.restype = ct.c_int
         lib.tt_fit_result.argtypes = [ct.c_void_p, ct.POINTER(tt_mpo_desc), ct.POINTER(ct.c_double)]
         lib.tt_fit_result.restype = ct.c_int
@@ -412,6 +414,12 @@ class Fit:
     def sweep(self, n_sweeps: int = 1) -> dict:
         rep = tt_sweep_report()
         _check(load().tt_fit_sweep(self.h, int(n_sweeps), ct.byref(rep)), self.h, "tt_fit_sweep")
+        return {k: getattr(rep, k) for k, _ in tt_sweep_report._fields_}
+
+    def merge(self) -> dict:
+        """tt_fit_merge: joins the segments of a site-gauge segment-parallel fit."""
+        rep = tt_sweep_report()
+        _check(load().tt_fit_merge(self.h, ct.byref(rep)), self.h, "tt_fit_merge")
         return {k: getattr(rep, k) for k, _ in tt_sweep_report._fields_}
 
     def bonds(self) -> list[int]:

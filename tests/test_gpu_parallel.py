@@ -128,9 +128,6 @@ def test_parallel_precision_switch():
 def test_parallel_rejects_bad_options():
     A, B = mpo_pair("kron_L10_chi16", 0)
     with pytest.raises(ttfit.TTError) as e:
-        ttfit.tt_fit_create(A, B, 8, 0.0, "site", n_segments=2)    # the site gauge needs a merge
-    assert e.value.code == ttfit.TT_ERR_INVALID_ARGUMENT
-    with pytest.raises(ttfit.TTError) as e:
         ttfit.tt_fit_create(A, B, 8, 0.0, "inverse", n_segments=6)  # 10 sites < 2 x 6
     assert e.value.code == ttfit.TT_ERR_INVALID_ARGUMENT
 
