@@ -74,6 +74,11 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
   return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46) | (2ull << 61);
 }
+// the same with the 64-byte swizzle (layout type 4): K-major rows of 64 bytes, 8-row groups SBO apart
+__device__ __forceinline__ uint64_t sdesc64(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46) | (4ull << 61);
+}
 __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
@@ -324,7 +329,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
 }
 
 bool make_map(CUtensorMap* map, const float* ptr, uint64_t inner, uint64_t outer, uint64_t row_stride_elems,
-              uint32_t box_inner, uint32_t box_outer) {
+              uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
   auto enc = encoder();
   if (!enc) return false;
   cuuint64_t dims[2] = {inner, outer};
@@ -332,7 +337,7 @@ bool make_map(CUtensorMap* map, const float* ptr, uint64_t inner, uint64_t outer
   cuuint32_t box[2] = {box_inner, box_outer};
   cuuint32_t es[2] = {1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)ptr, dims, strides, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -363,7 +368,12 @@ inline bool lin_stride(const IdxMap& m, long long& s) {
 constexpr int OZ_S = 6;
 constexpr int OZ_KC = 512;
 constexpr int OZ_TILES = 2 * OZ_S;
-constexpr int OZ_SMEM = OZ_TILES * TILE_BYTES + 1024 + 256;
+// k-blocks of 16 FP32 digits (64 bytes: the 64-byte swizzle span), so that two stages of the 12
+// digit tiles (2 x 96 KB) fit in shared memory and the TMA of one k-block overlaps the MMAs of the other
+constexpr int OZ_BK = 16;
+constexpr int OZ_TILE = BM * OZ_BK * 4;  // 8 KB
+constexpr int OZ_STAGES = 2;
+constexpr int OZ_SMEM = OZ_STAGES * OZ_TILES * OZ_TILE + 1024 + 256;
 constexpr int OZ_EZERO = -1000;  // exponent of an all-zero chunk
 
 // digits of one operand: X [R][K] (row stride ld, K contiguous) -> sl [OZ_S][R][Kp], ex [R][nch]
@@ -422,25 +432,26 @@ __device__ __forceinline__ void oz_mma(uint32_t tmem, uint64_t ad, uint64_t bd, 
 
 // One 128 x 128 output tile of one K-chunk (blockIdx.z) into the double-FP32
 // partial ws[z][M][N]. Warp 0: TMA producer; warp 1: tensor-memory owner and
-// MMA issuer; all four warps: epilogue. One stage holds the 2 OZ_S digit tiles
-// of a k-block (192 KB); the four accumulators fill the 512 tensor-memory columns.
+// MMA issuer; all four warps: epilogue. A stage holds the 2 OZ_S digit tiles of
+// a 16-wide k-block (96 KB); two stages alternate, so the loads of one k-block
+// run under the 42 MMAs of the other. The four accumulators fill the 512
+// tensor-memory columns.
 __global__ void __launch_bounds__(128, 1)
     gemm_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
                    int K, const int* __restrict__ eA, const int* __restrict__ eB, int nch, df32* __restrict__ ws,
                    uint32_t* errw) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = (uint64_t*)(smem + OZ_TILES * TILE_BYTES);  // [0] full, [1] empty, [2] accumulators ready
-  uint32_t* tmem_slot = (uint32_t*)(bars + 3);
+  // [0, 1] full, [2, 3] empty (per stage), [4] accumulators ready
+  uint64_t* bars = (uint64_t*)(smem + OZ_STAGES * OZ_TILES * OZ_TILE);
+  uint32_t* tmem_slot = (uint32_t*)(bars + 5);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN, z = blockIdx.z;
   const int kb0 = z * OZ_KC, kend = min(K, kb0 + OZ_KC);
-  const int nk = (kend - kb0 + BK - 1) / BK;
+  const int nk = (kend - kb0 + OZ_BK - 1) / OZ_BK;
   if (threadIdx.x == 0) {
-    mbar_init(su32(&bars[0]), 1);
-    mbar_init(su32(&bars[1]), 1);
-    mbar_init(su32(&bars[2]), 1);
+    for (int b = 0; b < 5; ++b) mbar_init(su32(&bars[b]), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
@@ -458,17 +469,19 @@ __global__ void __launch_bounds__(128, 1)
   int issued = 0;
   if (warp == 0 && lane == 0) {
     for (int kb = 0; kb < nk; ++kb) {
-      if (*abort_flag || !mbar_wait(su32(&bars[1]), (kb & 1) ^ 1)) {
+      const int st = kb & 1;
+      if (*abort_flag || !mbar_wait(su32(&bars[2 + st]), ((kb >> 1) & 1) ^ 1)) {
         *abort_flag = 1;
         break;
       }
-      const uint32_t full = su32(&bars[0]);
-      mbar_expect_tx(full, OZ_TILES * TILE_BYTES);
-      const int k = kb0 + kb * BK;
+      const uint32_t full = su32(&bars[st]);
+      mbar_expect_tx(full, OZ_TILES * OZ_TILE);
+      const int k = kb0 + kb * OZ_BK;
+      uint8_t* base = smem + st * OZ_TILES * OZ_TILE;
 #pragma unroll
       for (int i = 0; i < OZ_S; ++i) {
-        tma_load_2d(su32(smem + i * TILE_BYTES), &tmA, full, k, i * M + m0);
-        tma_load_2d(su32(smem + (OZ_S + i) * TILE_BYTES), &tmB, full, k, i * N + n0);
+        tma_load_2d(su32(base + i * OZ_TILE), &tmA, full, k, i * M + m0);
+        tma_load_2d(su32(base + (OZ_S + i) * OZ_TILE), &tmB, full, k, i * N + n0);
       }
       issued = kb + 1;
     }
@@ -477,32 +490,34 @@ __global__ void __launch_bounds__(128, 1)
     bool started[4] = {false, false, false, false};
     bool ok = true;
     for (int kb = 0; kb < nk; ++kb) {
-      if (*abort_flag || !mbar_wait(su32(&bars[0]), kb & 1)) {
+      const int st = kb & 1;
+      if (*abort_flag || !mbar_wait(su32(&bars[st]), (kb >> 1) & 1)) {
         *abort_flag = 1;
         ok = false;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint8_t* base = smem + st * OZ_TILES * OZ_TILE;
 #pragma unroll
       for (int i = 0; i < OZ_S; ++i)
 #pragma unroll
         for (int j = 0; j + i < OZ_S; ++j) {
           const int lev = min(i + j, 3);
-          const uint32_t a_base = su32(smem + i * TILE_BYTES), b_base = su32(smem + (OZ_S + j) * TILE_BYTES);
+          const uint32_t a_base = su32(base + i * OZ_TILE), b_base = su32(base + (OZ_S + j) * OZ_TILE);
 #pragma unroll
-          for (int kk = 0; kk < BK / 8; ++kk) {
-            oz_mma(tmem + lev * BN, sdesc(a_base + kk * 32, 16, 1024), sdesc(b_base + kk * 32, 16, 1024), idesc,
+          for (int kk = 0; kk < OZ_BK / 8; ++kk) {
+            oz_mma(tmem + lev * BN, sdesc64(a_base + kk * 32, 16, 512), sdesc64(b_base + kk * 32, 16, 512), idesc,
                    started[lev]);
             started[lev] = true;
           }
         }
-      mma_commit(su32(&bars[1]));  // frees the stage once these MMAs have read it
+      mma_commit(su32(&bars[2 + st]));  // frees the stage once these MMAs have read it
     }
-    if (ok) mma_commit(su32(&bars[2]));
+    if (ok) mma_commit(su32(&bars[4]));
   }
   __syncwarp();
   bool have = false;
-  if (nk > 0) have = mbar_wait(su32(&bars[2]), 0) && !*abort_flag;
+  if (nk > 0) have = mbar_wait(su32(&bars[4]), 0) && !*abort_flag;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const int m = m0 + warp * 32 + lane;
   df32* wrow = ws + ((size_t)z * M + (m < M ? m : 0)) * N;
@@ -536,8 +551,8 @@ __global__ void __launch_bounds__(128, 1)
   }
   if (nk == 0 && m < M)
     for (int n = n0; n < min(N, n0 + BN); ++n) wrow[n] = df32(0.f, 0.f);
-  if (warp == 0 && lane == 0 && *abort_flag)
-    for (int kb = 0; kb < issued; ++kb) mbar_wait(su32(&bars[0]), kb & 1);
+  if (warp == 0 && lane == 0 && *abort_flag)  // drain the loads still in flight (bounded waits)
+    for (int kb = 0; kb < issued; ++kb) mbar_wait(su32(&bars[kb & 1]), (kb >> 1) & 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1) {
@@ -625,8 +640,10 @@ cudaError_t gemm_oz(const GemmArgs<df32>& g, float* sA, float* sB, size_t slice_
   if (e != cudaSuccess) return e;
   if ((e = slice(g.N, g.B, ldb, sB, eB)) != cudaSuccess) return e;
   CUtensorMap ta, tb;
-  if (!make_map(&ta, sA, (uint64_t)Kp, (uint64_t)OZ_S * g.M, (uint64_t)Kp, BK, BM)) return cudaErrorNotSupported;
-  if (!make_map(&tb, sB, (uint64_t)Kp, (uint64_t)OZ_S * g.N, (uint64_t)Kp, BK, BN)) return cudaErrorNotSupported;
+  if (!make_map(&ta, sA, (uint64_t)Kp, (uint64_t)OZ_S * g.M, (uint64_t)Kp, OZ_BK, BM, CU_TENSOR_MAP_SWIZZLE_64B))
+    return cudaErrorNotSupported;
+  if (!make_map(&tb, sB, (uint64_t)Kp, (uint64_t)OZ_S * g.N, (uint64_t)Kp, OZ_BK, BN, CU_TENSOR_MAP_SWIZZLE_64B))
+    return cudaErrorNotSupported;
   if ((e = ensure_smem((const void*)gemm_oz_kernel, OZ_SMEM)) != cudaSuccess)
     return e;
   dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, nch);
