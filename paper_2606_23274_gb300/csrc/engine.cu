@@ -2576,8 +2576,6 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
       if (g->L == LA && g->bond && g->d_out && g->d_in)
         for (int l = 0; l < LA; ++l) mc = std::max(mc, prodll({g->bond[l], g->d_out[l], g->d_in[l], g->bond[l + 1]}));
     }
-    if (o.prepare_inputs) prepare_ab(h, mc);  // Alg. 5: left_orthogonalize(A), left_orthogonalize(B)
-    if (o.ab_rank > 0) project_ab(h, o.ab_rank, mc);
     // capacity of C bonds: min(chi_max, prod of local dims to the left / right)
     const int L = LA;
     D.cb.assign(L + 1, 1);
@@ -2587,17 +2585,25 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
       for (int j = l; j < L; ++j) right *= (double)D.ds[j] * D.dt[j];
       D.cb[l] = (int)std::min<double>(chi_max, std::min(left, right));
     }
-    // initial guess (right-canonical, orthogonality centre at site 1)
+    // initial guess (right-canonical, orthogonality centre at site 1). The random one does not
+    // depend on A or B: it is drawn on its own pool of streams while A and B are prepared.
     std::vector<double*> C0(L);
     std::vector<int> cbond;
+    struct StreamPool {  // destroyed on every exit, after its work has finished
+      cudaStream_t s[8] = {};
+      ~StreamPool() {
+        for (auto& x : s)
+          if (x) cudaStreamSynchronize(x), cudaStreamDestroy(x);
+      }
+    } guess_streams;
+    const int NS = 8;
+    cudaStream_t* pool = guess_streams.s;
+    std::vector<void*> dead;
     if (o.init == TT_INIT_RANDOM) {
       cbond = D.cb;
       // core l >= 2: orthonormal-row factor of a Gaussian matrix; the cores are
-      // independent, so their QRs run concurrently on a pool of streams
-      const int NS = 8;
-      cudaStream_t pool[NS];
-      for (auto& x : pool) CK(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
-      std::vector<void*> dead;
+      // independent, so their QRs run concurrently on the pool
+      for (int i = 0; i < NS; ++i) CK(cudaStreamCreateWithFlags(&pool[i], cudaStreamNonBlocking));
       CK(cudaStreamSynchronize(W(h).st));
       for (int j = 0; j < L; ++j) {
         cudaStream_t sj = pool[j % NS];
@@ -2615,9 +2621,14 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
           C0[j] = Q;
         }
       }
-      for (auto& x : pool) {
-        CK(cudaStreamSynchronize(x));
-        cudaStreamDestroy(x);
+    }
+    if (o.prepare_inputs) prepare_ab(h, mc);  // Alg. 5: left_orthogonalize(A), left_orthogonalize(B)
+    if (o.ab_rank > 0) project_ab(h, o.ab_rank, mc);
+    if (o.init == TT_INIT_RANDOM) {
+      for (int i = 0; i < NS; ++i) {
+        CK(cudaStreamSynchronize(pool[i]));
+        cudaStreamDestroy(pool[i]);
+        pool[i] = nullptr;
       }
       for (void* d : dead) h->pool.release(d);
     } else if (o.init == TT_INIT_ZIPUP) {  // Sec. 2.3.5: the zip-up contraction of A and B
