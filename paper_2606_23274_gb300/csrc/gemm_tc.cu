@@ -259,29 +259,59 @@ __global__ void __launch_bounds__(128, 1)
     const long long crow = (m < M) ? cm(m) : 0;
     const long long crow2 = (m < M && C2) ? cm2(m) : 0;
     float* wrow = ws ? ws + (size_t)blockIdx.z * M * N + (size_t)m * N : nullptr;
+    // A lane holds one accumulator row. Outputs whose consecutive columns are adjacent in memory
+    // (the split-K partials, and C when its column map has unit inner stride) are written from a
+    // transposed copy in shared memory instead (the pipeline stages are idle by now), so that the
+    // lanes of a warp store 32 consecutive columns of one row: one 128-byte segment per store
+    float* tbuf = (float*)smem + warp * 32 * 33;
+    const bool c_cols = ws != nullptr || cn.s2 == 1;
+    const bool c2_cols = C2 && cn2.s2 == 1;
 #pragma unroll 1
     for (int c = 0; c < BN; c += 32) {
       uint32_t r[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c, r);
-      if (m < M) {
+      if (c_cols || c2_cols) {
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) tbuf[lane * 33 + j] = __uint_as_float(r[j]);
+        __syncwarp();
+        const int n = n0 + c + lane;
+        if (n < N) {
+          const long long ccol = ws ? 0 : cn(n), ccol2 = c2_cols ? cn2(n) : 0;
+#pragma unroll 4
+          for (int i = 0; i < 32; ++i) {
+            const int mi = m0 + warp * 32 + i;
+            if (mi >= M) break;
+            const float v = tbuf[i * 33 + lane];
+            if (ws) {
+              ws[((size_t)blockIdx.z * M + mi) * N + n] = v;
+              continue;
+            }
+            const float out = alpha * v;
+            if (c2_cols) C2[cm2(mi) + ccol2] = out;
+            if (c_cols) {
+              const long long o = cm(mi) + ccol;
+              C[o] = beta != 0.f ? out + beta * C[o] : out;
+            }
+          }
+        }
+      }
+      if (m < M && !ws && (!c_cols || (C2 && !c2_cols))) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int n = n0 + c + j;
           if (n < N) {
-            const float v = __uint_as_float(r[j]);
-            if (ws) {
-              wrow[n] = v;
-            } else {
+            const float out = alpha * __uint_as_float(r[j]);
+            if (C2 && !c2_cols) C2[crow2 + cn2(n)] = out;
+            if (!c_cols) {
               const long long o = crow + cn(n);
-              float out = alpha * v;
-              if (C2) C2[crow2 + cn2(n)] = out;
-              if (beta != 0.f) out += beta * C[o];
-              C[o] = out;
+              C[o] = beta != 0.f ? out + beta * C[o] : out;
             }
           }
         }
       }
     }
+    (void)wrow;
   } else if (nk > 0 && threadIdx.x == 0 && errw) {
     atomicOr(errw, ERRW_TIMEOUT);
   }
@@ -523,6 +553,9 @@ __global__ void __launch_bounds__(128, 1)
   df32* wrow = ws + ((size_t)z * M + (m < M ? m : 0)) * N;
   const int ea = (m < M) ? eA[(size_t)m * nch + z] : OZ_EZERO;
   if (have) {
+    // a lane holds one row; the combined values go through a transposed copy in shared memory (the
+    // stages are idle by now), so that a warp stores 32 consecutive df32 of one row at a time
+    df32* tbuf = (df32*)smem + warp * 32 * 33;
 #pragma unroll 1
     for (int c = 0; c < BN; c += 32) {
       uint32_t r0[32], r1[32], r2[32], r3[32];
@@ -531,21 +564,29 @@ __global__ void __launch_bounds__(128, 1)
       tmem_ld32(base + BN, r1);
       tmem_ld32(base + 2 * BN, r2);
       tmem_ld32(base + 3 * BN, r3);
-      if (m < M) {
+      __syncwarp();
 #pragma unroll
-        for (int t = 0; t < 32; ++t) {
-          const int n = n0 + c + t;
-          if (n < N) {
-            const df32 s = two_sum(__uint_as_float(r0[t]), __uint_as_float(r1[t]));
-            const df32 u = two_sum(s.hi, __uint_as_float(r2[t]));
-            const df32 u2 = two_sum(u.hi, __uint_as_float(r3[t]));
-            const df32 v = renorm(u2.hi, __fadd_rn(__fadd_rn(u2.lo, u.lo), s.lo));
-            const int sc = max(ea + eB[(size_t)n * nch + z] - 14, -2 * 1000);
-            wrow[n] = df32(scalbnf(v.hi, sc), scalbnf(v.lo, sc));
-          }
+      for (int t = 0; t < 32; ++t) {
+        const df32 s = two_sum(__uint_as_float(r0[t]), __uint_as_float(r1[t]));
+        const df32 u = two_sum(s.hi, __uint_as_float(r2[t]));
+        const df32 u2 = two_sum(u.hi, __uint_as_float(r3[t]));
+        tbuf[lane * 33 + t] = renorm(u2.hi, __fadd_rn(__fadd_rn(u2.lo, u.lo), s.lo));
+      }
+      __syncwarp();
+      const int n = n0 + c + lane;
+      if (n < N) {
+        const int eb = eB[(size_t)n * nch + z];
+#pragma unroll 4
+        for (int i = 0; i < 32; ++i) {
+          const int mi = m0 + warp * 32 + i;
+          if (mi >= M) break;
+          const df32 v = tbuf[i * 33 + lane];
+          const int sc = max(eA[(size_t)mi * nch + z] + eb - 14, -2 * 1000);
+          ws[((size_t)z * M + mi) * N + n] = df32(scalbnf(v.hi, sc), scalbnf(v.lo, sc));
         }
       }
     }
+    (void)ea;
   } else if (nk > 0 && threadIdx.x == 0 && errw) {
     atomicOr(errw, ERRW_TIMEOUT);
   }
