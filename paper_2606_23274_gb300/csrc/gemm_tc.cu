@@ -253,11 +253,10 @@ __global__ void __launch_bounds__(128, 1)
   // ---------------- epilogue: all four warps, warp w owns accumulator rows 32w..32w+31
   bool have = false;
   if (nk > 0) have = mbar_wait(su32(&bars[2 * STAGES]), 0) && !*abort_flag;
+  have = __syncthreads_and(have);  // uniform: the epilogue below synchronises the CTA
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (have) {
     const int m = m0 + warp * 32 + lane;
-    const long long crow = (m < M) ? cm(m) : 0;
-    const long long crow2 = (m < M && C2) ? cm2(m) : 0;
     float* wrow = ws ? ws + (size_t)blockIdx.z * M * N + (size_t)m * N : nullptr;
     // A lane holds one accumulator row. Outputs whose consecutive columns are adjacent in memory
     // (the split-K partials, and C when its column map has unit inner stride) are written from a
@@ -266,6 +265,19 @@ __global__ void __launch_bounds__(128, 1)
     float* tbuf = (float*)smem + warp * 32 * 33;
     const bool c_cols = ws != nullptr || cn.s2 == 1;
     const bool c2_cols = C2 && cn2.s2 == 1;
+    // output offsets of the tile's rows and columns, evaluated once per CTA
+    long long* roff = (long long*)(smem + 4 * 32 * 33 * sizeof(float));
+    long long *roff2 = roff + BM, *coff = roff + 2 * BM, *coff2 = roff + 3 * BM;
+    {
+      const int t = threadIdx.x;
+      const bool mr = m0 + t < M, nr = n0 + t < N;
+      roff[t] = (!ws && mr) ? cm(m0 + t) : 0;
+      roff2[t] = (C2 && mr) ? cm2(m0 + t) : 0;
+      coff[t] = (!ws && nr) ? cn(n0 + t) : 0;
+      coff2[t] = (C2 && nr) ? cn2(n0 + t) : 0;
+    }
+    __syncthreads();
+    const long long crow = roff[warp * 32 + lane], crow2 = roff2[warp * 32 + lane];
 #pragma unroll 1
     for (int c = 0; c < BN; c += 32) {
       uint32_t r[32];
@@ -277,7 +289,7 @@ __global__ void __launch_bounds__(128, 1)
         __syncwarp();
         const int n = n0 + c + lane;
         if (n < N) {
-          const long long ccol = ws ? 0 : cn(n), ccol2 = c2_cols ? cn2(n) : 0;
+          const long long ccol = coff[c + lane], ccol2 = coff2[c + lane];
 #pragma unroll 4
           for (int i = 0; i < 32; ++i) {
             const int mi = m0 + warp * 32 + i;
@@ -288,9 +300,9 @@ __global__ void __launch_bounds__(128, 1)
               continue;
             }
             const float out = alpha * v;
-            if (c2_cols) C2[cm2(mi) + ccol2] = out;
+            if (c2_cols) C2[roff2[warp * 32 + i] + ccol2] = out;
             if (c_cols) {
-              const long long o = cm(mi) + ccol;
+              const long long o = roff[warp * 32 + i] + ccol;
               C[o] = beta != 0.f ? out + beta * C[o] : out;
             }
           }
@@ -302,9 +314,9 @@ __global__ void __launch_bounds__(128, 1)
           const int n = n0 + c + j;
           if (n < N) {
             const float out = alpha * __uint_as_float(r[j]);
-            if (C2 && !c2_cols) C2[crow2 + cn2(n)] = out;
+            if (C2 && !c2_cols) C2[crow2 + coff2[c + j]] = out;
             if (!c_cols) {
-              const long long o = crow + cn(n);
+              const long long o = crow + coff[c + j];
               C[o] = beta != 0.f ? out + beta * C[o] : out;
             }
           }
