@@ -558,11 +558,12 @@ def extras(ttfit, dev, stream, norm2_site):
     C5 = [torch.from_numpy(c).to(dev) for c in gaussian_mpo(32, 2, 96, 5, 2)]
     W5 = [torch.from_numpy(w).to(dev) for w in gaussian_mpo(32, 2, 32, 5, 3)]
     res5 = {}
-    for target, X in (("residual", C5), ("inner", W5)):
-        ttfit.tt_mpo_grad(A5, B5, X, target, "fp32", 0, stream=stream)  # warm-up
-        t, _ = _timed(stream, lambda: ttfit.tt_mpo_grad(A5, B5, X, target, "fp32", 0, stream=stream))
-        res5[target] = round(t, 4)
-    out["config5_adjoint_L32_chi96_fp32_s"] = res5
+    for prec in ("fp32", "tf32x3"):
+        for target, X in (("residual", C5), ("inner", W5)):
+            ttfit.tt_mpo_grad(A5, B5, X, target, prec, 0, stream=stream)  # warm-up
+            t, _ = _timed(stream, lambda: ttfit.tt_mpo_grad(A5, B5, X, target, prec, 0, stream=stream))
+            res5[f"{target}_{prec}"] = round(t, 4)
+    out["config5_adjoint_L32_chi96_s"] = res5
 
     # the zip-up contraction (Alg. 2) of the timed workload, alone and as the fit's initial guess
     # (Sec. 2.3.5), against the random guess of the timed fit

@@ -315,7 +315,9 @@ typedef enum {
  * gA, gB: caller device buffers with the shapes (d_out, d_in, bond) of A and
  * B, FP64 or FP32; receive dtarget/dA_l and dtarget/dB_l. *value (host, may be
  * NULL) receives the target. precision: TT_PREC_FP64 or TT_PREC_FP32 (the
- * contractions and environments in that type). checkpoint_every: left
+ * contractions and environments in that type), or TT_PREC_TF32_SPLIT (FP32
+ * environments; the contractions whose operands TMA can load run as 3xTF32 on
+ * the tensor cores, about FP32 accuracy, the others on the FP32 CUDA cores). checkpoint_every: left
  * environments are stored every k sites and recomputed in between during the
  * right-to-left gradient pass (1 = store all; 0 = about sqrt(L)), which bounds
  * memory at (L/k + k) environments; the four-layer ones hold (chi_A chi_B)^2

@@ -78,6 +78,10 @@ struct Ctx {
   int sm_count = 1;
   T* ws = nullptr;  // split-K workspace
   size_t ws_elems = 0;
+  bool tc = false;  // FP32: 3xTF32 products on the tensor cores
+  Arena* ar = nullptr;
+  T *sa = nullptr, *sb = nullptr;  // K-major copies of the operands of large tensor-core products
+  size_t sa_n = 0, sb_n = 0;
 };
 
 long long stride_of(const std::string& legs, char c, const Ext& ext) {
@@ -171,6 +175,34 @@ void einsum(Ctx<T>& cx, const Tn<const T>& A, const Tn<const T>& B, const Tn<T>&
   g.cn = map_in(gn, C.legs, ext);
   g.alpha = alpha;
   g.beta = beta;
+  if constexpr (sizeof(T) == 4) {
+    if (cx.tc && (long long)g.M * g.N * g.K >= (1ll << 18)) {
+      cudaError_t e = gemm_tf32(g, cx.ws, cx.ws_elems, cx.sm_count, nullptr, cx.st, true);
+      if (e == cudaSuccess) return;
+      if (e != cudaErrorNotSupported) GK(e);
+      // a large product whose operands TMA cannot load as they lie: copy them K-major first
+      // (O(size) against the O(M N K) of the product)
+      if ((long long)g.M * g.N * g.K >= (1ll << 24) && g.K % 4 == 0 && cx.ar) {
+        const size_t na = (size_t)g.M * g.K, nb = (size_t)g.N * g.K;
+        if (na > cx.sa_n) cx.sa = cx.ar->template alloc<T>(na), cx.sa_n = na;
+        if (nb > cx.sb_n) cx.sb = cx.ar->template alloc<T>(nb), cx.sb_n = nb;
+        GK(copy_map<T, T>(g.M, g.K, g.A, g.am, g.ak, cx.sa, IdxMap::lin(g.K), IdxMap::lin(1), 1.0, cx.st));
+        GK(copy_map<T, T>(g.N, g.K, g.B, g.bn, g.bk, cx.sb, IdxMap::lin(g.K), IdxMap::lin(1), 1.0, cx.st));
+        GemmArgs<T> h = g;
+        h.A = cx.sa;
+        h.am = IdxMap::lin(g.K);
+        h.ak = IdxMap::lin(1);
+        h.a_kfast = true;
+        h.B = cx.sb;
+        h.bn = IdxMap::lin(g.K);
+        h.bk = IdxMap::lin(1);
+        h.b_kfast = true;
+        e = gemm_tf32(h, cx.ws, cx.ws_elems, cx.sm_count, nullptr, cx.st, true);
+        if (e == cudaSuccess) return;
+        if (e != cudaErrorNotSupported) GK(e);
+      }
+    }
+  }
   GK(gemm_simt<T>(g, cx.ws, cx.ws_elems, cx.sm_count, cx.st));
 }
 
@@ -299,7 +331,7 @@ void store_cores(const T* in, const tt_mpo_desc* d, int l, long long n, cudaStre
 
 template <typename T>
 double run_grad(const tt_mpo_desc* Ad, const tt_mpo_desc* Bd, const tt_mpo_desc* Xd, int target, int ckpt,
-                cudaStream_t st, const tt_mpo_desc* gAd, const tt_mpo_desc* gBd) {
+                cudaStream_t st, const tt_mpo_desc* gAd, const tt_mpo_desc* gBd, bool tc = false) {
   Arena ar;
   Grad<T> G(ar);
   int LA, LB, LX, LgA, LgB;
@@ -321,6 +353,8 @@ double run_grad(const tt_mpo_desc* Ad, const tt_mpo_desc* Bd, const tt_mpo_desc*
   GK(cudaGetDevice(&dev));
   GK(cudaDeviceGetAttribute(&G.cx.sm_count, cudaDevAttrMultiProcessorCount, dev));
   G.cx.st = st;
+  G.cx.tc = tc;
+  G.cx.ar = &ar;
   G.L = L;
   G.a = bA;
   G.b = bB;
@@ -463,12 +497,14 @@ extern "C" tt_status tt_mpo_grad(const tt_mpo_desc* A, const tt_mpo_desc* B, con
                                  const tt_mpo_desc* gB, double* value) {
   if (!A || !B || !X || !gA || !gB) return TT_ERR_INVALID_ARGUMENT;
   if (target != TT_GRAD_RESIDUAL && target != TT_GRAD_INNER) return TT_ERR_INVALID_ARGUMENT;
-  if (precision != TT_PREC_FP64 && precision != TT_PREC_FP32) return TT_ERR_INVALID_ARGUMENT;
+  if (precision != TT_PREC_FP64 && precision != TT_PREC_FP32 && precision != TT_PREC_TF32_SPLIT)
+    return TT_ERR_INVALID_ARGUMENT;
   if (checkpoint_every < 0) return TT_ERR_INVALID_ARGUMENT;
   try {
     const double v = precision == TT_PREC_FP64
                          ? run_grad<double>(A, B, X, target, checkpoint_every, (cudaStream_t)stream, gA, gB)
-                         : run_grad<float>(A, B, X, target, checkpoint_every, (cudaStream_t)stream, gA, gB);
+                         : run_grad<float>(A, B, X, target, checkpoint_every, (cudaStream_t)stream, gA, gB,
+                                           precision == TT_PREC_TF32_SPLIT);
     if (value) *value = v;
     return TT_OK;
   } catch (const GradError& e) {

@@ -54,15 +54,34 @@ def test_uneven_bonds_and_dims():
     assert _relmax(_np(gA), oA) <= 1e-10 and _relmax(_np(gB), oB) <= 1e-10
 
 
-def test_fp32_matches_oracle():
+@pytest.mark.parametrize("precision", ["fp32", "tf32x3"])
+def test_fp32_matches_oracle(precision):
+    """FP32 environments; with tf32x3 the contractions TMA can load run as 3xTF32 on the
+    tensor cores (about FP32 accuracy)."""
     A = kron_sum_mpo(8, 12, 2, 0)
     B = kron_sum_mpo(8, 12, 2, 1)
     X = gaussian_mpo(8, 2, 10, 2, 2, 0.5)
     for target, fn in (("residual", f1_and_grads), ("inner", f2_and_grads)):
-        v, gA, gB = ttfit.tt_mpo_grad(A, B, X, target, "fp32")
+        v, gA, gB = ttfit.tt_mpo_grad(A, B, X, target, precision)
         vo, oA, oB = fn(X, A, B)
         assert abs(v - vo) <= 1e-4 * abs(vo)
         assert _relmax(_np(gA), oA) <= 1e-4 and _relmax(_np(gB), oB) <= 1e-4
+
+
+def test_tf32x3_config_size_matches_fp32():
+    """L = 32, chi = 96 (the adjoint configuration): the 3xTF32 gradients against the
+    all-FP32 ones."""
+    A = kron_sum_mpo(32, 96, 5, 0)
+    B = kron_sum_mpo(32, 96, 5, 1)
+    X = gaussian_mpo(32, 2, 96, 5, 2)
+    for target in ("residual", "inner"):
+        v1, gA1, gB1 = ttfit.tt_mpo_grad(A, B, X, target, "fp32")
+        v3, gA3, gB3 = ttfit.tt_mpo_grad(A, B, X, target, "tf32x3")
+        assert abs(v3 - v1) <= 1e-4 * abs(v1)
+        eA = max(float((a - b).norm() / b.norm()) for a, b in zip(gA3, gA1) if float(b.norm()) > 0)
+        eB = max(float((a - b).norm() / b.norm()) for a, b in zip(gB3, gB1) if float(b.norm()) > 0)
+        print(target, "tf32x3 vs fp32 gradients", eA, eB)
+        assert eA <= 1e-3 and eB <= 1e-3
 
 
 def test_central_finite_differences_of_the_gpu_value():
