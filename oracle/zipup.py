@@ -28,7 +28,7 @@ import numpy as np
 
 from . import philox
 from .fit import fix_signs, keep_rank
-from .mpo import left_orthogonalize, right_orthogonalize
+from .mpo import left_orthogonalize, qr_pos, right_orthogonalize
 
 
 def zipup_stream(site: int) -> int:
@@ -149,7 +149,8 @@ def project_bonds(X, k, seed=0, which=0):
     a bond is an isometry) is swept right to left; at site l the core with the
     remainder absorbed, M = X_l R_{l+1} reshaped chi_{l-1} x (d d' k), gets the
     range finder of Sec. 3: Y = M^T Omega (Omega chi_{l-1} x k Gaussian, stream
-    project_stream(which, l)), Q = the orthonormal factor of Y (d d' k x k);
+    project_stream(which, l)), Q = the orthonormal factor of Y (d d' k x k, the QR
+    with a non-negative diagonal of R, which fixes the bond basis the zip-up sketches);
     X_l <- Q^T and R_l = M Q. Where k >= min of M's sizes the bond is kept whole
     (Q = the orthonormal factor of M^T). The result is right-canonical."""
     X = left_orthogonalize([np.asarray(x, np.float64) for x in X])
@@ -165,9 +166,9 @@ def project_bonds(X, k, seed=0, which=0):
         M = T.reshape(a, s * t * c)
         if k < min(M.shape):
             Om = philox.normals(seed, project_stream(which, l + 1), a * k).reshape(a, k)
-            Q, _ = np.linalg.qr(M.T @ Om)
+            Q, _ = qr_pos(M.T @ Om)
         else:
-            Q, _ = np.linalg.qr(M.T)
+            Q, _ = qr_pos(M.T)
         out[l] = Q.T.reshape(Q.shape[1], s, t, c)
         R = M @ Q
     return out

@@ -165,3 +165,46 @@ def test_fit_from_zipup_guess_matches_oracle(update):
             assert f.bonds() == ref.st.history[s].bonds
     finally:
         f.destroy()
+
+
+def test_edge_cases_one_and_two_sites():
+    """Degenerate chains: one site (the product is the whole operator, no bond to truncate),
+    two sites with chi_max = 1 (the rank-one truncation of one bond), against the oracle."""
+    A = gaussian_mpo(1, 2, 3, 4, 0)
+    B = gaussian_mpo(1, 2, 3, 4, 1)
+    N = ttfit.tt_mpo_naive_product(_dev(A), _dev(B))
+    R = naive_product(A, B)
+    assert np.abs(N[0].cpu().numpy() - R[0]).max() <= 1e-14 * np.abs(R[0]).max()
+    C = ttfit.tt_mpo_zipup(A, B, 4, 0.0, precision="fp64", sv_cutoff=1e-13)
+    assert _rel(C, R) <= 1e-13
+    A = gaussian_mpo(2, 2, 3, 5, 0)
+    B = gaussian_mpo(2, 2, 2, 5, 1)
+    Ap, Bp = canonicalize_input(A), canonicalize_input(B)
+    for update in ("svd", "rsvd"):
+        R = zipup_right_to_left(Ap, Bp, 1, 0.0, 1e-13, update, 0, 2)
+        C = ttfit.tt_mpo_zipup(A, B, 1, 0.0, update=update, oversample=0, seed=2, precision="fp64",
+                               sv_cutoff=1e-13)
+        assert [c.shape[0] for c in C] == [1, 1]
+        assert _rel(C, R) <= 1e-12
+    X = naive_product(A, B)
+    C = ttfit.tt_mpo_compress(X, 1, 0.0, precision="fp64", sv_cutoff=1e-13)
+    R = compress(canonicalize_input(X), 1, 0.0, 1e-13)
+    assert _rel(C, R) <= 1e-12
+
+
+@pytest.mark.parametrize("gauge", ["site", "inverse"])
+def test_zipup_guess_with_projection_follows_oracle(gauge):
+    """The zip-up guess of the projected chains (both options together), both gauges."""
+    A, B = mpo_pair("kron_L10_chi16", seed=0)
+    ref = FitOracle(A, B, 16, 1e-10, gauge=gauge, init="zipup", update="rsvd", oversample=10, seed=7,
+                    conv_tol=0.0, ab_rank=8)
+    ref.sweep(3, stop_on_converge=False)
+    f = ttfit.tt_fit_create(A, B, 16, 1e-10, gauge, init="zipup", update="rsvd", oversample=10, seed=7,
+                            precision="fp64", conv_tol=0.0, sv_cutoff=1e-13, ab_rank=8)
+    try:
+        for s in range(3):
+            rep = f.sweep(1)
+            want = ref.st.history[s].norm2
+            assert abs(rep["norm2_C"] - want) <= 1e-9 * want, (s, rep["norm2_C"], want)
+    finally:
+        f.destroy()
