@@ -201,6 +201,27 @@ def run_fit(ttfit, Ain, Bin, schedule, seed, dev, stream, chi=CHI, lo_sweeps=LO_
     return rep, sweeps, phase_sweeps, phases, C, launches
 
 
+def dist_env():
+    """(world size, rank, local rank) from the launcher's environment (1, 0, 0 when run alone)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x, world, device):
+    """The largest x over the ranks: a step takes as long as its slowest replica."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seed(rank):
+    """Rank r fits its own, independent MPO pair: the workload drawn with seed r."""
+    return int(rank)
+
+
 def local_update_roof(flops, ms, pk):
     """The local update (halves, join, environment finish: minimal algorithmic flops over their summed
     event time) against the dense TF32 tensor rate, half the measured (else fallback) sustained bf16
@@ -220,9 +241,7 @@ def native(args):
     from paper_2606_23274_gb300 import ttfit
     from paper_2606_23274_gb300.synth import mpo_pair
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = dist_env()
     if world > 1:
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
@@ -233,7 +252,7 @@ def native(args):
     # inputs resident in HBM before the timed region; rank r fits its own pair
     from paper_2606_23274_gb300.synth import WORKLOADS
     chi = WORKLOADS[args.workload]["chi_C"]
-    A, B = mpo_pair(args.workload, seed=rank)
+    A, B = mpo_pair(args.workload, seed=replica_seed(rank))
     Ad = [torch.from_numpy(a).to(dev) for a in A]
     Bd = [torch.from_numpy(b).to(dev) for b in B]
     Ah = [torch.from_numpy(a).pin_memory() for a in A]
@@ -266,11 +285,7 @@ def native(args):
     barrier()
     wall = time.time() - t_wall0
     clk = clocks.stop()
-    t_step = statistics.mean(times)
-    tmax = torch.tensor([t_step], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    t_step = float(tmax.item())
+    t_step = max_over_ranks(statistics.mean(times), world, dev)
 
     e2e = None
     if not args.no_e2e:
@@ -676,8 +691,7 @@ def reference(args):
     """The FP64 oracle on the host cores. A step is one bulk window of the workload, measured;
     `value` is that window time scaled to a full fit (29 windows x 3 sweeps), and ms_per_step is
     the measured per-step time of the sample itself."""
-    rank = int(os.environ.get("RANK", "0"))
-    if rank != 0:
+    if dist_env()[1] != 0:  # under torchrun the other ranks exit without work
         return
     windows, sweeps = L_SITES - 1, 3
     for _ in range(args.warmup):

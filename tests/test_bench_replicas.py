@@ -1,0 +1,77 @@
+"""The multi-GPU mode of bench.py on CPU: one process per rank (gloo, world size 2,
+127.0.0.1), each fitting its own pair, the step time taken as the maximum over
+the ranks, and the reference arm running on rank 0 only. The data path has no
+collective; these are the only cross-rank steps."""
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, outdir):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE=str(world), RANK=str(rank),
+                      LOCAL_RANK=str(rank))
+    import bench
+    from paper_2606_23274_gb300.synth import mpo_pair
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        assert bench.dist_env() == (world, rank, rank)
+        # every rank reports its own step time; all of them see the slowest one
+        t = bench.max_over_ranks(0.25 + 0.5 * rank, world, "cpu")
+        # independent pairs: rank r draws the workload with seed r
+        A, _ = mpo_pair("kron_L10_chi16", seed=bench.replica_seed(rank))
+        sums = [None] * world
+        dist.all_gather_object(sums, float(sum(np.abs(a).sum() for a in A)))
+        dist.barrier()
+        with open(os.path.join(outdir, f"rank{rank}.txt"), "w") as f:
+            f.write(f"{t} {sums[0]} {sums[1]}\n")
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_replicas_take_the_slowest_step_and_fit_distinct_pairs(tmp_path):
+    world = 2
+    mp.start_processes(_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True,
+                       start_method="spawn")
+    rows = [open(tmp_path / f"rank{r}.txt").read().split() for r in range(world)]
+    for row in rows:
+        assert float(row[0]) == pytest.approx(0.75)          # the max over ranks, on every rank
+        assert float(row[1]) != float(row[2])               # the ranks' pairs differ
+    assert rows[0][1:] == rows[1][1:]
+
+
+def test_single_process_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    env = {k: os.environ.pop(k) for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK") if k in os.environ}
+    try:
+        assert bench.dist_env() == (1, 0, 0)
+        assert bench.max_over_ranks(1.25, 1, "cpu") == 1.25
+    finally:
+        os.environ.update(env)
+
+
+def test_reference_arm_runs_on_rank_zero_only(capsys, monkeypatch):
+    """Under torchrun the other ranks leave the reference arm without work or output."""
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    ns = type("A", (), {"steps": 1, "warmup": 0, "gpus": 2})()
+    assert bench.reference(ns) is None
+    assert capsys.readouterr().out == ""
