@@ -37,6 +37,9 @@ Readings of the paper taken here, where it is silent or ambiguous:
 * Singular pairs carry a fixed sign: the largest-magnitude entry of u_j is
   positive (the paper leaves the sign open; the sketch of Sec. 3.1 is not
   invariant under sign changes of the bond basis, so both sides fix it).
+* Non-unique results: at a cut with s_k / s_{k+1} <= 1 + 1e-6 the kept subspace is not
+  unique; gaps() reports the ratio per bond and pinned_bonds() the bonds whose spectrum
+  parity is meaningful.
 * Convergence: ||C||^2 = sum of kept s^2 at the last window of a sweep (the
   orthogonality centre); delta_s = | ||C||^2_s - ||C||^2_{s-1} | / ||C||^2_s.
 """
@@ -210,6 +213,7 @@ class FitOracle:
             C0 = right_orthogonalize(left_orthogonalize([np.asarray(x, np.float64) for x in init_C]))
         else:
             raise ValueError(init)
+        self.gap = [math.inf] * (L + 1)  # per bond: s_k / s_{k+1} of its latest update
         Y = [np.ones(1)] + [np.ones(C0[l].shape[3]) for l in range(L - 1)] + [np.ones(1)]
         self.st = FitState(A=A, B=B, Psi=C0, Y=Y, S=[None] * (L + 1))
         self._precompute_right_envs()
@@ -247,6 +251,9 @@ class FitOracle:
             U, S, Vt = exact_svd(M)
         k = keep_rank(S, norm_M, self.tau, L, self.chi_max, self.sv_cutoff)
         disc = math.sqrt(float(np.sum(S[k:] ** 2))) / norm_M if norm_M > 0 else 0.0
+        # gap at the cut, s_k / s_{k+1} (inf when nothing is cut): where it is ~1 the kept subspace
+        # is not unique, and neither are the bond's spectrum and cores in another arithmetic
+        self.gap[l] = float(S[k - 1] / S[k]) if k < len(S) and S[k] > 0 else math.inf
         U, Vt = fix_signs(U[:, :k], Vt[:k, :])
         S = S[:k]
         st.S[l] = S.copy()
@@ -304,6 +311,15 @@ class FitOracle:
     def lambdas(self):
         """Kept singular values of the last update of each inner bond 1..L-1."""
         return [s.copy() for s in self.st.S[1:self.L]]
+
+    def gaps(self):
+        """s_k / s_{k+1} at the cut of the last update of each inner bond 1..L-1 (inf: no cut)."""
+        return list(self.gap[1:self.L])
+
+    def pinned_bonds(self, rel=1e-6):
+        """Inner bonds (1-based) whose cut is not degenerate, gap > 1 + rel: their kept spectrum and
+        subspace are unique; at the others parity of the spectrum is declared unpinned."""
+        return [l for l, g in enumerate(self.gaps(), 1) if g > 1.0 + rel]
 
 
 def fit(A, B, chi_max, tol, n_sweeps, **kw):

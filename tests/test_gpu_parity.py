@@ -58,8 +58,14 @@ def test_truncated_fit_fp64_matches_oracle(gauge, update):
     assert _rel(C, Co) <= 1e-9
     for r, h in zip(reps, f.st.history):
         assert abs(r["norm2_C"] - h.norm2) <= 1e-11 * h.norm2
-    for got, ref in zip(lam, f.lambdas()):
-        assert np.allclose(got, ref, rtol=1e-9, atol=1e-12 * ref[0])
+    # spectra where the cut is not degenerate (the oracle's gap report); the operator above is
+    # compared everywhere
+    pinned = f.pinned_bonds()
+    print(gauge, update, "bonds with a degenerate cut (spectrum unpinned):",
+          [l for l in range(1, len(lam) + 1) if l not in pinned])
+    for l, (got, ref) in enumerate(zip(lam, f.lambdas()), 1):
+        if l in pinned:
+            assert np.allclose(got, ref, rtol=1e-9, atol=1e-12 * ref[0])
 
 
 def test_fp32_contractions_match_oracle():

@@ -323,3 +323,21 @@ def test_bond_spectra_match_dense_matricisations():
         r = len(got[l - 1])
         assert np.allclose(got[l - 1], ref[:r], rtol=1e-10, atol=1e-13 * ref[0])
         assert np.all(ref[r:] <= 1e-12 * ref[0])               # the bond holds the whole rank
+
+
+def test_gap_report_marks_a_degenerate_cut():
+    """A two-site operator with singular values (3, 2, 2, 1) across its bond, fitted to bond 2:
+    the cut falls inside the degenerate pair, so the gap is 1 and the bond is unpinned; to bond
+    3 the gap is 2 and the bond is pinned."""
+    from oracle.fit import FitOracle
+    rng = np.random.default_rng(3)
+    U, _ = np.linalg.qr(rng.standard_normal((4, 4)))
+    V, _ = np.linalg.qr(rng.standard_normal((4, 4)))
+    s = np.array([3.0, 2.0, 2.0, 1.0])
+    X = [(U * s).reshape(1, 2, 2, 4), V.T.reshape(4, 2, 2, 1)]
+    I = [np.eye(2).reshape(1, 2, 2, 1), np.eye(2).reshape(1, 2, 2, 1)]
+    for chi, gap, pinned in ((2, 1.0, []), (3, 2.0, [1])):
+        f = FitOracle(X, I, chi, 0.0, conv_tol=0.0)
+        f.sweep(1)
+        assert f.gaps()[0] == pytest.approx(gap, rel=1e-12)
+        assert f.pinned_bonds() == pinned
