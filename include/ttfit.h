@@ -134,8 +134,9 @@ typedef struct {
                        /* puts a rank-k projector Q Q^T on every bond of A and of B, Q the    */
                        /* orthonormal range of a k-column Philox Gaussian sketch of the bond  */
                        /* (streams (4 << 40) | l for A, (5 << 40) | l for B, site l 1-based), */
-                       /* drawn once at creation on the prepared chains (right to left, then */
-                       /* the QR sweep again); the fit then contracts bonds of at most k. The */
+                       /* drawn once at creation on the prepared chains (right to left; the  */
+                       /* QR sweep again only before a zip-up guess); the fit then contracts */
+                       /* bonds of at most k. The                                            */
                        /* fit approximates the product of the projected chains, so this needs */
                        /* A and B with decaying bond spectra. Needs prepare_inputs. 0 = off.  */
 } tt_fit_options;

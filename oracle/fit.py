@@ -26,8 +26,10 @@ Readings of the paper taken here, where it is silent or ambiguous:
 * Randomized bond projection (Sec. 3.2, option ab_rank = k): the projectors
   depend only on A and B, which the fit never changes, so they are drawn once:
   A and B are replaced by their projected chains (oracle/zipup.py
-  project_bonds, streams (4 << 40) | l for A and (5 << 40) | l for B), brought
-  back to left-canonical form, and the fit runs on them in either gauge.
+  project_bonds, streams (4 << 40) | l for A and (5 << 40) | l for B; they
+  come out right-canonical, and the fit does not depend on their gauge), and
+  the fit runs on them in either gauge. The zip-up guess left-orthogonalizes
+  its inputs itself.
 * Truncation (Sec. 2.3.4): keep k = min(chi_max, min{k : sqrt(sum_{j>k} s_j^2)
   <= (tau/L) ||M||_F}), then drop s_j <= sv_cutoff * s_1 (Sec. 2.3.1 allows
   dropping very small values before inversion; applied in both gauges), k >= 1.
@@ -197,8 +199,8 @@ class FitOracle:
             A, B = canonicalize_input(A), canonicalize_input(B)
         if ab_rank > 0:                          # Sec. 3.2: rank-k projectors on the A and B bonds
             from .zipup import project_bonds
-            A = left_orthogonalize(project_bonds(A, ab_rank, seed, 0))
-            B = left_orthogonalize(project_bonds(B, ab_rank, seed, 1))
+            A = project_bonds(A, ab_rank, seed, 0)
+            B = project_bonds(B, ab_rank, seed, 1)
         dout = [a.shape[1] for a in A]
         din = [b.shape[2] for b in B]
         if init == "random":

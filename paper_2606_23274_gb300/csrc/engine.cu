@@ -2223,10 +2223,12 @@ void zipup_rl(tt_fit* h, const ZipArgs& z, std::vector<double*>& C, std::vector<
 // Each prepared (left-canonical) chain is swept right to left as its zip-up
 // with the identity MPO, keeping the k-column Gaussian range of every bond
 // (streams (4 << 40) | l for A, (5 << 40) | l for B; bonds narrower than k stay
-// whole), in FP64 arithmetic, and is then brought back to left-canonical form by
-// the QR sweep.
+// whole), in FP64 arithmetic. The fit does not depend on the gauge of A and B,
+// so the projected chains stay right-canonical, unless the zip-up guess follows
+// (left_canonical): it sketches the bonds of left-canonical chains, so they are
+// brought back to that form by the QR sweep first.
 // The contractions of the fit then run on bonds of at most k.
-void project_ab(tt_fit* h, int k, long long mc) {
+void project_ab(tt_fit* h, int k, long long mc, bool left_canonical) {
   Dims& D = h->D;
   for (int which = 0; which < 2; ++which) {
     std::vector<double*>& X = which ? h->B64 : h->A64;
@@ -2255,9 +2257,11 @@ void project_ab(tt_fit* h, int k, long long mc) {
     for (double* p : X) h->pool.release(p);
     X = P;
     bx = pb;
-    Prep PX = make_prep(h, mc);
-    qr_sweep(h, PX, X, bx, dout, din);
-    finish_prep(h, PX);
+    if (left_canonical) {
+      Prep PX = make_prep(h, mc);
+      qr_sweep(h, PX, X, bx, dout, din);
+      finish_prep(h, PX);
+    }
   }
 }
 
@@ -2623,7 +2627,7 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
       }
     }
     if (o.prepare_inputs) prepare_ab(h, mc);  // Alg. 5: left_orthogonalize(A), left_orthogonalize(B)
-    if (o.ab_rank > 0) project_ab(h, o.ab_rank, mc);
+    if (o.ab_rank > 0) project_ab(h, o.ab_rank, mc, o.init == TT_INIT_ZIPUP);
     if (o.init == TT_INIT_RANDOM) {
       for (int i = 0; i < NS; ++i) {
         CK(cudaStreamSynchronize(pool[i]));

@@ -187,11 +187,11 @@ def test_fit_with_projected_inputs():
     f1.sweep(3, stop_on_converge=False)
     assert abs(f0.st.history[-1].norm2 - f1.st.history[-1].norm2) <= 1e-12 * f0.st.history[-1].norm2
     # a smaller rank fits the product of the projected chains
-    from oracle.mpo import canonicalize_input, left_orthogonalize
+    from oracle.mpo import canonicalize_input
     f2 = FitOracle(A, B, 12, 0.0, conv_tol=0.0, ab_rank=3, seed=4)
     f2.sweep(3, stop_on_converge=False)
-    Ap = left_orthogonalize(project_bonds(canonicalize_input(A), 3, 4, 0))
-    Bp = left_orthogonalize(project_bonds(canonicalize_input(B), 3, 4, 1))
+    Ap = project_bonds(canonicalize_input(A), 3, 4, 0)
+    Bp = project_bonds(canonicalize_input(B), 3, 4, 1)
     assert max(x.shape[3] for x in Ap) == 3
     f3 = FitOracle(Ap, Bp, 12, 0.0, conv_tol=0.0, seed=4, prepare_inputs=False)
     f3.sweep(3, stop_on_converge=False)
