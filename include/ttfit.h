@@ -57,12 +57,18 @@ typedef enum { TT_UPDATE_2SITE_SVD = 0, TT_UPDATE_2SITE_RSVD = 1 } tt_update;
  * FP32: FP32 CUDA-core kernels. TF32: tensor-core kernels (tcgen05, TF32
  * operands, FP32 accumulation in tensor memory). TF32_SPLIT: the same with
  * each operand split into a TF32 high part and an FP32 remainder, three
- * products (hi*hi + hi*lo + lo*hi): about FP32 accuracy. BF16_SPLIT: reserved,
- * rejected with TT_ERR_INVALID_ARGUMENT. DF32: every value of the chain is a
- * pair of floats hi + lo (about 48 significant bits) and every multiply-add
- * is an exact FP32 product plus a compensated sum, all on the FP32 pipes
- * (FP64-class contractions at several times the FP64 rate of this GPU);
- * factorisation as for FP64. The FP32, TF32 and TF32_SPLIT paths factorise in
+ * products (hi*hi + hi*lo + lo*hi): about FP32 accuracy. DF32: every value
+ * of the chain is a pair of floats hi + lo (about 48 significant bits);
+ * small contractions run on the FP32 pipes (an exact FP32 product plus a
+ * compensated sum per multiply-add), large ones on the tensor cores by a
+ * fixed-point digit split: each 512-wide chunk of a row is cut into six 8-bit
+ * digit planes, whose products accumulate exactly in FP32 at the leading
+ * levels (FP64-class contractions at several times the FP64 rate of this
+ * GPU); factorisation as for FP64. BF16_SPLIT: DF32 with the digit planes in
+ * BF16 on kind::f16 MMAs (the digits are exact in BF16; twice the TF32 tensor
+ * rate and half the bytes per plane); the same results as DF32 up to the
+ * order of the FP32 sums in the non-exact digit levels. The zip-up entry
+ * points reject it. The FP32, TF32 and TF32_SPLIT paths factorise in
  * FP32 and make the kept singular vectors an FP64 isometry (two
  * Newton-Schulz steps) before the gauge update; C is returned in FP64. */
 typedef enum {

@@ -270,6 +270,7 @@ struct tt_fit {
   bool hp_sweep = false;  // the current sweep uses the FP64-class sketch basis (factorize_hp)
   int escale = 0;         // the fit runs on 2^-ea A, 2^-eb B; C, its spectra and norm get 2^escale back
   bool use_oz = true;     // DF32 chains: contractions on the tensor cores by the digit split
+  bool oz_bf16 = false;   // ... with BF16 digit planes on kind::f16 (TT_PREC_BF16_SPLIT), else TF32 ones
   std::vector<void*> chain_bufs;  // buffers rebuilt when the chain precision changes
   // site-gauge segment-parallel fit: whether the sub-TTs have been merged since the last phase,
   // which phase ran last, and the orthogonality centre the merge left (-1: none)
@@ -332,7 +333,7 @@ void gemm(tt_fit* h, const GemmArgs<T>& g, bool chain = false) {
     Work& w = W(h);
     if (chain && h->use_oz && w.ozA && (long long)g.M * g.N * g.K >= (1ll << 21)) {
       cudaError_t e = gemm_oz(g, w.ozA, w.ozB, w.oz_slice, w.ozEA, w.ozEB, w.oz_exp, w.ozWs, w.oz_ws, h->sm_count,
-                              w.errw, w.st);
+                              w.errw, w.st, h->oz_bf16);
       if (e == cudaSuccess) {
         h->tc_launches += 1;
         return;
@@ -2511,7 +2512,9 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
     if (o.update != 0 && o.update != 1) return TT_ERR_INVALID_ARGUMENT;
     if (o.precision < 0 || o.precision > 5 || o.oversample < 0) return TT_ERR_INVALID_ARGUMENT;
     if (o.init < 0 || o.init > 3 || (o.init == TT_INIT_GIVEN && !o.init_C)) return TT_ERR_INVALID_ARGUMENT;
-    if (o.precision == TT_PREC_BF16_SPLIT) return TT_ERR_INVALID_ARGUMENT;  // reserved, not implemented
+    // BF16_SPLIT is the DF32 chain whose digit-split contractions run on BF16 digit planes
+    const bool oz_bf16 = o.precision == TT_PREC_BF16_SPLIT;
+    if (oz_bf16) o.precision = TT_PREC_DF32;
     if (o.edge_extra < 0) return TT_ERR_INVALID_ARGUMENT;
     if (o.fast_factor < 0 || o.fast_factor > 3) return TT_ERR_INVALID_ARGUMENT;
     if (o.ab_rank < 0 || (o.ab_rank > 0 && !o.prepare_inputs)) return TT_ERR_INVALID_ARGUMENT;
@@ -2541,6 +2544,7 @@ tt_status tt_fit_create(const tt_mpo_desc* A, const tt_mpo_desc* B, int chi_max,
     h->seed = o.seed;
     h->use_f32 = (o.precision != TT_PREC_FP64 && o.precision != TT_PREC_DF32);
     h->use_df = (o.precision == TT_PREC_DF32);
+    h->oz_bf16 = oz_bf16;
     h->fact_f32 = h->use_f32 || o.fast_factor;
     h->fast_factor = o.fast_factor;
     h->cutoff_user = o.sv_cutoff >= 0;
@@ -2894,7 +2898,9 @@ tt_status tt_fit_result(const tt_fit* hc, tt_mpo_desc* C, double* lambdas) {
 }
 
 tt_status tt_fit_set_precision(tt_fit* h, int precision, int fast_factor) {
-  if (!h || precision < 0 || precision > 5 || precision == TT_PREC_BF16_SPLIT) return TT_ERR_INVALID_ARGUMENT;
+  if (!h || precision < 0 || precision > 5) return TT_ERR_INVALID_ARGUMENT;
+  const bool oz_bf16 = precision == TT_PREC_BF16_SPLIT;  // the DF32 chain on BF16 digit planes
+  if (oz_bf16) precision = TT_PREC_DF32;
   if (fast_factor < 0 || fast_factor > 3) return TT_ERR_INVALID_ARGUMENT;
   if (h->poisoned) return TT_ERR_STATE;
   if (h->segs.size() > 1 && h->phases_done % 2 != 0) {
@@ -2911,6 +2917,7 @@ tt_status tt_fit_set_precision(tt_fit* h, int precision, int fast_factor) {
     h->precision = precision;
     h->use_f32 = f32;
     h->use_df = precision == TT_PREC_DF32;
+    h->oz_bf16 = oz_bf16;
     h->fact_f32 = f32 || fast_factor;
     h->fast_factor = fast_factor;
     if (!h->cutoff_user) h->cutoff = default_cutoff(precision, h->fact_f32);

@@ -17,6 +17,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include <cstdint>
 #include <climits>
 #include <cstring>
@@ -107,6 +108,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 __host__ __device__ constexpr uint32_t idesc_tf32(int m, int n, bool b_mn_major) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((b_mn_major ? 1u : 0u) << 16) | ((uint32_t)(n >> 3) << 17) |
          ((uint32_t)(m >> 4) << 24);
+}
+
+// kind::f16 with both operands BF16 (format 1 at bits 7-9 and 10-12), D = F32, both K-major
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
 template <bool B_MN, bool SPLIT>
@@ -370,15 +384,16 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   return fn;
 }
 
-bool make_map(CUtensorMap* map, const float* ptr, uint64_t inner, uint64_t outer, uint64_t row_stride_elems,
-              uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
+bool make_map(CUtensorMap* map, const void* ptr, uint64_t inner, uint64_t outer, uint64_t row_stride_elems,
+              uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B,
+              CUtensorMapDataType dt = CU_TENSOR_MAP_DATA_TYPE_FLOAT32, int elem_bytes = 4) {
   auto enc = encoder();
   if (!enc) return false;
   cuuint64_t dims[2] = {inner, outer};
-  cuuint64_t strides[1] = {row_stride_elems * 4};
+  cuuint64_t strides[1] = {row_stride_elems * (uint64_t)elem_bytes};
   cuuint32_t box[2] = {box_inner, box_outer};
   cuuint32_t es[2] = {1, 1};
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)ptr, dims, strides, box, es,
+  CUresult r = enc(map, dt, 2, (void*)ptr, dims, strides, box, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -406,14 +421,21 @@ inline bool lin_stride(const IdxMap& m, long long& s) {
 // weighted 2^-16 x 2^-24) and levels >= 3 share the fourth. The epilogue joins
 // the four in double-FP32 and scales by the chunk exponents; the chunks of K
 // are the split-K partials, summed in double-FP32 by splitk_reduce.
+//
+// The digits are integers of at most 8 significant bits times a power of two,
+// so they are exact in BF16 as well. The same split then runs on kind::f16
+// MMAs with BF16 digit planes: 16 digits of K per instruction instead of 8 at
+// the same issue cost (the BF16 tensor rate is twice the TF32 one), and half
+// the bytes per plane to write, load and stage.
 // ---------------------------------------------------------------------------
 constexpr int OZ_S = 6;
 constexpr int OZ_KC = 512;
 constexpr int OZ_TILES = 2 * OZ_S;
-// k-blocks of 16 FP32 digits (64 bytes: the 64-byte swizzle span), so that two stages of the 12
-// digit tiles (2 x 96 KB) fit in shared memory and the TMA of one k-block overlaps the MMAs of the other
-constexpr int OZ_BK = 16;
-constexpr int OZ_TILE = BM * OZ_BK * 4;  // 8 KB
+// k-blocks of 64 bytes (the 64-byte swizzle span: 16 TF32 or 32 BF16 digits), so that two stages of
+// the 12 digit tiles (2 x 96 KB) fit in shared memory and the TMA of one k-block overlaps the MMAs of
+// the other; each MMA takes 32 bytes of K
+constexpr int OZ_KBYTES = 64;
+constexpr int OZ_TILE = BM * OZ_KBYTES;  // 8 KB
 constexpr int OZ_STAGES = 2;
 constexpr int OZ_SMEM = OZ_STAGES * OZ_TILES * OZ_TILE + 1024 + 256;
 constexpr int OZ_EZERO = -1000;  // exponent of an all-zero chunk
@@ -425,9 +447,16 @@ template <>
 __device__ __forceinline__ float2 as_pair<df32>(df32 x) { return make_float2(x.hi, x.lo); }
 template <>
 __device__ __forceinline__ float2 as_pair<float>(float x) { return make_float2(x, 0.f); }
+// a digit in its plane's type (exact in both: at most 8 significant bits)
+template <typename D>
+__device__ __forceinline__ D as_digit(float d);
+template <>
+__device__ __forceinline__ float as_digit<float>(float d) { return d; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 as_digit<__nv_bfloat16>(float d) { return __float2bfloat16_rn(d); }
 
-template <typename T>
-__global__ void oz_slice_kernel(int R, int K, int Kp, const T* __restrict__ X, long long ld, float* __restrict__ sl,
+template <typename T, typename D>
+__global__ void oz_slice_kernel(int R, int K, int Kp, const T* __restrict__ X, long long ld, D* __restrict__ sl,
                                 int* __restrict__ ex, int nch) {
   const int lane = threadIdx.x & 31;
   const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -464,24 +493,30 @@ __global__ void oz_slice_kernel(int R, int K, int Kp, const T* __restrict__ X, l
       for (int i = 0; i < OZ_S; ++i) d[i] = 0.f;
     }
 #pragma unroll
-    for (int i = 0; i < OZ_S; ++i) sl[i * plane + (size_t)row * Kp + k] = d[i];
+    for (int i = 0; i < OZ_S; ++i) sl[i * plane + (size_t)row * Kp + k] = as_digit<D>(d[i]);
   }
 }
 
-__device__ __forceinline__ void oz_mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, bool acc) {
-  mma_tf32(tmem, ad, bd, idesc, acc ? 1u : 0u);
+template <typename D>
+__device__ __forceinline__ void oz_mma(uint32_t tmem, uint64_t ad, uint64_t bd, bool acc) {
+  if constexpr (sizeof(D) == 2)
+    mma_bf16(tmem, ad, bd, idesc_bf16(BM, BN), acc ? 1u : 0u);
+  else
+    mma_tf32(tmem, ad, bd, idesc_tf32(BM, BN, false), acc ? 1u : 0u);
 }
 
 // One 128 x 128 output tile of one K-chunk (blockIdx.z) into the double-FP32
 // partial ws[z][M][N]. Warp 0: TMA producer; warp 1: tensor-memory owner and
 // MMA issuer; all four warps: epilogue. A stage holds the 2 OZ_S digit tiles of
-// a 16-wide k-block (96 KB); two stages alternate, so the loads of one k-block
+// a 64-byte k-block (96 KB); two stages alternate, so the loads of one k-block
 // run under the 42 MMAs of the other. The four accumulators fill the 512
-// tensor-memory columns.
+// tensor-memory columns. D: the digit type (float: kind::tf32, BF16: kind::f16).
+template <typename D>
 __global__ void __launch_bounds__(128, 1)
     gemm_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
                    int K, const int* __restrict__ eA, const int* __restrict__ eB, int nch, df32* __restrict__ ws,
                    uint32_t* errw) {
+  constexpr int KB = OZ_KBYTES / (int)sizeof(D);  // digits of K per k-block
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   // [0, 1] full, [2, 3] empty (per stage), [4] accumulators ready
@@ -491,7 +526,7 @@ __global__ void __launch_bounds__(128, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN, z = blockIdx.z;
   const int kb0 = z * OZ_KC, kend = min(K, kb0 + OZ_KC);
-  const int nk = (kend - kb0 + OZ_BK - 1) / OZ_BK;
+  const int nk = (kend - kb0 + KB - 1) / KB;
   if (threadIdx.x == 0) {
     for (int b = 0; b < 5; ++b) mbar_init(su32(&bars[b]), 1);
     *abort_flag = 0;
@@ -518,7 +553,7 @@ __global__ void __launch_bounds__(128, 1)
       }
       const uint32_t full = su32(&bars[st]);
       mbar_expect_tx(full, OZ_TILES * OZ_TILE);
-      const int k = kb0 + kb * OZ_BK;
+      const int k = kb0 + kb * KB;
       uint8_t* base = smem + st * OZ_TILES * OZ_TILE;
 #pragma unroll
       for (int i = 0; i < OZ_S; ++i) {
@@ -528,7 +563,6 @@ __global__ void __launch_bounds__(128, 1)
       issued = kb + 1;
     }
   } else if (warp == 1 && lane == 0) {
-    const uint32_t idesc = idesc_tf32(BM, BN, false);
     bool started[4] = {false, false, false, false};
     bool ok = true;
     for (int kb = 0; kb < nk; ++kb) {
@@ -547,9 +581,9 @@ __global__ void __launch_bounds__(128, 1)
           const int lev = min(i + j, 3);
           const uint32_t a_base = su32(base + i * OZ_TILE), b_base = su32(base + (OZ_S + j) * OZ_TILE);
 #pragma unroll
-          for (int kk = 0; kk < OZ_BK / 8; ++kk) {
-            oz_mma(tmem + lev * BN, sdesc64(a_base + kk * 32, 16, 512), sdesc64(b_base + kk * 32, 16, 512), idesc,
-                   started[lev]);
+          for (int kk = 0; kk < OZ_KBYTES / 32; ++kk) {
+            oz_mma<D>(tmem + lev * BN, sdesc64(a_base + kk * 32, 16, 512), sdesc64(b_base + kk * 32, 16, 512),
+                      started[lev]);
             started[lev] = true;
           }
         }
@@ -663,45 +697,58 @@ cudaError_t gemm_tf32(const GemmArgs<float>& g, float* ws, size_t ws_elems, int 
   return splitk_reduce<float>(g, ws, splits, sm_count, st);
 }
 
-// FP64-class GEMM (double-FP32 operands and result) on the TF32 tensor cores
-// by the fixed-point digit split above. Operands must be K-major with 16-byte
-// aligned rows after padding, like gemm_tf32. sA, sB: digit planes of
-// OZ_S * M * Kp and OZ_S * N * Kp floats; eA, eB: M * nch and N * nch ints;
-// ws: nch * M * N double-FP32 partials. Returns cudaErrorNotSupported when a
-// layout or a capacity does not fit (the caller then uses the CUDA-core kernel).
+// FP64-class GEMM (double-FP32 operands and result) on the tensor cores by the
+// fixed-point digit split above: TF32 digit planes on kind::tf32, or BF16
+// digit planes on kind::f16 (bf16 = true). Operands must be K-major with
+// 16-byte aligned rows after padding, like gemm_tf32. sA, sB: digit planes,
+// OZ_S * M * Kp and OZ_S * N * Kp digits, in buffers of slice_elems floats
+// each; eA, eB: M * nch and N * nch ints; ws: nch * M * N double-FP32
+// partials. Returns cudaErrorNotSupported when a layout or a capacity does not
+// fit (the caller then uses the CUDA-core kernel).
 cudaError_t gemm_oz(const GemmArgs<df32>& g, float* sA, float* sB, size_t slice_elems, int* eA, int* eB,
-                    size_t exp_elems, df32* ws, size_t ws_elems, int sm_count, uint32_t* errw, cudaStream_t st) {
+                    size_t exp_elems, df32* ws, size_t ws_elems, int sm_count, uint32_t* errw, cudaStream_t st,
+                    bool bf16) {
   using namespace tc;
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
   if (g.K < 1) return cudaErrorNotSupported;
   long long lda, ldb, one;
   if (!lin_stride(g.am, lda) || !lin_stride(g.ak, one) || one != 1) return cudaErrorNotSupported;
   if (!lin_stride(g.bk, one) || one != 1 || !lin_stride(g.bn, ldb)) return cudaErrorNotSupported;
-  const int Kp = (g.K + 3) / 4 * 4;  // 16-byte rows of FP32 digits
+  const int eb = bf16 ? 2 : 4;                         // bytes per digit
+  const int Kp = (g.K + 16 / eb - 1) / (16 / eb) * (16 / eb);  // 16-byte rows of digits
   const int nch = (g.K + OZ_KC - 1) / OZ_KC;
-  if ((size_t)OZ_S * g.M * Kp > slice_elems || (size_t)OZ_S * g.N * Kp > slice_elems) return cudaErrorNotSupported;
+  const size_t cap = slice_elems * sizeof(float);
+  if ((size_t)OZ_S * g.M * Kp * eb > cap || (size_t)OZ_S * g.N * Kp * eb > cap) return cudaErrorNotSupported;
   if ((size_t)g.M * nch > exp_elems || (size_t)g.N * nch > exp_elems) return cudaErrorNotSupported;
   if ((size_t)nch * g.M * g.N > ws_elems) return cudaErrorNotSupported;
   auto slice = [&](int R, const df32* X, long long ld, float* sl, int* ex) {
     const long long warps = (long long)R * nch;
     const int blocks = (int)((warps * 32 + 255) / 256);
     ++tl_launches;
-    oz_slice_kernel<df32><<<blocks, 256, 0, st>>>(R, g.K, Kp, X, ld, sl, ex, nch);
+    if (bf16)
+      oz_slice_kernel<df32, __nv_bfloat16><<<blocks, 256, 0, st>>>(R, g.K, Kp, X, ld, (__nv_bfloat16*)sl, ex, nch);
+    else
+      oz_slice_kernel<df32, float><<<blocks, 256, 0, st>>>(R, g.K, Kp, X, ld, sl, ex, nch);
     return cudaGetLastError();
   };
   cudaError_t e = slice(g.M, g.A, lda, sA, eA);
   if (e != cudaSuccess) return e;
   if ((e = slice(g.N, g.B, ldb, sB, eB)) != cudaSuccess) return e;
   CUtensorMap ta, tb;
-  if (!make_map(&ta, sA, (uint64_t)Kp, (uint64_t)OZ_S * g.M, (uint64_t)Kp, OZ_BK, BM, CU_TENSOR_MAP_SWIZZLE_64B))
+  const CUtensorMapDataType dt = bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const uint32_t kb = OZ_KBYTES / eb;
+  if (!make_map(&ta, sA, (uint64_t)Kp, (uint64_t)OZ_S * g.M, (uint64_t)Kp, kb, BM, CU_TENSOR_MAP_SWIZZLE_64B, dt, eb))
     return cudaErrorNotSupported;
-  if (!make_map(&tb, sB, (uint64_t)Kp, (uint64_t)OZ_S * g.N, (uint64_t)Kp, OZ_BK, BN, CU_TENSOR_MAP_SWIZZLE_64B))
+  if (!make_map(&tb, sB, (uint64_t)Kp, (uint64_t)OZ_S * g.N, (uint64_t)Kp, kb, BN, CU_TENSOR_MAP_SWIZZLE_64B, dt, eb))
     return cudaErrorNotSupported;
-  if ((e = ensure_smem((const void*)gemm_oz_kernel, OZ_SMEM)) != cudaSuccess)
-    return e;
+  const void* kern = bf16 ? (const void*)gemm_oz_kernel<__nv_bfloat16> : (const void*)gemm_oz_kernel<float>;
+  if ((e = ensure_smem(kern, OZ_SMEM)) != cudaSuccess) return e;
   dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, nch);
   ++tl_launches;
-  gemm_oz_kernel<<<grid, 128, OZ_SMEM, st>>>(ta, tb, g.M, g.N, g.K, eA, eB, nch, ws, errw);
+  if (bf16)
+    gemm_oz_kernel<__nv_bfloat16><<<grid, 128, OZ_SMEM, st>>>(ta, tb, g.M, g.N, g.K, eA, eB, nch, ws, errw);
+  else
+    gemm_oz_kernel<float><<<grid, 128, OZ_SMEM, st>>>(ta, tb, g.M, g.N, g.K, eA, eB, nch, ws, errw);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return splitk_reduce<df32>(g, ws, nch, sm_count, st);
 }

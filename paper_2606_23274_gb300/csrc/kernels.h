@@ -36,13 +36,15 @@ cudaError_t splitk_reduce(const GemmArgs<T>& g, const T* ws, int splits, int sm_
 cudaError_t gemm_tf32(const GemmArgs<float>& g, float* ws, size_t ws_elems, int sm_count, uint32_t* errw,
                       cudaStream_t st, bool split = false);
 
-// FP64-class GEMM of double-FP32 operands on the TF32 tensor cores (fixed-point
-// digit split, exact FP32 accumulation of the leading digit levels); scratch as
+// FP64-class GEMM of double-FP32 operands on the tensor cores (fixed-point
+// digit split, exact FP32 accumulation of the leading digit levels), with TF32
+// digits (kind::tf32) or BF16 digits (kind::f16, bf16 = true); scratch as
 // documented in gemm_tc.cu. cudaErrorNotSupported: use gemm_simt.
 constexpr int OZ_DIGITS = 6;
 constexpr int OZ_CHUNK = 512;
 cudaError_t gemm_oz(const GemmArgs<df32>& g, float* sA, float* sB, size_t slice_elems, int* eA, int* eB,
-                    size_t exp_elems, df32* ws, size_t ws_elems, int sm_count, uint32_t* errw, cudaStream_t st);
+                    size_t exp_elems, df32* ws, size_t ws_elems, int sm_count, uint32_t* errw, cudaStream_t st,
+                    bool bf16 = false);
 
 // out[om(i) + on(j)] = (Tout) (scale * in[im(i) + in_(j)]), i < rows, j < cols
 template <typename Tin, typename Tout>

@@ -154,15 +154,17 @@ def test_fp64_path_matches_oracle_full_size():
             assert e["entries"] <= 1e-8 and e["lambdas"] <= 1e-9
 
 
-def test_timed_schedule_matches_oracle_full_size():
+@pytest.mark.parametrize("hi", ["df32", "bf16_split"])
+def test_timed_schedule_matches_oracle_full_size(hi):
     """The bench's schedule (one 3xTF32 sweep, then DF32 with fast_factor 1) at
     L = 30, chi = 128: ||C||^2 and the spectra against the oracle, and the
     operator within a relative Frobenius error of 1e-7 of the FP64 fit from the
     converged sweep (3) on (measured: 5e-9 at sweep 3, 4e-11 at sweep 4; the
-    mixed-precision bound is 1e-6)."""
+    mixed-precision bound is 1e-6). bf16_split: the same DF32 sweeps with the
+    digit planes of their tensor-core contractions in BF16."""
     g = _load("kron_L30_chi128")
-    for s, e in enumerate(_mixed_vs_fp64(g, "df32", 1, lo="tf32x3"), 1):
-        print("timed schedule L30 sweep", s, e)
+    for s, e in enumerate(_mixed_vs_fp64(g, hi, 1, lo="tf32x3"), 1):
+        print("timed schedule L30 sweep", hi, s, e)
         if s >= 2:
             assert e["norm2"] <= 1e-9
         if "lambdas" in e:

@@ -270,17 +270,20 @@ def test_fast_factor_fp64_converges():
     assert res <= res_o * (1 + 1e-6)
 
 
+@pytest.mark.parametrize("precision", ["df32", "bf16_split"])
 @pytest.mark.parametrize("gauge", ["site", "inverse"])
 @pytest.mark.parametrize("update", ["svd", "rsvd"])
-def test_df32_fit_matches_fp64_oracle(gauge, update):
-    """Double-FP32 contractions (FP64-class on the FP32 pipes) with the FP64
-    factorisation: the same results as the FP64 oracle to 1e-9."""
+def test_df32_fit_matches_fp64_oracle(gauge, update, precision):
+    """Double-FP32 contractions (FP64-class: the digit split on the TF32 or, for
+    bf16_split, the BF16 tensor cores, the small ones on the FP32 pipes) with the
+    FP64 factorisation: the same results as the FP64 oracle to 1e-9. The chain's
+    K = 1024 contractions take the digit split with two chunks."""
     A, B = mpo_pair("kron_L12_chi32", 1)
     chi, sweeps = 12, 4
     f = FitOracle(A, B, chi, 0.0, gauge=gauge, update=update, oversample=4, seed=3, sv_cutoff=1e-12)
     f.sweep(sweeps, stop_on_converge=False)
     C, reps, b, lam = _gpu_fit(A, B, chi, 0.0, sweeps, gauge=gauge, update=update, oversample=4, seed=3,
-                               precision="df32", sv_cutoff=1e-12, conv_tol=0.0)
+                               precision=precision, sv_cutoff=1e-12, conv_tol=0.0)
     assert b == f.bonds()
     assert _rel(C, f.result()) <= 1e-9
     for r, h in zip(reps, f.st.history):

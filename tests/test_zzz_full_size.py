@@ -1,7 +1,8 @@
 """The timed configuration at full size: L = 30, chi_A = chi_B = chi_C = 128,
 Kronecker-sum inputs (K = 128 terms), randomized update (k_s = 138), one 3xTF32
 sweep, then DF32 sweeps with the FP64-polished FP32 factorisation: the launch
-configuration bench.py times. Where the oracle cannot follow, check what holds
+configuration bench.py times (its DF32 contractions with BF16 digit planes,
+bf16_split; the TF32 digit planes, df32, are checked the same way). Where the oracle cannot follow, check what holds
 at any size, with plain PyTorch FP64 on the device (tests/mpo_props.py):
 
 * the fit converges to delta <= 1e-8;
@@ -37,12 +38,13 @@ def _gram_dev(c, left: bool) -> float:
     return float((G - torch.eye(G.shape[0], dtype=G.dtype, device=G.device)).abs().max())
 
 
-def test_timed_configuration_full_size():
+@pytest.mark.parametrize("hi", ["bf16_split", "df32"])
+def test_timed_configuration_full_size(hi):
     A, B = mpo_pair("kron_L30_chi128", seed=0)
     f = ttfit.tt_fit_create(A, B, 128, 1e-8, "site", update="rsvd", oversample=10, seed=0, precision="tf32x3")
     try:
         rep = f.sweep(1)
-        f.set_precision("df32", fast_factor=True)
+        f.set_precision(hi, fast_factor=True)
         for _ in range(8):
             rep = f.sweep(1)
             if rep["converged"]:
@@ -68,5 +70,5 @@ def test_timed_configuration_full_size():
     finally:
         g.destroy()
     err = diff_norm(C, Cref) / norm2(Cref) ** 0.5
-    print(f"timed configuration: relative Frobenius error vs the FP64 fit after {sweeps} sweeps: {err:.3e}")
+    print(f"timed configuration ({hi}): relative Frobenius error vs the FP64 fit after {sweeps} sweeps: {err:.3e}")
     assert err <= 1e-7
