@@ -421,7 +421,10 @@ def native(args):
         "accuracy": accuracy,
     }
     if rank == 0 and not args.no_extras and args.workload == WORKLOAD:
-        out["extras"] = extras(ttfit, dev, stream, out["norm2_C"])
+        try:
+            out["extras"] = extras(ttfit, dev, stream, out["norm2_C"])
+        except Exception as e:  # the timed line stands on its own; report what stopped the extras
+            out["extras"] = {"error": f"{type(e).__name__}: {e}"[:500]}
     if rank == 0 and not args.no_cpu_baseline and args.workload == WORKLOAD:
         out["cpu_baseline"] = cpu_baseline(sweeps)
     if rank == 0:
