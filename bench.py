@@ -145,7 +145,8 @@ def rel_frobenius(X, Y) -> float:
     return norm_of(S) / norm_of([y.double() for y in Y])
 
 
-STAGES = ("halves_ms", "join_ms", "env_finish_ms", "factorize_ms", "gauge_ms", "contraction_flops", "launches")
+STAGES = ("halves_ms", "join_ms", "env_finish_ms", "factorize_ms", "gauge_ms", "contraction_flops", "launches",
+          "tc_issued_flops", "cc_issued_flops")
 # peaks of the plain CUDA-core pipes (ALU bound): 152 SMs x FMA lanes per SM x 2 flop x max SM clock
 FMA_LANES = {"f64": 2, "f32": 128}
 DF32_INSTR = 15  # FP32 instructions of one double-FP32 multiply-add (csrc/common.cuh, madd)
@@ -174,6 +175,8 @@ def run_fit(ttfit, Ain, Bin, schedule, seed, dev, stream, chi=CHI, lo_sweeps=LO_
         history.append(rep["delta"])
         phase_sweeps[cur] += 1
         st = f.stage_times()
+        ex = f.exec_flops()
+        st["tc_issued_flops"], st["cc_issued_flops"] = ex["tensor_core"], ex["cuda_core"]
         for k in STAGES:
             phases[cur][k] += st[k]
         if rep["converged"] and (hi is None or cur == hi):
@@ -392,6 +395,8 @@ def native(args):
         roof = {"bound": "alu", "achieved": None, "peak": None, "unit": "TFLOP/s", "frac": None, "traffic": None,
                 "kernel": f"{dom_stage} ({dom_phase} phase)"}
     local_flops = sum(agg[p]["contraction_flops"] for p in names)
+    tc_issued = sum(agg[p]["tc_issued_flops"] for p in names)
+    cc_issued = sum(agg[p]["cc_issued_flops"] for p in names)
     local_ms = sum(agg[p]["halves_ms"] + agg[p]["join_ms"] + agg[p]["env_finish_ms"] for p in names)
     rep, sweeps, phase_sweeps, _, _, launches = results[-1]
     dtypes = {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "tf32x3": "tf32x3", "df32": "f32x2",
@@ -412,6 +417,14 @@ def native(args):
         "delta_history": [float(f"{d:.3e}") if d != float("inf") else None for d in rep["history"]],
         "local_update_tflops": round(local_flops / (local_ms * 1e-3) / 1e12, 3) if local_ms > 0 else None,
         "local_update": local_update_roof(local_flops, local_ms, pk, bf16_digits="bf16_split" in names),
+        "local_update_as_issued": {
+            "algorithmic_tflop_per_fit": round(local_flops / 1e12, 4),
+            "tensor_core_mma_tflop_per_fit": round(tc_issued / 1e12, 4),
+            "cuda_core_tflop_per_fit": round(cc_issued / 1e12, 4),
+            "issued_tensor_tflops": round(tc_issued / (local_ms * 1e-3) / 1e12, 2) if local_ms > 0 else None,
+            "note": "MMA flops as the tensor cores executed them (128 x 128 tiles, K per k-block, 3 passes for "
+                    "3xTF32, 21 digit pairs for the FP64-class digit split) over the same stage time as "
+                    "local_update; the algorithmic count credits none of that"},
         "stage_ms_per_fit": {p: {k: round(agg[p][k], 2) for k in STAGES[:5]} for p in names},
         "create_switch_export_ms": {k: round(statistics.mean(r[0]["host_ms"][k] for r in results), 2)
                                     for k in ("create", "switch", "export")},

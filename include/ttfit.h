@@ -252,6 +252,16 @@ const char* tt_fit_last_error(const tt_fit* h);
  * sweep ran. */
 tt_status tt_fit_stage_times(const tt_fit* h, double out[7]);
 
+/* The same contractions of the last tt_fit_sweep call as the hardware issued
+ * them: out[0] tensor-core MMA flops, with the tiles padded to 128 x 128 and K
+ * to the k-block, and every pass counted (3 for TF32_SPLIT, 21 digit pairs for
+ * the DF32 and BF16_SPLIT digit split); out[1] flops of the contractions that
+ * ran on the CUDA cores (2 M N K each, in the chain's own type). Against
+ * out[5] of tt_fit_stage_times this separates the work the method needs from
+ * the work its precision scheme adds (Sec. 2.3, Table 1 counts the former).
+ * Returns TT_ERR_STATE if no sweep ran. */
+tt_status tt_fit_exec_flops(const tt_fit* h, double out[2]);
+
 /* Kernel launches issued by this handle since tt_fit_create, cumulative over
  * creation (input preparation, initial guess, right environments), sweeps,
  * precision switches and result export. Lets a caller check that the work it

@@ -205,6 +205,9 @@ struct Work {
   bool connect_pending = false;  // ev[8], ev[9] recorded but not yet read
   double stage_ms[5] = {0, 0, 0, 0, 0};
   double flops = 0;
+  // the chain contractions as issued: tensor-core MMA flops (split passes, digit pairs and tile
+  // padding included) and CUDA-core flops
+  double tc_flops = 0, cc_flops = 0;
   void *X1 = nullptr, *Zs = nullptr, *Th = nullptr, *gws = nullptr;
   size_t gws_elems = 0;
   // factorisation workspace (FP64-sized)
@@ -326,9 +329,13 @@ struct FactT<df32> {
   using type = double;
 };
 
+inline double round_up(long long x, long long m) { return (double)((x + m - 1) / m * m); }
+
 template <typename T>
 void gemm(tt_fit* h, const GemmArgs<T>& g, bool chain = false) {
   const size_t wse = W(h).gws_elems * sizeof(double) / sizeof(T);
+  // MMA tiles are 128 x 128; K is issued in k-blocks, per 512-wide chunk for the digit split
+  const double mn = round_up(g.M, 128) * round_up(g.N, 128);
   if constexpr (std::is_same<T, df32>::value) {
     Work& w = W(h);
     if (chain && h->use_oz && w.ozA && (long long)g.M * g.N * g.K >= (1ll << 21)) {
@@ -336,6 +343,10 @@ void gemm(tt_fit* h, const GemmArgs<T>& g, bool chain = false) {
                               w.errw, w.st, h->oz_bf16);
       if (e == cudaSuccess) {
         h->tc_launches += 1;
+        const long long kc = OZ_CHUNK, kb = h->oz_bf16 ? 32 : 16;
+        const double k_issued = (double)(g.K / kc * kc) + (g.K % kc ? round_up(g.K % kc, kb) : 0.0);
+        const int pairs = OZ_DIGITS * (OZ_DIGITS + 1) / 2;  // digit pairs i + j < OZ_DIGITS
+        w.tc_flops += 2.0 * mn * k_issued * pairs;
         return;
       }
       if (e != cudaErrorNotSupported) CK(e);
@@ -348,12 +359,14 @@ void gemm(tt_fit* h, const GemmArgs<T>& g, bool chain = false) {
                                 h->precision == TT_PREC_TF32_SPLIT);
       if (e == cudaSuccess) {
         h->tc_launches += 1;
+        W(h).tc_flops += 2.0 * mn * round_up(g.K, 32) * (h->precision == TT_PREC_TF32_SPLIT ? 3 : 1);
         return;
       }
       if (e != cudaErrorNotSupported) CK(e);
     }
   }
   CK(gemm_simt<T>(g, (T*)W(h).gws, wse, h->sm_count, W(h).st));
+  if (chain) W(h).cc_flops += 2.0 * g.M * g.N * g.K;
 }
 
 template <typename Tin, typename Tout>
@@ -2747,6 +2760,8 @@ tt_status tt_fit_sweep(tt_fit* h, int n_sweeps, tt_sweep_report* rep) {
     for (Work* w : lanes(h)) {
       for (double& s : w->stage_ms) s = 0;
       w->flops = 0;
+      w->tc_flops = 0;
+      w->cc_flops = 0;
     }
     const long long launch0 = tl_launches;
     if (h->segs.size() > 1) {
@@ -2951,6 +2966,17 @@ tt_status tt_fit_stage_times(const tt_fit* h, double out[7]) {
     out[5] += w->flops;
   }
   out[6] = (double)h->sweep_launches;
+  return TT_OK;
+}
+
+tt_status tt_fit_exec_flops(const tt_fit* h, double out[2]) {
+  if (!h || !out) return TT_ERR_INVALID_ARGUMENT;
+  if (!h->have_times) return TT_ERR_STATE;
+  out[0] = out[1] = 0;
+  for (Work* w : lanes(const_cast<tt_fit*>(h))) {
+    out[0] += w->tc_flops;
+    out[1] += w->cc_flops;
+  }
   return TT_OK;
 }
 

@@ -80,6 +80,8 @@ def load():
         lib.tt_svd_truncated.argtypes = [ct.c_void_p, ct.c_int, ct.c_int, ct.c_int, ct.c_double, ct.c_void_p,
                                          ct.c_void_p, ct.c_void_p, ct.POINTER(ct.c_int), ct.c_void_p]
         lib.tt_svd_truncated.restype = ct.c_int
+        lib.tt_fit_exec_flops.argtypes = [ct.c_void_p, ct.POINTER(ct.c_double)]
+        lib.tt_fit_exec_flops.restype = ct.c_int
         lib.tt_fit_set_precision.argtypes = [ct.c_void_p, ct.c_int, ct.c_int]
         lib.tt_fit_set_precision.restype = ct.c_int
         lib.tt_fit_stage_times.argtypes = [ct.c_void_p, ct.POINTER(ct.c_double)]
@@ -474,6 +476,13 @@ class Fit:
         keys = ["halves_ms", "join_ms", "env_finish_ms", "factorize_ms", "gauge_ms", "contraction_flops",
                 "launches"]
         return dict(zip(keys, list(v)))
+
+    def exec_flops(self) -> dict:
+        """The last sweep's contractions as issued: tensor-core MMA flops (padding and split
+        passes included) and CUDA-core flops."""
+        v = (ct.c_double * 2)()
+        _check(load().tt_fit_exec_flops(self.h, v), self.h, "tt_fit_exec_flops")
+        return {"tensor_core": v[0], "cuda_core": v[1]}
 
     def launch_count(self) -> int:
         """Kernel launches this fit has issued since creation (tt_fit_launch_count)."""

@@ -371,3 +371,28 @@ def test_block_cache_reuse_and_release():
     assert [r["norm2_C"] for r in r0] == [r["norm2_C"] for r in r1]
     assert ttfit.tt_device_cache_release(-1) > 0
     assert ttfit.tt_device_cache_release(-1) == 0
+
+
+@pytest.mark.parametrize("precision,passes", [("fp64", None), ("df32", 21), ("bf16_split", 21), ("tf32x3", 3)])
+def test_issued_flops_account_for_the_algorithmic_ones(precision, passes):
+    """tt_fit_exec_flops against tt_fit_stage_times on the same sweeps: in FP64 every chain
+    contraction runs on the CUDA cores, so the two counts agree exactly; on the tensor cores
+    each algorithmic flop is issued once per pass (3xTF32: 3, digit split: 21 digit pairs) or
+    more (tile and k-block padding)."""
+    A, B = mpo_pair("kron_L12_chi32", 1)
+    f = ttfit.tt_fit_create(A, B, 12, 0.0, "site", update="rsvd", oversample=4, seed=3, precision=precision,
+                            conv_tol=0.0)
+    try:
+        for _ in range(2):
+            f.sweep(1)
+            alg = f.stage_times()["contraction_flops"]
+            ex = f.exec_flops()
+            assert alg > 0
+            if passes is None:
+                assert ex["tensor_core"] == 0.0 and ex["cuda_core"] == alg
+            else:
+                assert ex["tensor_core"] > 0.0
+                assert ex["tensor_core"] / passes + ex["cuda_core"] >= alg * (1 - 1e-12)
+                assert ex["cuda_core"] < alg
+    finally:
+        f.destroy()
