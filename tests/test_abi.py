@@ -97,3 +97,75 @@ def test_partition_matches_oracle_without_gpu():
                 assert [(a + 1, b + 1) for a, b in zip(first, last)] == partition(L, n, e), (L, n, e)
     one = (ct.c_int * 4)()
     assert lib.tt_partition(7, 4, 0, one, one) == ttfit.TT_ERR_INVALID_ARGUMENT   # 7 sites < 2 x 4
+
+
+def _host_desc(L, dout, din, bond, dtype=0, null_core=-1):
+    """An MPO descriptor whose core pointers are never dereferenced by the checks below."""
+    from paper_2606_23274_gb300 import ttfit
+    keep = [(ct.c_int * L)(*dout), (ct.c_int * L)(*din), (ct.c_int * (L + 1))(*bond)]
+    cores = (ct.c_void_p * L)(*[None if l == null_core else 0x1000 + 64 * l for l in range(L)])
+    keep.append(cores)
+    d = ttfit.tt_mpo_desc(L, keep[0], keep[1], keep[2], cores, dtype)
+    return d, keep
+
+
+def test_create_rejects_bad_arguments_before_any_device_call():
+    """tt_fit_create's argument and shape checks (include/ttfit.h: argument errors return
+    TT_ERR_INVALID_ARGUMENT, inconsistent legs or bonds TT_ERR_SHAPE_MISMATCH) run on the
+    host before the first CUDA call, so they are exercised here without a GPU."""
+    ttfit = _built_lib()
+    lib = ttfit.load()
+    INV, SHAPE = ttfit.TT_ERR_INVALID_ARGUMENT, ttfit.TT_ERR_SHAPE_MISMATCH
+    L = 4
+    A, ka = _host_desc(L, [2] * L, [2] * L, [1, 4, 4, 4, 1])
+    B, kb = _host_desc(L, [2] * L, [3] * L, [1, 4, 4, 4, 1])
+
+    def create(a=A, b=B, chi=8, tol=0.0, gauge=0, **opt):
+        o = ttfit.tt_fit_options()
+        o.struct_size = ct.sizeof(o)
+        o.update, o.oversample, o.precision, o.sv_cutoff, o.conv_tol, o.prepare_inputs = 1, 10, 3, -1.0, -1.0, 1
+        for k, v in opt.items():
+            setattr(o, k, v)
+        h = ct.c_void_p()
+        st = lib.tt_fit_create(ct.byref(a), ct.byref(b), chi, ct.c_double(tol), gauge, ct.byref(o), ct.byref(h))
+        assert not h.value  # nothing is handed out on failure
+        return st
+
+    lib.tt_fit_create.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_double, ct.c_int, ct.c_void_p,
+                                  ct.c_void_p]
+    # the problem: chi_max >= 1, tol >= 0 (not NaN), a known gauge
+    assert create(chi=0) == INV
+    assert create(tol=float("nan")) == INV
+    assert create(gauge=2) == INV
+    # options
+    assert create(struct_size=8) == INV
+    assert create(update=2) == INV
+    assert create(precision=6) == INV and create(precision=-1) == INV
+    assert create(oversample=-1) == INV
+    assert create(init=4) == INV
+    assert create(init=2) == INV                      # TT_INIT_GIVEN without init_C
+    assert create(edge_extra=-1) == INV
+    assert create(fast_factor=4) == INV
+    assert create(ab_rank=-1) == INV
+    assert create(ab_rank=2, prepare_inputs=0) == INV
+    # shapes: C = A B contracts A's input legs with B's output legs (B's input legs only reach C)
+    B3, kb3 = _host_desc(L, [3] * L, [2] * L, [1, 4, 4, 4, 1])
+    assert create(b=B3) == SHAPE
+    B5, kb5 = _host_desc(5, [2] * 5, [2] * 5, [1, 4, 4, 4, 4, 1])
+    assert create(b=B5) == SHAPE                      # different lengths
+    A1, ka1 = _host_desc(1, [2], [2], [1, 1])
+    B1, kb1 = _host_desc(1, [2], [2], [1, 1])
+    assert create(a=A1, b=B1) == INV                  # one site: no two-site window
+    assert create(n_segments=3) == INV                # fewer than 2 sites per segment
+    Abad, k1 = _host_desc(L, [2] * L, [2] * L, [2, 4, 4, 4, 1])
+    assert create(a=Abad) == SHAPE                    # bond[0] != 1
+    assert "bond[0]" in lib.tt_fit_last_error(None).decode()
+    Adt, k2 = _host_desc(L, [2] * L, [2] * L, [1, 4, 4, 4, 1], dtype=7)
+    assert create(a=Adt) == INV                       # unknown dtype
+    Anull, k3 = _host_desc(L, [2] * L, [2] * L, [1, 4, 4, 4, 1], null_core=2)
+    assert create(a=Anull) == INV
+    assert "NULL core" in lib.tt_fit_last_error(None).decode()
+    # every precision in the enum passes the option checks (BF16_SPLIT included); the shape check
+    # that follows is what stops these
+    for p in range(6):
+        assert create(b=B3, precision=p) == SHAPE
