@@ -75,3 +75,25 @@ def test_reference_arm_runs_on_rank_zero_only(capsys, monkeypatch):
     ns = type("A", (), {"steps": 1, "warmup": 0, "gpus": 2})()
     assert bench.reference(ns) is None
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_prints_the_contract_line(capsys, monkeypatch):
+    """bench.py --impl reference on rank 0: one JSON line with the contract's keys, the oracle timed
+    on a bounded sample (one bulk window per step)."""
+    sys.path.insert(0, ROOT)
+    import json
+    import bench
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    ns = type("A", (), {"steps": 1, "warmup": 0, "gpus": 1})()
+    bench.reference(ns)
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "s"
+    assert d["higher_is_better"] is False and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
