@@ -408,7 +408,8 @@ tt_status tt_mpo_naive_product(const tt_mpo_desc* A, const tt_mpo_desc* B, const
  * Sec. 3.1 with k_s = chi_max + oversample columns and the Philox stream
  * (3 << 40) | l of seed, where k_s < min of M's sizes), oversample, seed,
  * precision (FP64 and DF32: FP64 arithmetic; FP32, TF32, TF32_SPLIT: FP32, with
- * 3xTF32 tensor-core contractions for the TF32 ones), sv_cutoff, stream and
+ * 3xTF32 tensor-core contractions for the TF32 ones; BF16_SPLIT is rejected
+ * with TT_ERR_INVALID_ARGUMENT), sv_cutoff, stream and
  * prepare_inputs; the other fields are ignored. M_l with more than 1024 rows is
  * factorised through its (sketch's) Gram matrix, which resolves singular
  * values only down to about sqrt(eps) s_1. Needs d d' chi_max <= 1024 and
