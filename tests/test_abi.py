@@ -169,3 +169,33 @@ def test_create_rejects_bad_arguments_before_any_device_call():
     # that follows is what stops these
     for p in range(6):
         assert create(b=B3, precision=p) == SHAPE
+
+
+def test_zipup_rejects_bad_options_before_any_device_call():
+    """tt_mpo_zipup's option checks run on the host: BF16_SPLIT (not a zip-up precision), an unknown
+    precision and a negative oversample are argument errors, as are chi_max < 1 and a missing C."""
+    ttfit = _built_lib()
+    lib = ttfit.load()
+    INV = ttfit.TT_ERR_INVALID_ARGUMENT
+    L = 4
+    A, ka = _host_desc(L, [2] * L, [2] * L, [1, 4, 4, 4, 1])
+    B, kb = _host_desc(L, [2] * L, [2] * L, [1, 4, 4, 4, 1])
+    C, kc = _host_desc(L, [2] * L, [2] * L, [1, 4, 16, 4, 1])
+    bonds = (ct.c_int * (L + 1))()
+    lib.tt_mpo_zipup.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_double, ct.c_void_p, ct.c_void_p,
+                                 ct.c_void_p]
+
+    def zipup(chi=8, c=C, **opt):
+        o = ttfit.tt_fit_options()
+        o.struct_size = ct.sizeof(o)
+        o.update, o.oversample, o.precision, o.sv_cutoff, o.prepare_inputs = 1, 10, 0, -1.0, 1
+        for k, v in opt.items():
+            setattr(o, k, v)
+        return lib.tt_mpo_zipup(ct.byref(A), ct.byref(B), chi, ct.c_double(0.0), ct.byref(o),
+                                ct.byref(c) if c is not None else None, bonds)
+
+    assert zipup(precision=3) == INV
+    assert zipup(precision=6) == INV
+    assert zipup(oversample=-1) == INV
+    assert zipup(chi=0) == INV
+    assert zipup(c=None) == INV
