@@ -509,6 +509,7 @@ def extras(ttfit, dev, stream, norm2_site):
         seg[str(n_seg)] = {"time_to_tol_s": round(t, 4), "sweeps_or_phases": n, "converged": bool(rep["converged"]),
                            "delta": rep["delta"], "norm2_rel_to_site_fit": rep["norm2_C"] / norm2_site - 1.0,
                            "edge_extra": ee}
+    seg["schedule"] = "tf32x3>df32 (TF32 digit planes)"
     out["segments_inverse_gauge_L30_chi128"] = seg
     seg = {}
     for n_seg, ee in ((2, 0), (4, 2), (8, 2)):
@@ -516,6 +517,7 @@ def extras(ttfit, dev, stream, norm2_site):
         seg[str(n_seg)] = {"time_to_tol_s": round(t, 4), "phases": n, "converged": bool(rep["converged"]),
                            "delta": rep["delta"], "norm2_rel_to_site_fit": rep["norm2_C"] / norm2_site - 1.0,
                            "edge_extra": ee, "merges": 2}
+    seg["schedule"] = "tf32x3>df32 (TF32 digit planes), FP64 factorisation after the switch"
     out["segments_site_gauge_L30_chi128"] = seg
 
     # config 2: plain FP32 (FP32 CUDA-core contractions, FP32 SVD) vs mixed (3xTF32, then DF32 with the
