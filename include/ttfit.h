@@ -142,7 +142,7 @@ typedef struct {
                        /* (streams (4 << 40) | l for A, (5 << 40) | l for B, site l 1-based), */
                        /* drawn once at creation on the prepared chains (right to left; the  */
                        /* QR sweep again only before a zip-up guess); the fit then contracts */
-                       /* bonds of at most k. The                                            */
+                       /* bonds of at most k, in the environments and the update alike. The  */
                        /* fit approximates the product of the projected chains, so this needs */
                        /* A and B with decaying bond spectra. Needs prepare_inputs. 0 = off.  */
 } tt_fit_options;
