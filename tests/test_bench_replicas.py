@@ -97,3 +97,18 @@ def test_reference_arm_prints_the_contract_line(capsys, monkeypatch):
     assert d["higher_is_better"] is False and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_local_update_roofline_takes_the_peak_of_the_digit_type():
+    """The local-update fraction is taken against the TF32 rate (half of bf16) unless the FP64-class
+    sweeps run their digit products on the BF16 tensor cores; without a measured-peaks file the
+    recipe's fallback is used and said."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.local_update_roof(1.7e12, 1000.0, {})          # 1.7 TFLOP/s
+    assert r["peak"] == 850.0 and r["frac"] == round(1.7 / 850.0, 4) and "fallback" in r["peak_source"]
+    r = bench.local_update_roof(1.7e12, 1000.0, {}, bf16_digits=True)
+    assert r["peak"] == 1700.0 and r["frac"] == round(1.7 / 1700.0, 4)
+    r = bench.local_update_roof(1.7e12, 1000.0, {"bf16_tflops_sustained": 1707.0})
+    assert r["peak"] == 853.5 and "of measured" in r["peak_source"]
+    assert bench.local_update_roof(1.0, 0.0, {}) is None
