@@ -112,3 +112,21 @@ def test_local_update_roofline_takes_the_peak_of_the_digit_type():
     r = bench.local_update_roof(1.7e12, 1000.0, {"bf16_tflops_sustained": 1707.0})
     assert r["peak"] == 853.5 and "of measured" in r["peak_source"]
     assert bench.local_update_roof(1.0, 0.0, {}) is None
+
+
+def test_accuracy_helpers_match_the_oracle():
+    """The bench's accuracy figure (rel_frobenius) and its ||C||^2 check (sum_sq) run in torch on the
+    tensors' device; on CPU tensors they agree with the oracle's pinned difference norm and norm."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    from oracle.mpo import mpo_diff_norm, mpo_norm
+    from paper_2606_23274_gb300.synth import gaussian_mpo
+    X = gaussian_mpo(6, 2, 5, 0, 0)
+    Y = [y + 1e-3 * x for x, y in zip(gaussian_mpo(6, 2, 5, 0, 1), X)]   # X near Y
+    tX = [torch.from_numpy(x) for x in X]
+    tY = [torch.from_numpy(y) for y in Y]
+    want = mpo_diff_norm(X, Y) / mpo_norm(Y)
+    assert abs(bench.rel_frobenius(tX, tY) - want) <= 1e-10 * want
+    assert bench.rel_frobenius(tY, tY) <= 1e-14
+    assert np.isclose(bench.sum_sq(tX), mpo_norm(X) ** 2, rtol=1e-12)
