@@ -1,7 +1,11 @@
-"""The multi-GPU mode of bench.py on CPU: one process per rank (gloo, world size 2,
-127.0.0.1), each fitting its own pair, the step time taken as the maximum over
-the ranks, and the reference arm running on rank 0 only. The data path has no
-collective; these are the only cross-rank steps."""
+"""bench.py's host logic on CPU.
+
+* The multi-GPU mode: one process per rank (gloo, world size 2, 127.0.0.1), each
+  fitting its own pair, the step time taken as the maximum over the ranks, and the
+  reference arm running on rank 0 only. The data path has no collective; these are
+  the only cross-rank steps.
+* The reference arm's JSON line.
+* The roofline and accuracy helpers behind the bench line."""
 import os
 import socket
 import sys
