@@ -199,3 +199,23 @@ def test_zipup_rejects_bad_options_before_any_device_call():
     assert zipup(oversample=-1) == INV
     assert zipup(chi=0) == INV
     assert zipup(c=None) == INV
+
+
+def test_binding_builds_options_and_has_no_cpu_fallback():
+    """The binding maps names to the header's enums (stream given, so no device is touched), and
+    without a GPU a fit fails loudly instead of computing anywhere else."""
+    ttfit = _built_lib()
+    o, _ = ttfit._options(update="rsvd", precision="bf16_split", init="zipup", ab_rank=3, fast_factor=True,
+                          n_segments=2, edge_extra=1, stream=0)
+    assert (o.update, o.precision, o.init, o.ab_rank, o.fast_factor, o.n_segments, o.edge_extra) == \
+        (1, 3, 3, 3, 1, 2, 1)
+    assert ttfit.PRECISION == {"fp64": 0, "fp32": 1, "tf32": 2, "bf16_split": 3, "tf32x3": 4, "df32": 5}
+    with pytest.raises(KeyError):
+        ttfit._options(precision="fp16", stream=0)
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2606_23274_gb300.synth import gaussian_mpo
+    A = gaussian_mpo(4, 2, 2, 0, 0)
+    with pytest.raises(RuntimeError):    # torch finds no device for the inputs; nothing falls back
+        ttfit.tt_fit_create(A, A, 4, 0.0)
